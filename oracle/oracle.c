@@ -1,0 +1,461 @@
+/*
+ * Plain single-threaded CPU oracle of the diffusion-free bit-level video
+ * cipher of arXiv 2505.07158 ("Real-Time Bit-Level Encryption of Full
+ * High-Definition Video Without Diffusion").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * statement of what the cipher computes.  Only the test-suite, the smoke
+ * check and the benchmark's CPU-baseline leg load it.  It shares no code,
+ * header, table or constant generator with the CUDA library: the SHA-256
+ * round constants below are *derived* here from their FIPS 180-4 definition
+ * (integer cube and square roots of the first primes), while the CUDA side
+ * carries its own table.
+ *
+ * Build: gcc -std=c11 -O2 -ffp-contract=off -fno-fast-math -fPIC -shared.
+ * -ffp-contract=off is required: the chaotic iteration must round every
+ * multiply and add separately (no fused multiply-add), also on aarch64.
+ *
+ * Every function cites the passage of the paper it follows.  Where the paper
+ * is silent or garbled, the reading taken is stated at the function.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+/* ------------------------------------------------------------------------ */
+/* SHA-256 (FIPS 180-4), used by Sec. II-A to digest each sub-frame.        */
+/* ------------------------------------------------------------------------ */
+
+static uint32_t sha_k[64];
+static uint32_t sha_h0[8];
+static int sha_ready = 0;
+
+/* floor(cbrt(x)) for x < 2^105, by bisection on integers. */
+static uint64_t icbrt128(unsigned __int128 x) {
+    uint64_t lo = 0, hi = (uint64_t)1 << 36;
+    while (hi - lo > 1) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        unsigned __int128 c = (unsigned __int128)mid * mid * mid;
+        if (c <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+/* floor(sqrt(x)) for x < 2^70, by bisection on integers. */
+static uint64_t isqrt128(unsigned __int128 x) {
+    uint64_t lo = 0, hi = (uint64_t)1 << 36;
+    while (hi - lo > 1) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        unsigned __int128 c = (unsigned __int128)mid * mid;
+        if (c <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+/* FIPS 180-4 Sec. 4.2.2 / 5.3.3: K_t = first 32 bits of the fractional part
+ * of the cube root of the t-th prime; H0_i = first 32 bits of the fractional
+ * part of the square root of the i-th prime.  floor(r * 2^32) mod 2^32 with
+ * r = p^(1/3) equals floor(cbrt(p * 2^96)) mod 2^32 exactly. */
+static void sha_init_constants(void) {
+    uint32_t primes[64];
+    int cnt = 0;
+    for (uint32_t c = 2; cnt < 64; ++c) {
+        int is_p = 1;
+        for (uint32_t d = 2; d * d <= c; ++d)
+            if (c % d == 0) { is_p = 0; break; }
+        if (is_p) primes[cnt++] = c;
+    }
+    for (int t = 0; t < 64; ++t)
+        sha_k[t] = (uint32_t)icbrt128((unsigned __int128)primes[t] << 96);
+    for (int i = 0; i < 8; ++i)
+        sha_h0[i] = (uint32_t)isqrt128((unsigned __int128)primes[i] << 64);
+    sha_ready = 1;
+}
+
+static uint32_t rotr32(uint32_t x, int n) { return (x >> n) | (x << (32 - n)); }
+
+/* FIPS 180-4 Sec. 6.2.2: one compression of a 64-byte block. */
+static void sha_compress(uint32_t H[8], const uint8_t blk[64]) {
+    uint32_t W[64];
+    for (int t = 0; t < 16; ++t)
+        W[t] = ((uint32_t)blk[4 * t] << 24) | ((uint32_t)blk[4 * t + 1] << 16) |
+               ((uint32_t)blk[4 * t + 2] << 8) | (uint32_t)blk[4 * t + 3];
+    for (int t = 16; t < 64; ++t) {
+        uint32_t s0 = rotr32(W[t - 15], 7) ^ rotr32(W[t - 15], 18) ^ (W[t - 15] >> 3);
+        uint32_t s1 = rotr32(W[t - 2], 17) ^ rotr32(W[t - 2], 19) ^ (W[t - 2] >> 10);
+        W[t] = s1 + W[t - 7] + s0 + W[t - 16];
+    }
+    uint32_t a = H[0], b = H[1], c = H[2], d = H[3];
+    uint32_t e = H[4], f = H[5], g = H[6], h = H[7];
+    for (int t = 0; t < 64; ++t) {
+        uint32_t S1 = rotr32(e, 6) ^ rotr32(e, 11) ^ rotr32(e, 25);
+        uint32_t ch = (e & f) ^ (~e & g);
+        uint32_t T1 = h + S1 + ch + sha_k[t] + W[t];
+        uint32_t S0 = rotr32(a, 2) ^ rotr32(a, 13) ^ rotr32(a, 22);
+        uint32_t maj = (a & b) ^ (a & c) ^ (b & c);
+        uint32_t T2 = S0 + maj;
+        h = g; g = f; f = e; e = d + T1;
+        d = c; c = b; b = a; a = T1 + T2;
+    }
+    H[0] += a; H[1] += b; H[2] += c; H[3] += d;
+    H[4] += e; H[5] += f; H[6] += g; H[7] += h;
+}
+
+/* FIPS 180-4 Sec. 5.1.1 padding + Sec. 6.2 hash computation. */
+void oracle_sha256(const uint8_t *msg, uint64_t len, uint8_t out[32]) {
+    if (!sha_ready) sha_init_constants();
+    uint32_t H[8];
+    memcpy(H, sha_h0, sizeof H);
+    uint64_t full = len / 64;
+    for (uint64_t b = 0; b < full; ++b) sha_compress(H, msg + 64 * b);
+    uint8_t tail[128];
+    memset(tail, 0, sizeof tail);
+    uint64_t rem = len - 64 * full;
+    if (rem) memcpy(tail, msg + 64 * full, rem);
+    tail[rem] = 0x80;
+    uint64_t tail_len = (rem + 1 + 8 <= 64) ? 64 : 128;
+    uint64_t bits = len * 8;
+    for (int i = 0; i < 8; ++i) tail[tail_len - 1 - i] = (uint8_t)(bits >> (8 * i));
+    sha_compress(H, tail);
+    if (tail_len == 128) sha_compress(H, tail + 64);
+    for (int i = 0; i < 8; ++i) {
+        out[4 * i] = (uint8_t)(H[i] >> 24);
+        out[4 * i + 1] = (uint8_t)(H[i] >> 16);
+        out[4 * i + 2] = (uint8_t)(H[i] >> 8);
+        out[4 * i + 3] = (uint8_t)H[i];
+    }
+}
+
+/* Sec. II-A, Algorithm 1 (partition, hash, fold): the frame's N bytes are
+ * split into n sub-frames f_i; H = h_1 xor ... xor h_n with h_i = SHA-256(f_i).
+ * Reading (partition not given by the paper): sub-frame i is the contiguous
+ * byte range [floor(i*N/n), floor((i+1)*N/n)) of the raw H x W x C buffer. */
+void oracle_frame_digest(const uint8_t *frame, uint64_t N, uint32_t n, uint8_t H[32]) {
+    memset(H, 0, 32);
+    for (uint32_t i = 0; i < n; ++i) {
+        uint64_t lo = (uint64_t)(((unsigned __int128)N * i) / n);
+        uint64_t hi = (uint64_t)(((unsigned __int128)N * (i + 1)) / n);
+        uint8_t hi_dig[32];
+        oracle_sha256(frame + lo, hi - lo, hi_dig);
+        for (int b = 0; b < 32; ++b) H[b] ^= hi_dig[b];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Key and initial-condition reconstruction (Sec. II-A, Fig. 1a).           */
+/* ------------------------------------------------------------------------ */
+
+static uint64_t le64(const uint8_t *p) {
+    uint64_t v = 0;
+    for (int i = 7; i >= 0; --i) v = (v << 8) | p[i];
+    return v;
+}
+
+/* The paper's key is the five doubles x0, y0, z0, w0, gamma (Sec. IV-A).
+ * Reading for a 256-bit key: k_m = little-endian uint64 of key bytes
+ * [8m, 8m+8); v_m = (k_m >> 11) * 2^-53 * u_m for m = x, y, z, w, and
+ * gamma = -1.52 + 1.46 * ((k0^k1^k2^k3) >> 11) * 2^-53, inside the
+ * hyperchaotic range -1.52 <= gamma <= -0.06 of Eq. (1). */
+void oracle_key_to_ic(const uint8_t key[32], const uint32_t u[4], double ic[5]) {
+    uint64_t k[4];
+    for (int m = 0; m < 4; ++m) k[m] = le64(key + 8 * m);
+    for (int m = 0; m < 4; ++m) {
+        double unit = (double)(k[m] >> 11) * 0x1p-53;
+        ic[m] = unit * (double)u[m];
+    }
+    double g = (double)((k[0] ^ k[1] ^ k[2] ^ k[3]) >> 11) * 0x1p-53;
+    ic[4] = -1.52 + 1.46 * g;
+}
+
+/* Sec. II-A, Fig. 1a: reconstruct one initial condition v from 8 bytes of H.
+ * (1) integer: the two least significant bytes of v's integer part XOR two
+ *     bytes of H, reduced mod the predefined upper bound u;
+ * (2) fraction: the six least significant bytes of v's fractional part XOR
+ *     six bytes of H;
+ * (3) combine the two.
+ * Readings: v is taken by magnitude; "the six least significant bytes of the
+ * fractional part" are the 48-bit fixed-point fraction floor(frac * 2^48);
+ * H bytes are consumed little-endian (hb[0..1] integer, hb[2..7] fraction);
+ * a non-finite v or |v| >= 2^52 contributes integer 0 and fraction 0. */
+double oracle_reconstruct(double v, const uint8_t hb[8], uint32_t u) {
+    double a = fabs(v);
+    uint64_t I = 0, F48 = 0;
+    if (a < 0x1p52) {           /* false for NaN too */
+        I = (uint64_t)a;         /* truncation toward zero */
+        double F = a - (double)I; /* exact: the fractional part of a double */
+        F48 = (uint64_t)(F * 0x1p48);
+    }
+    uint64_t hi16 = (uint64_t)hb[0] | ((uint64_t)hb[1] << 8);
+    uint64_t h48 = 0;
+    for (int i = 5; i >= 0; --i) h48 = (h48 << 8) | hb[2 + i];
+    uint64_t ip = ((I & 0xFFFFu) ^ hi16) % u;
+    double fp = (double)(F48 ^ h48) * 0x1p-48;
+    return (double)ip + fp;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Lorenz hyperchaotic system, Eq. (1), integrated by classical RK4.        */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. (1) with sigma = 10, rho = 28, beta = 8/3 (Sec. II-A). */
+static void lhcs_f(const double s[4], double gamma, double out[4]) {
+    const double sigma = 10.0, rho = 28.0, beta = 8.0 / 3.0;
+    double x = s[0], y = s[1], z = s[2], w = s[3];
+    out[0] = sigma * (y - x) + w;
+    out[1] = (rho * x - y) - x * z;
+    out[2] = x * y - beta * z;
+    out[3] = gamma * w - y * z;
+}
+
+/* Reading (the paper names no integrator or step): classical fourth-order
+ * Runge-Kutta with step h, every operation rounded to nearest in binary64,
+ * no contraction, in this order:
+ *   k1 = f(s); k2 = f(s + (h/2) k1); k3 = f(s + (h/2) k2); k4 = f(s + h k3);
+ *   s' = s + (h/6) * (((k1 + 2 k2) + 2 k3) + k4),
+ * with h/2 and h/6 each rounded once. */
+void oracle_rk4_step(double s[4], double gamma, double h) {
+    double hh = h / 2.0, h6 = h / 6.0;
+    double k1[4], k2[4], k3[4], k4[4], t[4];
+    lhcs_f(s, gamma, k1);
+    for (int v = 0; v < 4; ++v) t[v] = s[v] + hh * k1[v];
+    lhcs_f(t, gamma, k2);
+    for (int v = 0; v < 4; ++v) t[v] = s[v] + hh * k2[v];
+    lhcs_f(t, gamma, k3);
+    for (int v = 0; v < 4; ++v) t[v] = s[v] + h * k3[v];
+    lhcs_f(t, gamma, k4);
+    for (int v = 0; v < 4; ++v) {
+        double acc = ((k1[v] + 2.0 * k2[v]) + 2.0 * k3[v]) + k4[v];
+        s[v] = s[v] + h6 * acc;
+    }
+}
+
+/* Sec. II-A and Algorithm 1 (reconstruct, initialise LHCS_m, iterate):
+ * v = the stream's chaining state (the user's x0..w0 for the first frame,
+ * x_2n..w_2n of the previous frame's LHCS_m run afterwards).  Each of x, y,
+ * z, w is reconstructed with 8 bytes of H (x: H[0..7], y: H[8..15], ...),
+ * LHCS_m is iterated 2n times, IR[t] = state after step t+1 (t = 0..2n-1),
+ * and the new chaining state is the last iterate. */
+void oracle_master(const double v[4], const uint8_t H[32], const uint32_t u[4],
+                   double gamma, double h, uint32_t n, double *IR, double new_state[4]) {
+    double s[4];
+    for (int m = 0; m < 4; ++m) s[m] = oracle_reconstruct(v[m], H + 8 * m, u[m]);
+    for (uint32_t t = 0; t < 2 * n; ++t) {
+        oracle_rk4_step(s, gamma, h);
+        for (int m = 0; m < 4; ++m) IR[4 * t + m] = s[m];
+    }
+    for (int m = 0; m < 4; ++m) new_state[m] = s[m];
+}
+
+/* Sec. II-B and Algorithm 2 (data generation by worker i, 0-based here).
+ * Readings: LHCS_w^{i,1} starts from IR[2i], LHCS_w^{i,2} from IR[2i+1]; a
+ * worker iterates both, and each iterate (the state after a step) yields, for
+ * x, y, z, w in turn, the six low bytes of the 52-bit mantissa, least
+ * significant first.  The worker's byte stream S_i is the byte-wise XOR of
+ * the two systems' bytes (per-element XOR of 16-bit distances equals XOR of
+ * their bytes).  Worker i owns D[floor(i*L_D/n), floor((i+1)*L_D/n)) and
+ * B[floor(i*N/n), floor((i+1)*N/n)) with L_D = C*(h+w), N = h*w*C; it fills
+ * its D slice first, one 16-bit distance from every two bytes (little-endian),
+ * then its B slice, one byte per byte.  D layout: D[c*h + i] is the
+ * horizontal distance of row i, channel c; D[C*h + c*w + j] the vertical
+ * distance of pixel column j, channel c. */
+void oracle_keystream(const double *IR, uint32_t n, double gamma, double hstep,
+                      uint32_t hgt, uint32_t wid, uint32_t C, uint16_t *D, uint8_t *B) {
+    uint64_t LD = (uint64_t)C * (hgt + wid);
+    uint64_t LB = (uint64_t)hgt * wid * C;
+    for (uint32_t i = 0; i < n; ++i) {
+        uint64_t d0 = (uint64_t)(((unsigned __int128)LD * i) / n);
+        uint64_t d1 = (uint64_t)(((unsigned __int128)LD * (i + 1)) / n);
+        uint64_t b0 = (uint64_t)(((unsigned __int128)LB * i) / n);
+        uint64_t b1 = (uint64_t)(((unsigned __int128)LB * (i + 1)) / n);
+        uint64_t need = 2 * (d1 - d0) + (b1 - b0);
+        double s1[4], s2[4];
+        for (int m = 0; m < 4; ++m) { s1[m] = IR[4 * (2 * i) + m]; s2[m] = IR[4 * (2 * i + 1) + m]; }
+        uint8_t *S = (uint8_t *)malloc(need + 24);
+        uint64_t pos = 0;
+        while (pos < need) {
+            oracle_rk4_step(s1, gamma, hstep);
+            oracle_rk4_step(s2, gamma, hstep);
+            for (int m = 0; m < 4; ++m) {
+                uint64_t u1, u2;
+                memcpy(&u1, &s1[m], 8);
+                memcpy(&u2, &s2[m], 8);
+                for (int b = 0; b < 6; ++b)
+                    S[pos++] = (uint8_t)((u1 >> (8 * b)) ^ (u2 >> (8 * b)));
+            }
+        }
+        for (uint64_t m = 0; m < d1 - d0; ++m)
+            D[d0 + m] = (uint16_t)(S[2 * m] | ((uint16_t)S[2 * m + 1] << 8));
+        for (uint64_t m = 0; m < b1 - b0; ++m)
+            B[b0 + m] = S[2 * (d1 - d0) + m];
+        free(S);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Frame encryption on the expanded bit matrices (Sec. II-C, Algos 3-7).    */
+/* ------------------------------------------------------------------------ */
+
+/* One channel c at a time, with the paper's [8w x h] bit matrices stored as
+ * one byte per bit, row i of length 8w.  Algorithm 1 runs Algos 3..7 in turn
+ * and swaps M_t <- M_e after each; the swap is read as taking effect after
+ * Algos 4, 5 and 6 (after Algo 3 the extracted bits are already in M_t).
+ * Readings: d_h of (row i, channel c) is D[c*h + i]; d_v of (pixel column j,
+ * channel c) is D[C*h + c*w + j] -- Algo 5 gives one d_v per thread, shared by
+ * its eight bits, and Eq. (3)'s unbalanced parentheses are read as Algo 5's
+ * ((i + (d_v mod h)) mod h); the byte b of Algo 6 for thread (i, j, c) is
+ * B[(i*w + j)*C + c]. */
+void oracle_permute_encrypt(const uint8_t *F, uint32_t h, uint32_t w, uint32_t C,
+                            const uint16_t *D, const uint8_t *B, uint8_t *E) {
+    uint64_t W8 = 8ull * w;
+    uint8_t *Mt = (uint8_t *)malloc(h * W8);
+    uint8_t *Me = (uint8_t *)malloc(h * W8);
+    for (uint32_t c = 0; c < C; ++c) {
+        /* Algorithm 3: bit k of F_o^c(i,j), least significant first. */
+        for (uint32_t i = 0; i < h; ++i)
+            for (uint32_t j = 0; j < w; ++j) {
+                uint8_t p = F[((uint64_t)i * w + j) * C + c];
+                for (int k = 0; k < 8; ++k) {
+                    Mt[i * W8 + 8ull * j + k] = p & 1u;
+                    p >>= 1;
+                }
+            }
+        /* Algorithm 4: horizontal circular shift of row i by d_h. */
+        for (uint32_t i = 0; i < h; ++i) {
+            uint64_t dh = D[(uint64_t)c * h + i] % W8;
+            for (uint32_t j = 0; j < w; ++j)
+                for (int k = 0; k < 8; ++k)
+                    Me[i * W8 + (8ull * j + k + dh) % W8] = Mt[i * W8 + 8ull * j + k];
+        }
+        { uint8_t *t = Mt; Mt = Me; Me = t; }
+        /* Algorithm 5: vertical circular shift of pixel column j by d_v. */
+        for (uint32_t j = 0; j < w; ++j) {
+            uint64_t dv = D[(uint64_t)C * h + (uint64_t)c * w + j] % h;
+            for (uint32_t i = 0; i < h; ++i)
+                for (int k = 0; k < 8; ++k)
+                    Me[((i + dv) % h) * W8 + 8ull * j + k] = Mt[i * W8 + 8ull * j + k];
+        }
+        { uint8_t *t = Mt; Mt = Me; Me = t; }
+        /* Algorithm 6: XOR with the bits of b, least significant first. */
+        for (uint32_t i = 0; i < h; ++i)
+            for (uint32_t j = 0; j < w; ++j) {
+                uint8_t b = B[((uint64_t)i * w + j) * C + c];
+                for (int k = 0; k < 8; ++k) {
+                    Me[i * W8 + 8ull * j + k] = Mt[i * W8 + 8ull * j + k] ^ (b & 1u);
+                    b >>= 1;
+                }
+            }
+        { uint8_t *t = Mt; Mt = Me; Me = t; }
+        /* Algorithm 7: rebuild the byte, k from 7 down to 0, shifting left
+         * after every bit but the last. */
+        for (uint32_t i = 0; i < h; ++i)
+            for (uint32_t j = 0; j < w; ++j) {
+                uint32_t px = 0;
+                for (int k = 7; k >= 0; --k) {
+                    px |= Mt[i * W8 + 8ull * j + k];
+                    if (k != 0) px <<= 1;
+                }
+                E[((uint64_t)i * w + j) * C + c] = (uint8_t)px;
+            }
+    }
+    free(Mt);
+    free(Me);
+}
+
+/* Decryption: the paper gives it only as "the inverse transformation of the
+ * encryption procedure" (Sec. II-D).  On the same bit matrices, in reverse
+ * order: XOR with B (Algo 6 is an involution), undo the vertical shift
+ * (row (i + d_v) mod h goes back to row i), undo the horizontal shift (bit
+ * (p + d_h) mod 8w goes back to p), rebuild bytes. */
+void oracle_permute_decrypt(const uint8_t *E, uint32_t h, uint32_t w, uint32_t C,
+                            const uint16_t *D, const uint8_t *B, uint8_t *F) {
+    uint64_t W8 = 8ull * w;
+    uint8_t *Mt = (uint8_t *)malloc(h * W8);
+    uint8_t *Me = (uint8_t *)malloc(h * W8);
+    for (uint32_t c = 0; c < C; ++c) {
+        for (uint32_t i = 0; i < h; ++i)
+            for (uint32_t j = 0; j < w; ++j) {
+                uint8_t p = E[((uint64_t)i * w + j) * C + c];
+                for (int k = 0; k < 8; ++k) {
+                    Mt[i * W8 + 8ull * j + k] = p & 1u;
+                    p >>= 1;
+                }
+            }
+        for (uint32_t i = 0; i < h; ++i)
+            for (uint32_t j = 0; j < w; ++j) {
+                uint8_t b = B[((uint64_t)i * w + j) * C + c];
+                for (int k = 0; k < 8; ++k) {
+                    Me[i * W8 + 8ull * j + k] = Mt[i * W8 + 8ull * j + k] ^ (b & 1u);
+                    b >>= 1;
+                }
+            }
+        { uint8_t *t = Mt; Mt = Me; Me = t; }
+        for (uint32_t j = 0; j < w; ++j) {
+            uint64_t dv = D[(uint64_t)C * h + (uint64_t)c * w + j] % h;
+            for (uint32_t i = 0; i < h; ++i)
+                for (int k = 0; k < 8; ++k)
+                    Me[i * W8 + 8ull * j + k] = Mt[((i + dv) % h) * W8 + 8ull * j + k];
+        }
+        { uint8_t *t = Mt; Mt = Me; Me = t; }
+        for (uint32_t i = 0; i < h; ++i) {
+            uint64_t dh = D[(uint64_t)c * h + i] % W8;
+            for (uint64_t p = 0; p < W8; ++p)
+                Me[i * W8 + p] = Mt[i * W8 + (p + dh) % W8];
+        }
+        { uint8_t *t = Mt; Mt = Me; Me = t; }
+        for (uint32_t i = 0; i < h; ++i)
+            for (uint32_t j = 0; j < w; ++j) {
+                uint32_t px = 0;
+                for (int k = 7; k >= 0; --k) {
+                    px |= Mt[i * W8 + 8ull * j + k];
+                    if (k != 0) px <<= 1;
+                }
+                F[((uint64_t)i * w + j) * C + c] = (uint8_t)px;
+            }
+    }
+    free(Mt);
+    free(Me);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Whole frame, Algorithm 1: digest -> reconstruct -> LHCS_m -> workers ->  */
+/* confusion + XOR.  `state` is the stream's chaining state (in/out).       */
+/* ------------------------------------------------------------------------ */
+
+void oracle_frame_keystream(double state[4], double gamma, double hstep, uint32_t n,
+                            const uint32_t u[4], const uint8_t H[32], uint32_t h,
+                            uint32_t w, uint32_t C, uint16_t *D, uint8_t *B) {
+    double *IR = (double *)malloc(sizeof(double) * 8 * n);
+    double ns[4];
+    oracle_master(state, H, u, gamma, hstep, n, IR, ns);
+    oracle_keystream(IR, n, gamma, hstep, h, w, C, D, B);
+    for (int m = 0; m < 4; ++m) state[m] = ns[m];
+    free(IR);
+}
+
+void oracle_encrypt_frame(double state[4], double gamma, double hstep, uint32_t n,
+                          const uint32_t u[4], const uint8_t *F, uint32_t h, uint32_t w,
+                          uint32_t C, uint8_t *E, uint8_t H[32]) {
+    uint64_t N = (uint64_t)h * w * C;
+    uint64_t LD = (uint64_t)C * (h + w);
+    oracle_frame_digest(F, N, n, H);
+    uint16_t *D = (uint16_t *)malloc(sizeof(uint16_t) * (LD ? LD : 1));
+    uint8_t *B = (uint8_t *)malloc(N ? N : 1);
+    oracle_frame_keystream(state, gamma, hstep, n, u, H, h, w, C, D, B);
+    oracle_permute_encrypt(F, h, w, C, D, B, E);
+    free(D);
+    free(B);
+}
+
+void oracle_decrypt_frame(double state[4], double gamma, double hstep, uint32_t n,
+                          const uint32_t u[4], const uint8_t *E, uint32_t h, uint32_t w,
+                          uint32_t C, const uint8_t H[32], uint8_t *F) {
+    uint64_t N = (uint64_t)h * w * C;
+    uint64_t LD = (uint64_t)C * (h + w);
+    uint16_t *D = (uint16_t *)malloc(sizeof(uint16_t) * (LD ? LD : 1));
+    uint8_t *B = (uint8_t *)malloc(N ? N : 1);
+    oracle_frame_keystream(state, gamma, hstep, n, u, H, h, w, C, D, B);
+    oracle_permute_decrypt(E, h, w, C, D, B, F);
+    free(D);
+    free(B);
+}

@@ -1,0 +1,74 @@
+"""Pins for the worker data generation (Sec. II-B, Algorithm 2).
+
+* two identically seeded systems cancel: that worker's D and B slices are 0;
+* a system seeded at the origin (an equilibrium of Eq. (1)) contributes zero
+  bytes, so the worker's stream is the other system's mantissa bytes alone --
+  compared here with bytes taken by ``struct`` from the oracle's trajectory,
+  with the slice bounds recomputed in Python integers;
+* perturbing worker p's seeds changes only worker p's slices."""
+import struct
+
+import numpy as np
+import pytest
+
+import oracle
+import synth_inputs as si
+
+
+def _slices(L, n):
+    return [((L * i) // n, (L * (i + 1)) // n) for i in range(n)]
+
+
+def _ir(n, seed):
+    g = si.rng(seed)
+    return np.column_stack([g.uniform(0, 20, 2 * n), g.uniform(0, 20, 2 * n), g.uniform(0, 40, 2 * n), g.uniform(0, 20, 2 * n)])
+
+
+@pytest.mark.parametrize("h,w,C,n", [(8, 8, 3, 4), (5, 7, 1, 3), (30, 40, 3, 32), (1, 1, 3, 2)])
+def test_equal_seeds_cancel(h, w, C, n):
+    IR = _ir(n, 1)
+    p = n // 2
+    IR[2 * p + 1] = IR[2 * p]
+    D, B = oracle.keystream(IR, -1.0, h, w, C, n)
+    d0, d1 = _slices(C * (h + w), n)[p]
+    b0, b1 = _slices(h * w * C, n)[p]
+    assert np.all(D[d0:d1] == 0) and np.all(B[b0:b1] == 0)
+    others = np.concatenate([D[:d0], D[d1:]])
+    if others.size > 8:
+        assert np.any(others != 0)
+
+
+@pytest.mark.parametrize("h,w,C,n", [(8, 8, 3, 4), (5, 7, 1, 3), (20, 31, 3, 6), (2, 3, 4, 5)])
+def test_origin_partner_exposes_single_stream(h, w, C, n):
+    gamma = -0.9
+    IR = _ir(n, 2)
+    IR[1::2] = 0.0                      # second system of every worker at the origin
+    D, B = oracle.keystream(IR, gamma, h, w, C, n)
+    dsl, bsl = _slices(C * (h + w), n), _slices(h * w * C, n)
+    for i in range(n):
+        (d0, d1), (b0, b1) = dsl[i], bsl[i]
+        need = 2 * (d1 - d0) + (b1 - b0)
+        steps = -(-need // 24)
+        traj = oracle.rk4_trajectory(IR[2 * i], gamma, steps)
+        S = bytearray()
+        for t in range(steps):
+            for m in range(4):
+                S += struct.pack("<d", traj[t, m])[:6]
+        exp_D = [S[2 * k] | S[2 * k + 1] << 8 for k in range(d1 - d0)]
+        exp_B = list(S[2 * (d1 - d0): 2 * (d1 - d0) + (b1 - b0)])
+        assert list(D[d0:d1]) == exp_D
+        assert list(B[b0:b1]) == exp_B
+
+
+def test_workers_are_independent():
+    h, w, C, n = 12, 9, 3, 6
+    IR = _ir(n, 3)
+    D, B = oracle.keystream(IR, -1.2, h, w, C, n)
+    IR2 = IR.copy()
+    IR2[2 * 4, 1] += 1e-9
+    D2, B2 = oracle.keystream(IR2, -1.2, h, w, C, n)
+    dsl, bsl = _slices(C * (h + w), n), _slices(h * w * C, n)
+    for i in range(n):
+        (d0, d1), (b0, b1) = dsl[i], bsl[i]
+        same = np.array_equal(D[d0:d1], D2[d0:d1]) and np.array_equal(B[b0:b1], B2[b0:b1])
+        assert same == (i != 4)
