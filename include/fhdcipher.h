@@ -1,0 +1,164 @@
+/*
+ * fhdcipher -- C ABI of a GB300 (sm_103a) implementation of the
+ * diffusion-free bit-level video cipher of arXiv 2505.07158, "Real-Time
+ * Bit-Level Encryption of Full High-Definition Video Without Diffusion".
+ *
+ * Per frame (Algorithm 1 of the paper): the frame digest H (XOR of the
+ * SHA-256 digests of n sub-frames, Sec. II-A), the initial-condition
+ * reconstruction from H and the stream's chaining state, 2n iterations of the
+ * master Lorenz hyperchaotic system LHCS_m (Eq. (1)), 2n worker systems that
+ * expand the shift distances D and XOR bytes B (Sec. II-B, Algorithm 2), and
+ * one pass of bit-level horizontal + vertical circular shifts and XOR
+ * (Sec. II-C, Algos 3-7); decryption runs the exact inverse.
+ *
+ * Conventions for every entry point:
+ *  - Frames are H x W x C uint8, C-contiguous, channel fastest (HWC), with
+ *    1 <= C <= 4, 1 <= H, W <= 32768.  Frame, digest, D and B pointers are
+ *    DEVICE pointers owned by the caller; the library never frees them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued asynchronously; a return of FHD_OK means the
+ *    arguments were accepted and the work enqueued, not that it finished.
+ *  - Errors: 0 on success, a negative FHD_ERR_* code otherwise; nothing is
+ *    enqueued when an argument check fails.  cipher_last_error() gives a
+ *    message.  No call ever falls back to the CPU.
+ *  - One handle is used from one host thread and one CUDA stream at a time:
+ *    its scratch buffers are reused by every call.
+ */
+#ifndef FHDCIPHER_H
+#define FHDCIPHER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    FHD_OK = 0,
+    FHD_ERR_INVALID_ARG = -1, /* null pointer, zero or oversized dimension, bad parameter */
+    FHD_ERR_OOM = -2,         /* device or pinned allocation failed */
+    FHD_ERR_BAD_STREAM = -3,  /* unknown or closed stream id */
+    FHD_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+    FHD_ERR_CUDA = -6,        /* a CUDA runtime call failed */
+    FHD_ERR_STATE = -7,       /* device status word reports a failed kernel check */
+    FHD_ERR_TOO_LARGE = -8    /* request exceeds a documented maximum */
+};
+
+#define FHD_MAX_DIM 32768u
+#define FHD_MAX_WORKERS 1024u
+#define FHD_STATE_BYTES 48u /* x, y, z, w, gamma (binary64) + frame counter (uint64) */
+
+typedef struct fhd_cipher fhd_cipher;
+
+/* Protocol parameters; both ends of a channel must use the same values
+ * (the paper requires the same worker count n on sender and receiver,
+ * Sec. V).  A zero field takes its default. */
+typedef struct {
+    uint32_t n_workers;  /* n: sub-frames per frame and worker pairs; default 32 (Tab. speedEvaluation) */
+    double rk4_h;        /* step of the RK4 integration of Eq. (1); default 0.001 */
+    uint32_t u_bound[4]; /* reconstruction upper bounds u_x, u_y, u_z, u_w; default 20, 20, 40, 20 */
+} fhd_params;
+
+/* One frame of a batch.  `digest` is written by encrypt_frames (the 32-byte
+ * H the receiver needs, Sec. V) and read by decrypt_frames. */
+typedef struct {
+    uint32_t stream_id;
+    uint32_t height, width, channels;
+    const uint8_t *src; /* device, height*width*channels bytes */
+    uint8_t *dst;       /* device, same size; must not overlap src */
+    uint8_t *digest;    /* device, 32 bytes */
+} fhd_frame;
+
+/* Create a cipher from a 256-bit key.  The paper's key is the five doubles
+ * x0, y0, z0, w0, gamma (Sec. IV-A); the 32 key bytes map to them as
+ * k_m = little-endian uint64 of bytes [8m, 8m+8), v_m = (k_m >> 11) 2^-53 u_m,
+ * gamma = -1.52 + 1.46 ((k0^k1^k2^k3) >> 11) 2^-53.  `params` may be NULL.
+ * Selects the current CUDA device.  On success *out owns device memory. */
+int cipher_init(const uint8_t key[32], const fhd_params *params, fhd_cipher **out);
+
+/* Create a cipher from the paper's own key (x0, y0, z0, w0, gamma), Sec. II-A. */
+int cipher_init_raw(double x0, double y0, double z0, double w0, double gamma,
+                    const fhd_params *params, fhd_cipher **out);
+
+/* Open a video stream whose chaining state starts at the cipher's key
+ * (Algorithm 1: the first frame reconstructs from the user inputs). */
+int cipher_open_stream(fhd_cipher *c, uint32_t *stream_id);
+
+/* Open a stream with its own 256-bit key (same mapping as cipher_init). */
+int cipher_open_stream_key(fhd_cipher *c, const uint8_t key[32], uint32_t *stream_id);
+
+/* Close a stream; its id may be reused by a later open. */
+int cipher_close_stream(fhd_cipher *c, uint32_t stream_id);
+
+/* Encrypt `count` frames (Algorithm 1 per frame).  Frames of one stream are
+ * processed in array order and each advances that stream's chaining state
+ * (Sec. II-A: the next frame reconstructs from x_2n..w_2n of this one).
+ * Frames of different streams and sizes may be mixed in one call; they run
+ * in one batched pass.  count == 0 is a no-op. */
+int encrypt_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream);
+
+/* Decrypt `count` frames: the inverse of encrypt_frames given each frame's
+ * transmitted digest (read from frames[i].digest). */
+int decrypt_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream);
+
+/* Copy a stream's chaining state (FHD_STATE_BYTES bytes) to host memory
+ * after synchronising the handle's last CUDA stream; for exact resume. */
+int cipher_export_state(fhd_cipher *c, uint32_t stream_id, void *buf, size_t len);
+
+/* Overwrite a stream's chaining state from FHD_STATE_BYTES bytes of host memory. */
+int cipher_import_state(fhd_cipher *c, uint32_t stream_id, const void *buf, size_t len);
+
+/* Synchronise `stream`, then read and clear the device status word.
+ * Returns FHD_OK, FHD_ERR_STATE or FHD_ERR_TIMEOUT, or FHD_ERR_CUDA. */
+int cipher_sync_status(fhd_cipher *c, void *stream);
+
+/* Last error message of this handle (never NULL; valid until the next call). */
+const char *cipher_last_error(const fhd_cipher *c);
+
+/* Free the handle and its device memory (synchronises the device first). */
+void cipher_destroy(fhd_cipher *c);
+
+/* ---- The hot path's steps, one call each (device pointers, async). ---- */
+
+/* Sec. II-A: digest[32] = XOR over i < n of SHA-256 of bytes
+ * [floor(i*nbytes/n), floor((i+1)*nbytes/n)) of `data` (FIPS 180-4).
+ * nbytes may be 0.  `count` independent buffers of equal size laid end to end
+ * (data + k*nbytes -> digest + 32k) are hashed in one launch. */
+int fhd_frame_digest(const uint8_t *data, uint64_t nbytes, uint32_t n, uint32_t count,
+                     uint8_t *digest, void *stream);
+
+/* Sec. II-A and Algorithm 1: reconstruct x, y, z, w from state[0..3] and the
+ * 32-byte digest H, iterate LHCS_m 2n times with gamma = state[4]; write the
+ * iterates to IR (2n x 4 binary64, row t = state after step t+1) and the last
+ * iterate back into state[0..3].  `state` (5 doubles), `H` and `IR` are
+ * device pointers. */
+int fhd_master(double *state, const uint8_t *H, const fhd_params *params, double *IR, void *stream);
+
+/* Sec. II-B and Algorithm 2: from IR (2n x 4 binary64, device), run the n
+ * worker pairs and fill D (C*(h+w) uint16: D[c*h+i] row shifts, then
+ * D[C*h+c*w+j] pixel-column shifts) and B (h*w*C bytes, frame order). */
+int fhd_keystream(const double *IR, double gamma, const fhd_params *params, uint32_t height,
+                  uint32_t width, uint32_t channels, uint16_t *D, uint8_t *B, void *stream);
+
+/* Sec. II-C, Algos 3-7 fused: dst = XOR(B, vertical shift(horizontal bit
+ * shift(src))) with the distances in D, one frame, device pointers. */
+int fhd_permute_encrypt(const uint8_t *src, uint8_t *dst, uint32_t height, uint32_t width,
+                        uint32_t channels, const uint16_t *D, const uint8_t *B, void *stream);
+
+/* Exact inverse of fhd_permute_encrypt. */
+int fhd_permute_decrypt(const uint8_t *src, uint8_t *dst, uint32_t height, uint32_t width,
+                        uint32_t channels, const uint16_t *D, const uint8_t *B, void *stream);
+
+/* Strip width (pixels) the permutation kernels use for this shape, and the
+ * override hook of the autotuner: 0 restores the built-in choice. */
+uint32_t fhd_strip_width(uint32_t height, uint32_t width, uint32_t channels);
+int fhd_set_strip_width(uint32_t height, uint32_t width, uint32_t channels, uint32_t P);
+
+/* Library version string. */
+const char *fhd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FHDCIPHER_H */

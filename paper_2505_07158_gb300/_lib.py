@@ -1,0 +1,306 @@
+"""ctypes binding of ``libfhdcipher.so`` (argument marshalling only).
+
+Every entry point of ``include/fhdcipher.h`` is exposed under the same name.
+Tensors are CUDA ``torch.uint8`` (frames, digests, B), ``torch.uint16``-sized
+``torch.int16`` (D) or ``torch.float64`` (states, iterates); their device
+pointers are handed to the library, which enqueues its kernels on the current
+torch CUDA stream (or the stream given).  There is no CPU path: if the
+library cannot be loaded the import of this module raises."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Iterable, Sequence
+
+import torch
+
+from . import build as _build
+
+FHD_OK = 0
+FHD_ERR_INVALID_ARG = -1
+FHD_ERR_OOM = -2
+FHD_ERR_BAD_STREAM = -3
+FHD_ERR_TIMEOUT = -5
+FHD_ERR_CUDA = -6
+FHD_ERR_STATE = -7
+FHD_ERR_TOO_LARGE = -8
+FHD_STATE_BYTES = 48
+
+# Every symbol the header declares (checked by the CPU test-suite).
+EXPORTS = (
+    "cipher_init", "cipher_init_raw", "cipher_open_stream", "cipher_open_stream_key", "cipher_close_stream",
+    "encrypt_frames", "decrypt_frames", "cipher_export_state", "cipher_import_state", "cipher_sync_status",
+    "cipher_last_error", "cipher_destroy", "fhd_frame_digest", "fhd_master", "fhd_keystream",
+    "fhd_permute_encrypt", "fhd_permute_decrypt", "fhd_strip_width", "fhd_set_strip_width", "fhd_version",
+)
+
+
+class FhdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fhdcipher error {code}: {msg}")
+        self.code = code
+
+
+class FhdParams(ctypes.Structure):
+    _fields_ = [("n_workers", ctypes.c_uint32), ("rk4_h", ctypes.c_double), ("u_bound", ctypes.c_uint32 * 4)]
+
+
+class FhdFrame(ctypes.Structure):
+    _fields_ = [("stream_id", ctypes.c_uint32), ("height", ctypes.c_uint32), ("width", ctypes.c_uint32),
+                ("channels", ctypes.c_uint32), ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p),
+                ("digest", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load (building first if needed) the in-tree library."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(path or _build.build())
+        P, u32, u64, dbl, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double, ctypes.c_int
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        sig = {
+            "cipher_init": (i32, [P, P, PP]),
+            "cipher_init_raw": (i32, [dbl, dbl, dbl, dbl, dbl, P, PP]),
+            "cipher_open_stream": (i32, [P, ctypes.POINTER(u32)]),
+            "cipher_open_stream_key": (i32, [P, P, ctypes.POINTER(u32)]),
+            "cipher_close_stream": (i32, [P, u32]),
+            "encrypt_frames": (i32, [P, u32, P, P]),
+            "decrypt_frames": (i32, [P, u32, P, P]),
+            "cipher_export_state": (i32, [P, u32, P, ctypes.c_size_t]),
+            "cipher_import_state": (i32, [P, u32, P, ctypes.c_size_t]),
+            "cipher_sync_status": (i32, [P, P]),
+            "cipher_last_error": (ctypes.c_char_p, [P]),
+            "cipher_destroy": (None, [P]),
+            "fhd_frame_digest": (i32, [P, u64, u32, u32, P, P]),
+            "fhd_master": (i32, [P, P, P, P, P]),
+            "fhd_keystream": (i32, [P, dbl, P, u32, u32, u32, P, P, P]),
+            "fhd_permute_encrypt": (i32, [P, P, u32, u32, u32, P, P, P]),
+            "fhd_permute_decrypt": (i32, [P, P, u32, u32, u32, P, P, P]),
+            "fhd_strip_width": (u32, [u32, u32, u32]),
+            "fhd_set_strip_width": (i32, [u32, u32, u32, u32]),
+            "fhd_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _check(code: int, handle=None):
+    if code != FHD_OK:
+        msg = load().cipher_last_error(handle).decode(errors="replace")
+        raise FhdError(code, msg)
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _params(n_workers=32, rk4_h=0.001, u_bound=(20, 20, 40, 20)) -> FhdParams:
+    p = FhdParams()
+    p.n_workers = n_workers
+    p.rk4_h = rk4_h
+    for m in range(4):
+        p.u_bound[m] = u_bound[m]
+    return p
+
+
+def _frame_tensor(t: torch.Tensor, what: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.uint8 or not t.is_contiguous():
+        raise ValueError(f"{what} must be a contiguous CUDA uint8 tensor")
+    if t.dim() != 3:
+        raise ValueError(f"{what} must have shape (height, width, channels)")
+    return t
+
+
+def _digest_tensor(t: torch.Tensor):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.uint8 or not t.is_contiguous() or t.numel() != 32:
+        raise ValueError("digest must be a contiguous CUDA uint8 tensor of 32 bytes")
+    return t
+
+
+class Cipher:
+    """A cipher handle: key, protocol parameters and device-resident streams."""
+
+    def __init__(self, key: bytes | None = None, ic: Sequence[float] | None = None, n_workers: int = 32,
+                 rk4_h: float = 0.001, u_bound=(20, 20, 40, 20)):
+        lib = load()
+        self.params = _params(n_workers, rk4_h, u_bound)
+        self.n_workers = n_workers
+        h = ctypes.c_void_p()
+        if ic is not None:
+            x0, y0, z0, w0, g = (float(v) for v in ic)
+            code = lib.cipher_init_raw(x0, y0, z0, w0, g, ctypes.byref(self.params), ctypes.byref(h))
+        else:
+            if key is None or len(key) != 32:
+                raise ValueError("key must be 32 bytes (or pass ic=)")
+            kb = (ctypes.c_uint8 * 32).from_buffer_copy(bytes(key))
+            code = lib.cipher_init(kb, ctypes.byref(self.params), ctypes.byref(h))
+        _check(code)
+        self._h = h
+
+    def _handle(self):
+        if self._h is None:
+            raise RuntimeError("cipher closed")
+        return self._h
+
+    def open_stream(self, key: bytes | None = None) -> int:
+        sid = ctypes.c_uint32()
+        if key is None:
+            code = load().cipher_open_stream(self._handle(), ctypes.byref(sid))
+        else:
+            kb = (ctypes.c_uint8 * 32).from_buffer_copy(bytes(key))
+            code = load().cipher_open_stream_key(self._handle(), kb, ctypes.byref(sid))
+        _check(code, self._h)
+        return sid.value
+
+    def close_stream(self, sid: int):
+        _check(load().cipher_close_stream(self._handle(), sid), self._h)
+
+    @staticmethod
+    def _frames(items) -> ctypes.Array:
+        items = list(items)
+        arr = (FhdFrame * max(len(items), 1))()
+        for k, (sid, src, dst, digest) in enumerate(items):
+            _frame_tensor(src, "src")
+            _frame_tensor(dst, "dst")
+            _digest_tensor(digest)
+            if src.shape != dst.shape:
+                raise ValueError("src and dst shapes differ")
+            h, w, c = src.shape
+            arr[k] = FhdFrame(sid, h, w, c, src.data_ptr(), dst.data_ptr(), digest.data_ptr())
+        return arr, len(items)
+
+    def encrypt_frames(self, items: Iterable, stream=None):
+        """items: (stream_id, src, dst, digest) tuples; digest (32 B) is written."""
+        arr, n = self._frames(items)
+        _check(load().encrypt_frames(self._handle(), n, arr, _stream_ptr(stream)), self._h)
+
+    def decrypt_frames(self, items: Iterable, stream=None):
+        """items: (stream_id, src, dst, digest) tuples; digest (32 B) is read."""
+        arr, n = self._frames(items)
+        _check(load().decrypt_frames(self._handle(), n, arr, _stream_ptr(stream)), self._h)
+
+    def encrypt(self, sid: int, src: torch.Tensor, stream=None):
+        dst = torch.empty_like(src)
+        dig = torch.empty(32, dtype=torch.uint8, device=src.device)
+        self.encrypt_frames([(sid, src, dst, dig)], stream)
+        return dst, dig
+
+    def decrypt(self, sid: int, src: torch.Tensor, digest: torch.Tensor, stream=None):
+        dst = torch.empty_like(src)
+        self.decrypt_frames([(sid, src, dst, digest)], stream)
+        return dst
+
+    def export_state(self, sid: int) -> bytes:
+        buf = (ctypes.c_uint8 * FHD_STATE_BYTES)()
+        _check(load().cipher_export_state(self._handle(), sid, buf, FHD_STATE_BYTES), self._h)
+        return bytes(buf)
+
+    def import_state(self, sid: int, data: bytes):
+        buf = (ctypes.c_uint8 * FHD_STATE_BYTES).from_buffer_copy(bytes(data))
+        _check(load().cipher_import_state(self._handle(), sid, buf, FHD_STATE_BYTES), self._h)
+
+    def sync_status(self, stream=None):
+        _check(load().cipher_sync_status(self._handle(), _stream_ptr(stream)), self._h)
+
+    def last_error(self) -> str:
+        return load().cipher_last_error(self._h).decode(errors="replace")
+
+    def close(self):
+        if self._h is not None:
+            load().cipher_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- one call per step of the hot path ----
+
+def fhd_frame_digest(data: torch.Tensor, n: int = 32, count: int = 1, out: torch.Tensor | None = None, stream=None):
+    """XOR of sub-frame SHA-256 digests of ``count`` equal buffers laid end to end."""
+    if not data.is_cuda or data.dtype != torch.uint8 or not data.is_contiguous():
+        raise ValueError("data must be a contiguous CUDA uint8 tensor")
+    if data.numel() % max(count, 1):
+        raise ValueError("data size must be a multiple of count")
+    nbytes = data.numel() // max(count, 1)
+    if out is None:
+        out = torch.empty((count, 32), dtype=torch.uint8, device=data.device)
+    ptr = data.data_ptr() if data.numel() else 0
+    _check(load().fhd_frame_digest(ctypes.c_void_p(ptr), nbytes, n, count, ctypes.c_void_p(out.data_ptr()),
+                                   _stream_ptr(stream)))
+    return out
+
+
+def fhd_master(state5: torch.Tensor, H: torch.Tensor, n_workers=32, rk4_h=0.001, u_bound=(20, 20, 40, 20),
+               IR: torch.Tensor | None = None, stream=None):
+    """Reconstruct + 2n LHCS_m steps; ``state5`` (float64 x5, CUDA) is updated in place."""
+    assert state5.is_cuda and state5.dtype == torch.float64 and state5.numel() == 5
+    if IR is None:
+        IR = torch.empty((2 * n_workers, 4), dtype=torch.float64, device=state5.device)
+    p = _params(n_workers, rk4_h, u_bound)
+    _check(load().fhd_master(ctypes.c_void_p(state5.data_ptr()), ctypes.c_void_p(H.data_ptr()), ctypes.byref(p),
+                             ctypes.c_void_p(IR.data_ptr()), _stream_ptr(stream)))
+    return IR
+
+
+def fhd_keystream(IR: torch.Tensor, gamma: float, height: int, width: int, channels: int, n_workers=32,
+                  rk4_h=0.001, stream=None):
+    """Worker pairs -> (D int16[C*(h+w)] holding uint16 bits, B uint8[h*w*C])."""
+    assert IR.is_cuda and IR.dtype == torch.float64 and IR.is_contiguous()
+    D = torch.empty(channels * (height + width), dtype=torch.int16, device=IR.device)
+    B = torch.empty(height * width * channels, dtype=torch.uint8, device=IR.device)
+    p = _params(n_workers, rk4_h)
+    _check(load().fhd_keystream(ctypes.c_void_p(IR.data_ptr()), float(gamma), ctypes.byref(p), height, width,
+                                channels, ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                                _stream_ptr(stream)))
+    return D, B
+
+
+def _permute(fn, src, D, B, out, stream):
+    _frame_tensor(src, "src")
+    h, w, c = src.shape
+    if out is None:
+        out = torch.empty_like(src)
+    _check(fn(ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(out.data_ptr()), h, w, c,
+              ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(B.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def fhd_permute_encrypt(src: torch.Tensor, D: torch.Tensor, B: torch.Tensor, out=None, stream=None):
+    return _permute(load().fhd_permute_encrypt, src, D, B, out, stream)
+
+
+def fhd_permute_decrypt(src: torch.Tensor, D: torch.Tensor, B: torch.Tensor, out=None, stream=None):
+    return _permute(load().fhd_permute_decrypt, src, D, B, out, stream)
+
+
+def fhd_strip_width(height: int, width: int, channels: int) -> int:
+    return int(load().fhd_strip_width(height, width, channels))
+
+
+def fhd_set_strip_width(height: int, width: int, channels: int, P: int):
+    _check(load().fhd_set_strip_width(height, width, channels, P))
+
+
+def fhd_version() -> str:
+    return load().fhd_version().decode()

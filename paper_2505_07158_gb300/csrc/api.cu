@@ -1,0 +1,480 @@
+// Host side of the C ABI declared in include/fhdcipher.h: argument checks,
+// per-stream chaining state, scratch management and the four launches of a
+// batch (K1 sub-frame SHA-256, K2a master LHCS, K2b worker LHCS pairs,
+// K3/K4 fused permutation).  Every step of the cipher runs in the kernels;
+// the host only validates, lays out descriptors and enqueues.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using fhd::Batch;
+using fhd::FrameDesc;
+using fhd::StreamState;
+
+struct fhd_cipher {
+    int device = 0;
+    uint32_t n = 32;
+    double h = 0.001;
+    uint32_t u[4] = {20, 20, 40, 20};
+    double key_ic[5] = {0, 0, 0, 0, 0};
+    std::vector<StreamState> mirror;   // host copy of gamma (and initial state)
+    std::vector<uint8_t> open;
+    StreamState *d_states = nullptr;
+    size_t cap_states = 0;
+    unsigned *d_status = nullptr;
+    uint8_t *d_scratch = nullptr;
+    size_t scratch_cap = 0;
+    cudaStream_t last_stream = nullptr;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_err;   // last error of the handle-less entry points
+
+int fail(fhd_cipher *c, int code, const std::string &msg) {
+    if (c) c->err = msg; else g_err = msg;
+    return code;
+}
+
+int cuda_fail(fhd_cipher *c, cudaError_t e, const char *what) {
+    return fail(c, FHD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool resolve_params(const fhd_params *p, uint32_t &n, double &h, uint32_t u[4], std::string &why) {
+    n = 32;
+    h = 0.001;
+    const uint32_t du[4] = {20, 20, 40, 20};
+    for (int m = 0; m < 4; ++m) u[m] = du[m];
+    if (!p) return true;
+    if (p->n_workers) n = p->n_workers;
+    if (p->rk4_h != 0.0) h = p->rk4_h;
+    for (int m = 0; m < 4; ++m)
+        if (p->u_bound[m]) u[m] = p->u_bound[m];
+    if (n > FHD_MAX_WORKERS) { why = "n_workers exceeds FHD_MAX_WORKERS"; return false; }
+    if (!(h > 0.0) || !(h < 1.0)) { why = "rk4_h must be in (0, 1)"; return false; }
+    for (int m = 0; m < 4; ++m)
+        if (u[m] > 65536u) { why = "u_bound entries must be <= 65536"; return false; }
+    return true;
+}
+
+// 256-bit key -> x0, y0, z0, w0, gamma (the mapping documented in the header).
+// Built with -ffp-contract=off: each product and sum is rounded on its own.
+void key_to_ic(const uint8_t key[32], const uint32_t u[4], double ic[5]) {
+    uint64_t k[4];
+    for (int m = 0; m < 4; ++m) {
+        uint64_t v = 0;
+        for (int i = 7; i >= 0; --i) v = (v << 8) | key[8 * m + i];
+        k[m] = v;
+    }
+    for (int m = 0; m < 4; ++m) {
+        volatile double unit = (double)(k[m] >> 11) * 0x1p-53;
+        ic[m] = unit * (double)u[m];
+    }
+    volatile double g = (double)((k[0] ^ k[1] ^ k[2] ^ k[3]) >> 11) * 0x1p-53;
+    volatile double prod = 1.46 * g;
+    ic[4] = -1.52 + prod;
+}
+
+uint64_t align16(uint64_t x) { return (x + 15) & ~15ull; }
+
+std::mutex g_prep_mu;
+bool g_prepared[64] = {};
+
+cudaError_t prepare_device() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_prep_mu);
+    if (dev >= 0 && dev < 64 && g_prepared[dev]) return cudaSuccess;
+    e = fhd::permute_prepare();
+    if (e == cudaSuccess && dev >= 0 && dev < 64) g_prepared[dev] = true;
+    return e;
+}
+
+bool check_dims(uint32_t h, uint32_t w, uint32_t C, std::string &why) {
+    if (h == 0 || w == 0 || C == 0) { why = "frame dimensions must be non-zero"; return false; }
+    if (C > 4) { why = "channels must be 1..4"; return false; }
+    if (h > 16384u || w > FHD_MAX_DIM) { why = "frame exceeds 16384 rows or 32768 columns"; return false; }
+    if (fhd::strip_width(h, w, C) == 0) { why = "frame too tall for the shared-memory strip"; return false; }
+    return true;
+}
+
+int init_common(const double ic[5], uint32_t n, double h, const uint32_t u[4], fhd_cipher **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    e = prepare_device();
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("prepare: ") + cudaGetErrorString(e));
+    fhd_cipher *c = new fhd_cipher();
+    c->device = dev;
+    c->n = n;
+    c->h = h;
+    for (int m = 0; m < 4; ++m) c->u[m] = u[m];
+    for (int m = 0; m < 5; ++m) c->key_ic[m] = ic[m];
+    e = cudaMalloc(&c->d_status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(unsigned));
+    if (e != cudaSuccess) {
+        cudaFree(c->d_status);
+        delete c;
+        return fail(nullptr, FHD_ERR_OOM, std::string("cudaMalloc status: ") + cudaGetErrorString(e));
+    }
+    *out = c;
+    return FHD_OK;
+}
+
+int open_with_ic(fhd_cipher *c, const double ic[5], uint32_t *id) {
+    if (!c || !id) return fail(c, FHD_ERR_INVALID_ARG, "null argument");
+    uint32_t slot = 0;
+    while (slot < c->open.size() && c->open[slot]) ++slot;
+    if (slot >= c->cap_states) {
+        size_t cap = c->cap_states ? 2 * c->cap_states : 64;
+        while (cap <= slot) cap *= 2;
+        StreamState *d = nullptr;
+        cudaError_t e = cudaMalloc(&d, cap * sizeof(StreamState));
+        if (e != cudaSuccess) return fail(c, FHD_ERR_OOM, std::string("cudaMalloc states: ") + cudaGetErrorString(e));
+        if (c->d_states) {
+            if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+            cudaDeviceSynchronize();
+            e = cudaMemcpy(d, c->d_states, c->cap_states * sizeof(StreamState), cudaMemcpyDeviceToDevice);
+            cudaFree(c->d_states);
+            if (e != cudaSuccess) { cudaFree(d); c->d_states = nullptr; c->cap_states = 0;
+                return cuda_fail(c, e, "copy states"); }
+        }
+        c->d_states = d;
+        c->cap_states = cap;
+    }
+    if (slot >= c->open.size()) {
+        c->open.resize(slot + 1, 0);
+        c->mirror.resize(slot + 1);
+    }
+    StreamState st{};
+    for (int m = 0; m < 4; ++m) st.v[m] = ic[m];
+    st.gamma = ic[4];
+    st.frames = 0;
+    if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+    cudaError_t e = cudaMemcpy(c->d_states + slot, &st, sizeof st, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "upload state");
+    c->mirror[slot] = st;
+    c->open[slot] = 1;
+    *id = slot;
+    return FHD_OK;
+}
+
+int ensure_scratch(fhd_cipher *c, size_t need) {
+    if (need <= c->scratch_cap) return FHD_OK;
+    if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+    cudaDeviceSynchronize();
+    cudaFree(c->d_scratch);
+    c->d_scratch = nullptr;
+    c->scratch_cap = 0;
+    size_t cap = need + need / 8;
+    cudaError_t e = cudaMalloc(&c->d_scratch, cap);
+    if (e != cudaSuccess) {
+        c->d_scratch = nullptr;
+        return fail(c, FHD_ERR_OOM, std::string("cudaMalloc scratch: ") + cudaGetErrorString(e));
+    }
+    c->scratch_cap = cap;
+    return FHD_OK;
+}
+
+// Per-frame scratch: n sub-frame digests, 2n LHCS_m iterates, D, B.
+uint64_t frame_scratch(uint32_t n, uint32_t h, uint32_t w, uint32_t C) {
+    return align16(32ull * n) + align16(64ull * n) + align16(2ull * C * (h + w)) + align16((uint64_t)h * w * C);
+}
+
+int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream, bool encrypt) {
+    if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
+    if (count == 0) return FHD_OK;
+    if (!frames) return fail(c, FHD_ERR_INVALID_ARG, "null frames");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (uint32_t k = 0; k < count; ++k) {
+        const fhd_frame &f = frames[k];
+        std::string why;
+        if (!f.src || !f.dst || !f.digest) return fail(c, FHD_ERR_INVALID_ARG, "frame " + std::to_string(k) + ": null pointer");
+        if (!check_dims(f.height, f.width, f.channels, why)) return fail(c, FHD_ERR_INVALID_ARG, "frame " + std::to_string(k) + ": " + why);
+        if (f.stream_id >= c->open.size() || !c->open[f.stream_id])
+            return fail(c, FHD_ERR_BAD_STREAM, "frame " + std::to_string(k) + ": stream not open");
+        uint64_t N = (uint64_t)f.height * f.width * f.channels;
+        const uint8_t *s0 = f.src, *d0 = f.dst;
+        if (s0 < d0 + N && d0 < s0 + N) return fail(c, FHD_ERR_INVALID_ARG, "frame " + std::to_string(k) + ": src and dst overlap");
+    }
+    cudaError_t e = prepare_device();
+    if (e != cudaSuccess) return cuda_fail(c, e, "prepare");
+    static thread_local Batch b;   // ~12 KB: kept off the stack
+    for (uint32_t base = 0; base < count; base += fhd::kMaxBatch) {
+        uint32_t m = count - base < (uint32_t)fhd::kMaxBatch ? count - base : (uint32_t)fhd::kMaxBatch;
+        std::memset(&b, 0, sizeof b);
+        b.count = m;
+        b.n = c->n;
+        b.hstep = c->h;
+        b.hhalf = c->h / 2.0;
+        b.hsixth = c->h / 6.0;
+        for (int q = 0; q < 4; ++q) b.u[q] = c->u[q];
+        uint64_t need = 0;
+        for (uint32_t k = 0; k < m; ++k) {
+            const fhd_frame &f = frames[base + k];
+            need += frame_scratch(c->n, f.height, f.width, f.channels);
+        }
+        int rc = ensure_scratch(c, need);
+        if (rc != FHD_OK) return rc;
+        uint8_t *p = c->d_scratch;
+        uint32_t ctas = 0;
+        for (uint32_t k = 0; k < m; ++k) {
+            const fhd_frame &f = frames[base + k];
+            FrameDesc &d = b.f[k];
+            d.src = f.src;
+            d.dst = f.dst;
+            d.digest = f.digest;
+            d.h = f.height;
+            d.w = f.width;
+            d.C = f.channels;
+            d.N = (uint64_t)f.height * f.width * f.channels;
+            d.slot = f.stream_id;
+            d.gamma = c->mirror[f.stream_id].gamma;
+            d.part = p; p += align16(32ull * c->n);
+            d.IR = reinterpret_cast<double *>(p); p += align16(64ull * c->n);
+            d.D = reinterpret_cast<uint16_t *>(p); p += align16(2ull * d.C * (d.h + d.w));
+            d.B = p; p += align16(d.N);
+            d.P = fhd::strip_width(d.h, d.w, d.C);
+            d.cta0 = ctas;
+            ctas += fhd::permute_strips(d.w, d.P);
+        }
+        b.perm_ctas = ctas;
+        // Group frames by stream (stable): each master CTA walks one stream in order.
+        std::vector<uint32_t> seen;
+        uint32_t pos = 0;
+        for (uint32_t k = 0; k < m; ++k) {
+            uint32_t sid = b.f[k].slot;
+            bool dup = false;
+            for (uint32_t x : seen) if (x == sid) { dup = true; break; }
+            if (dup) continue;
+            seen.push_back(sid);
+            b.group_begin[b.groups++] = (uint16_t)pos;
+            for (uint32_t k2 = k; k2 < m; ++k2)
+                if (b.f[k2].slot == sid) b.order[pos++] = (uint16_t)k2;
+        }
+        b.group_begin[b.groups] = (uint16_t)pos;
+        if (encrypt && (e = fhd::launch_sha_subframes(b, s)) != cudaSuccess) return cuda_fail(c, e, "sha launch");
+        if ((e = fhd::launch_master(b, c->d_states, encrypt, c->d_status, s)) != cudaSuccess) return cuda_fail(c, e, "master launch");
+        if ((e = fhd::launch_keystream(b, s)) != cudaSuccess) return cuda_fail(c, e, "keystream launch");
+        if ((e = fhd::launch_permute(b, encrypt, s)) != cudaSuccess) return cuda_fail(c, e, "permute launch");
+    }
+    c->last_stream = s;
+    return FHD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *fhd_version(void) { return "fhdcipher 0.1 (sm_103a)"; }
+
+int cipher_init(const uint8_t key[32], const fhd_params *params, fhd_cipher **out) {
+    if (!key || !out) return fail(nullptr, FHD_ERR_INVALID_ARG, "null argument");
+    uint32_t n, u[4];
+    double h;
+    std::string why;
+    if (!resolve_params(params, n, h, u, why)) return fail(nullptr, FHD_ERR_INVALID_ARG, why);
+    double ic[5];
+    key_to_ic(key, u, ic);
+    return init_common(ic, n, h, u, out);
+}
+
+int cipher_init_raw(double x0, double y0, double z0, double w0, double gamma, const fhd_params *params,
+                    fhd_cipher **out) {
+    if (!out) return fail(nullptr, FHD_ERR_INVALID_ARG, "null argument");
+    uint32_t n, u[4];
+    double h;
+    std::string why;
+    if (!resolve_params(params, n, h, u, why)) return fail(nullptr, FHD_ERR_INVALID_ARG, why);
+    const double ic[5] = {x0, y0, z0, w0, gamma};
+    return init_common(ic, n, h, u, out);
+}
+
+int cipher_open_stream(fhd_cipher *c, uint32_t *stream_id) {
+    if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
+    return open_with_ic(c, c->key_ic, stream_id);
+}
+
+int cipher_open_stream_key(fhd_cipher *c, const uint8_t key[32], uint32_t *stream_id) {
+    if (!c || !key) return fail(c, FHD_ERR_INVALID_ARG, "null argument");
+    double ic[5];
+    key_to_ic(key, c->u, ic);
+    return open_with_ic(c, ic, stream_id);
+}
+
+int cipher_close_stream(fhd_cipher *c, uint32_t stream_id) {
+    if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
+    if (stream_id >= c->open.size() || !c->open[stream_id]) return fail(c, FHD_ERR_BAD_STREAM, "stream not open");
+    c->open[stream_id] = 0;
+    return FHD_OK;
+}
+
+int encrypt_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream) {
+    return run_frames(c, count, frames, stream, true);
+}
+
+int decrypt_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream) {
+    return run_frames(c, count, frames, stream, false);
+}
+
+int cipher_export_state(fhd_cipher *c, uint32_t stream_id, void *buf, size_t len) {
+    if (!c || !buf) return fail(c, FHD_ERR_INVALID_ARG, "null argument");
+    if (len < FHD_STATE_BYTES) return fail(c, FHD_ERR_INVALID_ARG, "buffer shorter than FHD_STATE_BYTES");
+    if (stream_id >= c->open.size() || !c->open[stream_id]) return fail(c, FHD_ERR_BAD_STREAM, "stream not open");
+    cudaError_t e = c->last_stream ? cudaStreamSynchronize(c->last_stream) : cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(buf, c->d_states + stream_id, FHD_STATE_BYTES, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "export state");
+    return FHD_OK;
+}
+
+int cipher_import_state(fhd_cipher *c, uint32_t stream_id, const void *buf, size_t len) {
+    if (!c || !buf) return fail(c, FHD_ERR_INVALID_ARG, "null argument");
+    if (len < FHD_STATE_BYTES) return fail(c, FHD_ERR_INVALID_ARG, "buffer shorter than FHD_STATE_BYTES");
+    if (stream_id >= c->open.size() || !c->open[stream_id]) return fail(c, FHD_ERR_BAD_STREAM, "stream not open");
+    StreamState st;
+    std::memcpy(&st, buf, sizeof st);
+    cudaError_t e = c->last_stream ? cudaStreamSynchronize(c->last_stream) : cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_states + stream_id, &st, sizeof st, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "import state");
+    c->mirror[stream_id] = st;
+    return FHD_OK;
+}
+
+int cipher_sync_status(fhd_cipher *c, void *stream) {
+    if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+    unsigned st = 0;
+    e = cudaMemcpy(&st, c->d_status, sizeof st, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read status");
+    if (st & fhd::kStatusTimeout) return fail(c, FHD_ERR_TIMEOUT, "a bounded device wait timed out");
+    if (st) return fail(c, FHD_ERR_STATE, "device status word " + std::to_string(st));
+    return FHD_OK;
+}
+
+const char *cipher_last_error(const fhd_cipher *c) { return c ? c->err.c_str() : g_err.c_str(); }
+
+void cipher_destroy(fhd_cipher *c) {
+    if (!c) return;
+    cudaDeviceSynchronize();
+    cudaFree(c->d_scratch);
+    cudaFree(c->d_states);
+    cudaFree(c->d_status);
+    delete c;
+}
+
+int fhd_frame_digest(const uint8_t *data, uint64_t nbytes, uint32_t n, uint32_t count, uint8_t *digest,
+                     void *stream) {
+    if ((!data && nbytes) || !digest) return fail(nullptr, FHD_ERR_INVALID_ARG, "null argument");
+    if (n == 0 || n > FHD_MAX_WORKERS) return fail(nullptr, FHD_ERR_INVALID_ARG, "n must be 1..FHD_MAX_WORKERS");
+    if (count == 0) return FHD_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint8_t *part = nullptr;
+    cudaError_t e = cudaMallocAsync(&part, 32ull * n * count, s);
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+    e = fhd::launch_sha_plain(data, nbytes, n, count, part, s);
+    if (e == cudaSuccess) e = fhd::launch_fold(part, n, count, digest, s);
+    cudaFreeAsync(part, s);
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("digest launch: ") + cudaGetErrorString(e));
+    return FHD_OK;
+}
+
+int fhd_master(double *state, const uint8_t *H, const fhd_params *params, double *IR, void *stream) {
+    if (!state || !H || !IR) return fail(nullptr, FHD_ERR_INVALID_ARG, "null argument");
+    uint32_t n, u[4];
+    double h;
+    std::string why;
+    if (!resolve_params(params, n, h, u, why)) return fail(nullptr, FHD_ERR_INVALID_ARG, why);
+    cudaError_t e = fhd::launch_master_raw(state, H, n, h, u, IR, nullptr, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("master launch: ") + cudaGetErrorString(e));
+    return FHD_OK;
+}
+
+int fhd_keystream(const double *IR, double gamma, const fhd_params *params, uint32_t height, uint32_t width,
+                  uint32_t channels, uint16_t *D, uint8_t *B, void *stream) {
+    if (!IR || !D || !B) return fail(nullptr, FHD_ERR_INVALID_ARG, "null argument");
+    uint32_t n, u[4];
+    double h;
+    std::string why;
+    if (!resolve_params(params, n, h, u, why)) return fail(nullptr, FHD_ERR_INVALID_ARG, why);
+    if (!check_dims(height, width, channels, why)) return fail(nullptr, FHD_ERR_INVALID_ARG, why);
+    static thread_local Batch b;
+    std::memset(&b, 0, sizeof b);
+    b.count = 1;
+    b.n = n;
+    b.hstep = h;
+    b.hhalf = h / 2.0;
+    b.hsixth = h / 6.0;
+    FrameDesc &d = b.f[0];
+    d.IR = const_cast<double *>(IR);
+    d.D = D;
+    d.B = B;
+    d.gamma = gamma;
+    d.h = height;
+    d.w = width;
+    d.C = channels;
+    d.N = (uint64_t)height * width * channels;
+    cudaError_t e = fhd::launch_keystream(b, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("keystream launch: ") + cudaGetErrorString(e));
+    return FHD_OK;
+}
+
+static int permute_one(const uint8_t *src, uint8_t *dst, uint32_t height, uint32_t width, uint32_t channels,
+                       const uint16_t *D, const uint8_t *B, void *stream, bool encrypt) {
+    if (!src || !dst || !D || !B) return fail(nullptr, FHD_ERR_INVALID_ARG, "null argument");
+    std::string why;
+    if (!check_dims(height, width, channels, why)) return fail(nullptr, FHD_ERR_INVALID_ARG, why);
+    uint64_t N = (uint64_t)height * width * channels;
+    if (src < dst + N && dst < src + N) return fail(nullptr, FHD_ERR_INVALID_ARG, "src and dst overlap");
+    cudaError_t e = prepare_device();
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("prepare: ") + cudaGetErrorString(e));
+    static thread_local Batch b;
+    std::memset(&b, 0, sizeof b);
+    b.count = 1;
+    FrameDesc &d = b.f[0];
+    d.src = src;
+    d.dst = dst;
+    d.D = const_cast<uint16_t *>(D);
+    d.B = const_cast<uint8_t *>(B);
+    d.h = height;
+    d.w = width;
+    d.C = channels;
+    d.N = N;
+    d.P = fhd::strip_width(height, width, channels);
+    d.cta0 = 0;
+    b.perm_ctas = fhd::permute_strips(width, d.P);
+    e = fhd::launch_permute(b, encrypt, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("permute launch: ") + cudaGetErrorString(e));
+    return FHD_OK;
+}
+
+int fhd_permute_encrypt(const uint8_t *src, uint8_t *dst, uint32_t height, uint32_t width, uint32_t channels,
+                        const uint16_t *D, const uint8_t *B, void *stream) {
+    return permute_one(src, dst, height, width, channels, D, B, stream, true);
+}
+
+int fhd_permute_decrypt(const uint8_t *src, uint8_t *dst, uint32_t height, uint32_t width, uint32_t channels,
+                        const uint16_t *D, const uint8_t *B, void *stream) {
+    return permute_one(src, dst, height, width, channels, D, B, stream, false);
+}
+
+uint32_t fhd_strip_width(uint32_t height, uint32_t width, uint32_t channels) {
+    if (!height || !width || !channels || channels > 4) return 0;
+    return fhd::strip_width(height, width, channels);
+}
+
+int fhd_set_strip_width(uint32_t height, uint32_t width, uint32_t channels, uint32_t P) {
+    if (!height || !width || !channels || channels > 4 || P > 4096)
+        return fail(nullptr, FHD_ERR_INVALID_ARG, "bad strip override");
+    return fhd::set_strip_override(height, width, channels, P) == 0 ? FHD_OK
+                                                                     : fail(nullptr, FHD_ERR_TOO_LARGE, "override table full");
+}
+
+}  // extern "C"

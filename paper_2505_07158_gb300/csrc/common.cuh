@@ -1,0 +1,76 @@
+// Internal declarations shared by the CUDA translation units of libfhdcipher.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/fhdcipher.h"
+
+namespace fhd {
+
+// Frames per launch: the per-frame descriptors travel as a kernel parameter
+// (well under the 32 KB parameter limit of sm_70+ with CUDA 12.1+).
+constexpr int kMaxBatch = 128;
+
+// Per-frame launch descriptor.  All pointers are device pointers.
+struct FrameDesc {
+    const uint8_t *src;
+    uint8_t *dst;
+    uint8_t *digest;   // 32 bytes: written by encrypt (H), read by decrypt
+    uint8_t *B;        // N bytes of XOR keystream (scratch)
+    uint16_t *D;       // C*(h+w) shift distances (scratch)
+    double *IR;        // 2n x 4 iterates of LHCS_m (scratch)
+    uint8_t *part;     // n x 32 sub-frame digests (scratch)
+    uint64_t N;        // h*w*C
+    double gamma;      // control parameter of the frame's stream
+    uint32_t h, w, C;
+    uint32_t slot;     // index of the stream's chaining state
+    uint32_t P;        // strip width in pixels for the permutation kernels
+    uint32_t cta0;     // first permutation CTA of this frame
+};
+
+struct Batch {
+    uint32_t count;
+    uint32_t n;               // worker pairs / sub-frames per frame
+    uint32_t groups;          // streams in this batch (master CTAs)
+    uint32_t perm_ctas;       // total permutation CTAs
+    double hstep, hhalf, hsixth;   // RK4 step h, h/2 and h/6 (rounded once, on the host)
+    uint32_t u[4];            // reconstruction bounds
+    uint16_t order[kMaxBatch];          // frame indices grouped by stream, in call order
+    uint16_t group_begin[kMaxBatch + 1];
+    FrameDesc f[kMaxBatch];
+};
+
+// Chaining state of one video stream (Sec. II-A): x, y, z, w, gamma, frames done.
+struct StreamState {
+    double v[4];
+    double gamma;
+    unsigned long long frames;
+};
+static_assert(sizeof(StreamState) == FHD_STATE_BYTES, "state layout");
+
+// Device status word bits (cipher_sync_status).
+enum : unsigned {
+    kStatusNonFinite = 1u << 0,  // a chaotic state became NaN/Inf
+    kStatusTimeout = 1u << 1,    // a bounded wait gave up
+    kStatusBounds = 1u << 2,     // a bounds check failed (checked builds)
+};
+
+// Launchers (one per kernel family); each returns the launch error.
+cudaError_t launch_sha_subframes(const Batch &b, cudaStream_t s);
+cudaError_t launch_sha_plain(const uint8_t *data, uint64_t nbytes, uint32_t n, uint32_t count,
+                             uint8_t *part, cudaStream_t s);
+cudaError_t launch_fold(const uint8_t *part, uint32_t n, uint32_t count, uint8_t *digest, cudaStream_t s);
+cudaError_t launch_master(const Batch &b, StreamState *states, bool encrypt, unsigned *status, cudaStream_t s);
+cudaError_t launch_master_raw(double *state5, const uint8_t *H, uint32_t n, double hstep, const uint32_t u[4],
+                              double *IR, unsigned *status, cudaStream_t s);
+cudaError_t launch_keystream(const Batch &b, cudaStream_t s);
+cudaError_t launch_permute(const Batch &b, bool encrypt, cudaStream_t s);
+
+// Strip width for the permutation kernels; dynamic shared memory per CTA.
+uint32_t strip_width(uint32_t h, uint32_t w, uint32_t C);
+size_t permute_smem_bytes(uint32_t h, uint32_t P, uint32_t C, bool encrypt);
+uint32_t permute_strips(uint32_t w, uint32_t P);
+cudaError_t permute_prepare();   // opt in to large dynamic shared memory
+int set_strip_override(uint32_t h, uint32_t w, uint32_t C, uint32_t P);
+
+}  // namespace fhd

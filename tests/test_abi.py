@@ -1,0 +1,61 @@
+"""The C-ABI library loads and exports every symbol include/fhdcipher.h declares
+(no GPU needed: only host-side logic is exercised here)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fhdcipher.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_0-9]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2505_07158_gb300 as fhd
+    return fhd.load()
+
+
+def test_header_declares_the_documented_api():
+    import paper_2505_07158_gb300 as fhd
+    assert declared_functions() == sorted(fhd.EXPORTS)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    import paper_2505_07158_gb300 as fhd
+    out = subprocess.run(["nm", "-D", "--defined-only", fhd.library_path()], capture_output=True, text=True).stdout
+    exported = set(line.split()[-1] for line in out.splitlines() if line.strip())
+    for name in declared_functions():
+        assert name in exported, name
+        assert getattr(lib, name) is not None
+
+
+def test_host_side_argument_checks(lib):
+    import paper_2505_07158_gb300 as fhd
+    out = ctypes.c_void_p()
+    assert lib.cipher_init(None, None, ctypes.byref(out)) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.encrypt_frames(None, 1, None, None) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.cipher_open_stream(None, None) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.fhd_permute_encrypt(None, None, 4, 4, 3, None, None, None) == fhd.FHD_ERR_INVALID_ARG
+    assert b"null" in lib.cipher_last_error(None)
+    assert lib.fhd_set_strip_width(0, 4, 3, 8) == fhd.FHD_ERR_INVALID_ARG
+
+
+def test_strip_width_fits_shared_memory(lib):
+    import paper_2505_07158_gb300 as fhd
+    assert fhd.fhd_strip_width(1080, 1920, 3) == 64
+    assert fhd.fhd_strip_width(2160, 3840, 3) == 32
+    assert fhd.fhd_strip_width(4320, 7680, 3) == 16
+    assert fhd.fhd_strip_width(1, 1, 1) == 1
+    assert fhd.fhd_strip_width(16384, 32768, 4) >= 1
+    for h, w, c in [(480, 640, 3), (720, 1280, 3), (3, 5, 3), (16384, 7, 4)]:
+        P = fhd.fhd_strip_width(h, w, c)
+        assert P >= 1 and h * (P + 1) * c + 4 * (P + 1) * c + 16 <= 232448
