@@ -155,6 +155,23 @@ int fhd_permute_decrypt(const uint8_t *src, uint8_t *dst, uint32_t height, uint3
 uint32_t fhd_strip_width(uint32_t height, uint32_t width, uint32_t channels);
 int fhd_set_strip_width(uint32_t height, uint32_t width, uint32_t channels, uint32_t P);
 
+/* ---- Instrumentation (not part of the cipher). ---- */
+
+/* Kernel kinds reported by cipher_profile_read, in this order. */
+enum { FHD_K_SHA = 0, FHD_K_MASTER = 1, FHD_K_KEYSTREAM = 2, FHD_K_ENCRYPT = 3, FHD_K_DECRYPT = 4, FHD_K_COUNT = 5 };
+
+/* Start (enable != 0) or stop recording a CUDA event pair on the launch
+ * stream around every kernel this handle launches. */
+int cipher_profile(fhd_cipher *c, int enable);
+
+/* Wait for the recorded events, add up per kernel kind the elapsed
+ * milliseconds and launch counts since the last read into ms[FHD_K_COUNT]
+ * and launches[FHD_K_COUNT], and forget them. */
+int cipher_profile_read(fhd_cipher *c, double *ms, uint32_t *launches);
+
+/* Number of kernels this library has launched in this process. */
+uint64_t fhd_launch_count(void);
+
 /* Library version string. */
 const char *fhd_version(void);
 

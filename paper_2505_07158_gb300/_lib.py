@@ -33,7 +33,9 @@ EXPORTS = (
     "encrypt_frames", "decrypt_frames", "cipher_export_state", "cipher_import_state", "cipher_sync_status",
     "cipher_last_error", "cipher_destroy", "fhd_frame_digest", "fhd_master", "fhd_keystream",
     "fhd_permute_encrypt", "fhd_permute_decrypt", "fhd_strip_width", "fhd_set_strip_width", "fhd_version",
+    "cipher_profile", "cipher_profile_read", "fhd_launch_count",
 )
+KERNEL_KINDS = ("sha", "master", "keystream", "encrypt", "decrypt")
 
 
 class FhdError(RuntimeError):
@@ -86,6 +88,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "fhd_strip_width": (u32, [u32, u32, u32]),
             "fhd_set_strip_width": (i32, [u32, u32, u32, u32]),
             "fhd_version": (ctypes.c_char_p, []),
+            "cipher_profile": (i32, [P, i32]),
+            "cipher_profile_read": (i32, [P, P, P]),
+            "fhd_launch_count": (ctypes.c_uint64, []),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -219,6 +224,17 @@ class Cipher:
     def sync_status(self, stream=None):
         _check(load().cipher_sync_status(self._handle(), _stream_ptr(stream)), self._h)
 
+    def profile(self, enable: bool = True):
+        """Record CUDA events around every kernel this handle launches."""
+        _check(load().cipher_profile(self._handle(), 1 if enable else 0), self._h)
+
+    def profile_read(self) -> dict:
+        """{kind: (ms, launches)} since the last read (synchronises on the events)."""
+        ms = (ctypes.c_double * 5)()
+        n = (ctypes.c_uint32 * 5)()
+        _check(load().cipher_profile_read(self._handle(), ms, n), self._h)
+        return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_KINDS)}
+
     def last_error(self) -> str:
         return load().cipher_last_error(self._h).decode(errors="replace")
 
@@ -300,6 +316,10 @@ def fhd_strip_width(height: int, width: int, channels: int) -> int:
 
 def fhd_set_strip_width(height: int, width: int, channels: int, P: int):
     _check(load().fhd_set_strip_width(height, width, channels, P))
+
+
+def fhd_launch_count() -> int:
+    return int(load().fhd_launch_count())
 
 
 def fhd_version() -> str:

@@ -3,6 +3,7 @@
 // batch (K1 sub-frame SHA-256, K2a master LHCS, K2b worker LHCS pairs,
 // K3/K4 fused permutation).  Every step of the cipher runs in the kernels;
 // the host only validates, lays out descriptors and enqueues.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -30,11 +31,35 @@ struct fhd_cipher {
     size_t scratch_cap = 0;
     cudaStream_t last_stream = nullptr;
     std::string err;
+    bool prof = false;
+    struct Rec { int kind; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
 };
 
 namespace {
 
 thread_local std::string g_err;   // last error of the handle-less entry points
+std::atomic<uint64_t> g_launches{0};
+
+cudaEvent_t take_event(fhd_cipher *c) {
+    if (!c->pool.empty()) { cudaEvent_t e = c->pool.back(); c->pool.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Launch one kernel family, counting it and (when profiling) bracketing it
+// with events on the launch stream.
+template <class F>
+cudaError_t timed(fhd_cipher *c, int kind, cudaStream_t s, F &&launch) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (c && c->prof) { a = take_event(c); b = take_event(c); cudaEventRecord(a, s); }
+    cudaError_t e = launch();
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (c && c->prof) { cudaEventRecord(b, s); c->recs.push_back({kind, a, b}); }
+    return e;
+}
 
 int fail(fhd_cipher *c, int code, const std::string &msg) {
     if (c) c->err = msg; else g_err = msg;
@@ -259,10 +284,14 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
                 if (b.f[k2].slot == sid) b.order[pos++] = (uint16_t)k2;
         }
         b.group_begin[b.groups] = (uint16_t)pos;
-        if (encrypt && (e = fhd::launch_sha_subframes(b, s)) != cudaSuccess) return cuda_fail(c, e, "sha launch");
-        if ((e = fhd::launch_master(b, c->d_states, encrypt, c->d_status, s)) != cudaSuccess) return cuda_fail(c, e, "master launch");
-        if ((e = fhd::launch_keystream(b, s)) != cudaSuccess) return cuda_fail(c, e, "keystream launch");
-        if ((e = fhd::launch_permute(b, encrypt, s)) != cudaSuccess) return cuda_fail(c, e, "permute launch");
+        if (encrypt && (e = timed(c, FHD_K_SHA, s, [&] { return fhd::launch_sha_subframes(b, s); })) != cudaSuccess)
+            return cuda_fail(c, e, "sha launch");
+        if ((e = timed(c, FHD_K_MASTER, s, [&] { return fhd::launch_master(b, c->d_states, encrypt, c->d_status, s); })) != cudaSuccess)
+            return cuda_fail(c, e, "master launch");
+        if ((e = timed(c, FHD_K_KEYSTREAM, s, [&] { return fhd::launch_keystream(b, s); })) != cudaSuccess)
+            return cuda_fail(c, e, "keystream launch");
+        if ((e = timed(c, encrypt ? FHD_K_ENCRYPT : FHD_K_DECRYPT, s, [&] { return fhd::launch_permute(b, encrypt, s); })) != cudaSuccess)
+            return cuda_fail(c, e, "permute launch");
     }
     c->last_stream = s;
     return FHD_OK;
@@ -361,9 +390,37 @@ int cipher_sync_status(fhd_cipher *c, void *stream) {
 
 const char *cipher_last_error(const fhd_cipher *c) { return c ? c->err.c_str() : g_err.c_str(); }
 
+int cipher_profile(fhd_cipher *c, int enable) {
+    if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
+    c->prof = enable != 0;
+    return FHD_OK;
+}
+
+int cipher_profile_read(fhd_cipher *c, double *ms, uint32_t *launches) {
+    if (!c || !ms || !launches) return fail(c, FHD_ERR_INVALID_ARG, "null argument");
+    for (int k = 0; k < FHD_K_COUNT; ++k) { ms[k] = 0.0; launches[k] = 0; }
+    int rc = FHD_OK;
+    for (auto &r : c->recs) {
+        float t = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e != cudaSuccess) rc = cuda_fail(c, e, "profile events");
+        ms[r.kind] += t;
+        launches[r.kind] += 1;
+        c->pool.push_back(r.a);
+        c->pool.push_back(r.b);
+    }
+    c->recs.clear();
+    return rc;
+}
+
+uint64_t fhd_launch_count(void) { return g_launches.load(); }
+
 void cipher_destroy(fhd_cipher *c) {
     if (!c) return;
     cudaDeviceSynchronize();
+    for (auto &r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : c->pool) cudaEventDestroy(e);
     cudaFree(c->d_scratch);
     cudaFree(c->d_states);
     cudaFree(c->d_status);
@@ -379,8 +436,8 @@ int fhd_frame_digest(const uint8_t *data, uint64_t nbytes, uint32_t n, uint32_t 
     uint8_t *part = nullptr;
     cudaError_t e = cudaMallocAsync(&part, 32ull * n * count, s);
     if (e != cudaSuccess) return fail(nullptr, FHD_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
-    e = fhd::launch_sha_plain(data, nbytes, n, count, part, s);
-    if (e == cudaSuccess) e = fhd::launch_fold(part, n, count, digest, s);
+    e = timed(nullptr, FHD_K_SHA, s, [&] { return fhd::launch_sha_plain(data, nbytes, n, count, part, s); });
+    if (e == cudaSuccess) e = timed(nullptr, FHD_K_SHA, s, [&] { return fhd::launch_fold(part, n, count, digest, s); });
     cudaFreeAsync(part, s);
     if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("digest launch: ") + cudaGetErrorString(e));
     return FHD_OK;
@@ -392,7 +449,8 @@ int fhd_master(double *state, const uint8_t *H, const fhd_params *params, double
     double h;
     std::string why;
     if (!resolve_params(params, n, h, u, why)) return fail(nullptr, FHD_ERR_INVALID_ARG, why);
-    cudaError_t e = fhd::launch_master_raw(state, H, n, h, u, IR, nullptr, (cudaStream_t)stream);
+    cudaError_t e = timed(nullptr, FHD_K_MASTER, (cudaStream_t)stream,
+                          [&] { return fhd::launch_master_raw(state, H, n, h, u, IR, nullptr, (cudaStream_t)stream); });
     if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("master launch: ") + cudaGetErrorString(e));
     return FHD_OK;
 }
@@ -421,7 +479,8 @@ int fhd_keystream(const double *IR, double gamma, const fhd_params *params, uint
     d.w = width;
     d.C = channels;
     d.N = (uint64_t)height * width * channels;
-    cudaError_t e = fhd::launch_keystream(b, (cudaStream_t)stream);
+    cudaError_t e = timed(nullptr, FHD_K_KEYSTREAM, (cudaStream_t)stream,
+                          [&] { return fhd::launch_keystream(b, (cudaStream_t)stream); });
     if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("keystream launch: ") + cudaGetErrorString(e));
     return FHD_OK;
 }
@@ -450,7 +509,8 @@ static int permute_one(const uint8_t *src, uint8_t *dst, uint32_t height, uint32
     d.P = fhd::strip_width(height, width, channels);
     d.cta0 = 0;
     b.perm_ctas = fhd::permute_strips(width, d.P);
-    e = fhd::launch_permute(b, encrypt, (cudaStream_t)stream);
+    e = timed(nullptr, encrypt ? FHD_K_ENCRYPT : FHD_K_DECRYPT, (cudaStream_t)stream,
+              [&] { return fhd::launch_permute(b, encrypt, (cudaStream_t)stream); });
     if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("permute launch: ") + cudaGetErrorString(e));
     return FHD_OK;
 }
