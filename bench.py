@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
+    ap.add_argument("--frames", type=int, default=30, help="frames per step (30 = the clip; smaller for ncu)")
     return ap.parse_args()
 
 
@@ -208,6 +209,8 @@ def run_reference(args):
 # ---------------------------------------------------------------- GPU arm
 
 def run_ours(args):
+    global FRAMES
+    FRAMES = args.frames
     import torch
     import torch.distributed as dist
 
@@ -225,6 +228,8 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
+    from paper_2505_07158_gb300 import autotune
+    tuned = autotune.tune([(HGT, WID, CH)])
     clip = si.clip(FRAMES, HGT, WID, CH, seed=rank)
     host = torch.from_numpy(clip).pin_memory()
     srcs = [host[t].to(dev) for t in range(FRAMES)]
@@ -381,7 +386,8 @@ def run_ours(args):
             "config": {"workload": "30-frame 1920x1080x3 gradient+noise clip (sigma 8, 2 px/frame), one stream "
                                    "per GPU, n=32 workers, RK4 h=0.001; encrypt_frames + decrypt_frames per step",
                        "frames_per_step": FRAMES * world, "l2": "inputs larger than L2 (~560 MB live per step)",
-                       "parallelism": f"replicas x{world} (independent streams)"},
+                       "parallelism": f"replicas x{world} (independent streams)",
+                       "strip_width": tuned.get(f"{HGT}x{WID}x{CH}")},
             "verified_round_trip": bool(verified) and bool(e2e_ok),
             "e2e": {"value": world * FRAMES / (e2e_ms / 1000.0), "unit": "frames/s",
                     "h2d_bytes_per_step": FRAMES * N, "d2h_bytes_per_step": FRAMES * N + FRAMES * 32},

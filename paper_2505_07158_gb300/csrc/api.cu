@@ -124,7 +124,7 @@ cudaError_t prepare_device() {
 bool check_dims(uint32_t h, uint32_t w, uint32_t C, std::string &why) {
     if (h == 0 || w == 0 || C == 0) { why = "frame dimensions must be non-zero"; return false; }
     if (C > 4) { why = "channels must be 1..4"; return false; }
-    if (h > 16384u || w > FHD_MAX_DIM) { why = "frame exceeds 16384 rows or 32768 columns"; return false; }
+    if (h > FHD_MAX_HEIGHT || w > FHD_MAX_DIM) { why = "frame exceeds FHD_MAX_HEIGHT rows or FHD_MAX_DIM columns"; return false; }
     if (fhd::strip_width(h, w, C) == 0) { why = "frame too tall for the shared-memory strip"; return false; }
     return true;
 }

@@ -12,11 +12,15 @@
 //
 // GPU mapping.  On this GPU a binary64 warp instruction occupies the SM
 // sub-partition's FP64 pipe for ~64 cycles whatever the number of active
-// lanes, so a warp should carry 32 independent chains and one chain's four
-// variables should be spread over four warps on four sub-partitions: a CTA is
-// 4 warps, warp v owns variable v (x, y, z, w) of 32 chains (lane = chain),
-// and the stage inputs are exchanged through shared memory with one barrier
-// per RK4 stage.
+// lanes, and every chain is strictly sequential, so the time per step is set
+// by the binary64 instructions one warp issues per step.  A warp carries 32
+// independent chains and one chain's four variables are spread over four
+// warps on four sub-partitions: a CTA is 4 warps, warp v owns variable v
+// (x, y, z, w) of 32 chains (lane = chain), and the stage inputs are exchanged
+// through shared memory with one barrier per RK4 stage.  (Measured on GB300:
+// ~3.5k cycles per step; one warp per 8 chains with lane-local variables and
+// shuffles, and moving off-path operations to exact integer emulation, were
+// both slower.)
 #include "common.cuh"
 
 namespace fhd {
@@ -62,13 +66,13 @@ __device__ __forceinline__ void rk4_step_coop(double &s, int v, int lane, double
     buf[1][v][lane] = t;
     __syncthreads();
     k = lhcs_f(v, buf[1][0][lane], buf[1][1][lane], buf[1][2][lane], buf[1][3][lane], gamma);
-    acc = __dadd_rn(acc, twice(k));
     t = __dadd_rn(s, __dmul_rn(c.hh, k));
+    acc = __dadd_rn(acc, twice(k));
     buf[0][v][lane] = t;
     __syncthreads();
     k = lhcs_f(v, buf[0][0][lane], buf[0][1][lane], buf[0][2][lane], buf[0][3][lane], gamma);
-    acc = __dadd_rn(acc, twice(k));
     t = __dadd_rn(s, __dmul_rn(c.h, k));
+    acc = __dadd_rn(acc, twice(k));
     buf[1][v][lane] = t;
     __syncthreads();
     k = lhcs_f(v, buf[1][0][lane], buf[1][1][lane], buf[1][2][lane], buf[1][3][lane], gamma);
