@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
     ap.add_argument("--frames", type=int, default=30, help="frames per step (30 = the clip; smaller for ncu)")
+    ap.add_argument("--serve-seconds", type=float, default=6.0, help="length of each serving run (60 s = full config)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the mixed-batch and serving measurements")
     return ap.parse_args()
 
 
@@ -369,6 +371,8 @@ def run_ours(args):
                         "note": f"{N_WORKERS} sequential messages per frame: one thread each"}
     dominant = max(kern, key=lambda k: kern[k]["share"]) if kern else None
 
+    extras = {} if args.no_extras else run_extras(args, rank, fhd, torch)
+
     line = None
     if rank == 0:
         cpu = None
@@ -399,12 +403,84 @@ def run_ours(args):
             "kernels": kern,
             "kernel_roofs": roofs,
             "cpu_baseline": cpu,
+            **extras,
         }
         print(json.dumps(line))
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+MIXED = [(480, 640, 3), (720, 1280, 3), (1080, 1920, 3), (2160, 3840, 3)]
+SERVE_RES = [(480, 640, 3), (720, 1280, 3), (1080, 1920, 3)]
+
+
+def run_extras(args, rank, fhd, torch):
+    """Batched mixed-resolution graph launch (64 frames) and the serving loop."""
+    from paper_2505_07158_gb300 import autotune, batching, serving
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {}
+    # ---- 64 frames: 16 each of VGA, 720p, 1080p, 4K; one stream (own key) per frame
+    autotune.tune(MIXED)
+    shapes = [s for s in MIXED for _ in range(16)]
+    frames = [torch.from_numpy(si.gradient_frame(*s, t=k, seed=rank + 11)).to(dev) for k, s in enumerate(shapes)]
+    keys = [si.key(1000 * (rank + 1) + k) for k in range(len(shapes))]
+    enc = fhd.Cipher(keys[0], n_workers=N_WORKERS)
+    enc_items, dec_items, dec = batching.mixed_batch(shapes, keys, enc, frames, dev)
+    g_enc = batching.GraphedCall(enc, enc_items, encrypt=True)
+    g_dec = batching.GraphedCall(dec, dec_items, encrypt=False)
+    g_enc.replay(); g_dec.replay()
+    torch.cuda.synchronize()
+    ok = all(torch.equal(it[2], fr) for it, fr in zip(dec_items, frames))
+    reps = 3
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        g_enc.replay()
+        g_dec.replay()
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b) / reps
+    nbytes = sum(int(np.prod(s)) for s in shapes)
+    # the same 64 frames one call per frame (plain path)
+    torch.cuda.synchronize()
+    a.record()
+    for ei, di in zip(enc_items, dec_items):
+        enc.encrypt_frames([ei])
+        dec.decrypt_frames([di])
+    b.record()
+    b.synchronize()
+    plain_ms = a.elapsed_time(b)
+    out["batched_mixed64"] = {
+        "workload": "64 frames (16 x 640x480, 720p, 1080p, 2160p x3 uint8), one stream and key per frame, "
+                    "encrypt + decrypt as two CUDA-graph replays",
+        "frames_per_s": len(shapes) / (ms / 1000.0), "GB_per_s": 2 * nbytes / (ms / 1000.0) / 1e9,
+        "ms_per_batch_round_trip": ms, "plain_per_frame_frames_per_s": len(shapes) / (plain_ms / 1000.0),
+        "kernels_per_replay": g_enc.kernels_per_replay + g_dec.kernels_per_replay, "round_trip_ok": bool(ok),
+        "strip_widths": {f"{h}x{w}x{c}": fhd.fhd_strip_width(h, w, c) for (h, w, c) in MIXED}}
+    enc.close(); dec.close()
+    del frames, enc_items, dec_items, g_enc, g_dec
+    torch.cuda.empty_cache()
+    # ---- serving: 32 streams, resolutions drawn from VGA / 720p / 1080p, Poisson arrivals
+    g = si.rng(77 + rank)
+    sshapes = [SERVE_RES[int(g.integers(3))] for _ in range(32)]
+    skeys = [si.key(5000 + 100 * rank + k) for k in range(32)]
+    pool = {s: [torch.from_numpy(si.gradient_frame(*s, t=t, seed=5)).to(dev) for t in range(4)] for s in SERVE_RES}
+    serve = {}
+    for fps in (24.0, 30.0, 60.0):
+        st, srv = serving.run(skeys, sshapes, pool, fps=fps, duration=args.serve_seconds, seed=int(fps),
+                              n_workers=N_WORKERS, budget_bytes=20 << 30)
+        srv.close()
+        serve[f"{int(fps)}fps"] = st
+    st, srv = serving.run(skeys, sshapes, pool, fps=30.0, duration=min(args.serve_seconds, 3.0), seed=30,
+                          n_workers=N_WORKERS, budget_bytes=20 << 30, mode="plain")
+    srv.close()
+    serve["plain_30fps"] = st
+    out["serving"] = {"workload": f"32 streams, resolutions uniform over 640x480 / 1280x720 / 1920x1080 x3, "
+                                  f"Poisson arrivals, 20 GB HBM budget, {args.serve_seconds:g} s per rate "
+                                  f"(plain: one frame per call, one CUDA stream)", **serve}
+    return out
 
 
 def main():

@@ -21,8 +21,13 @@
  *  - Errors: 0 on success, a negative FHD_ERR_* code otherwise; nothing is
  *    enqueued when an argument check fails.  cipher_last_error() gives a
  *    message.  No call ever falls back to the CPU.
- *  - One handle is used from one host thread and one CUDA stream at a time:
- *    its scratch buffers are reused by every call.
+ *  - One handle is used from one host thread at a time.  It keeps scratch
+ *    buffers per CUDA stream, so calls on different CUDA streams may run
+ *    concurrently on the device; frames of one video stream must still reach
+ *    the device in order (same CUDA stream, or the caller orders the streams
+ *    with events).  A call may be captured into a CUDA graph once the same
+ *    batch has run uncaptured on that CUDA stream (the scratch is then sized);
+ *    stream open/close/export/import synchronise and must not be captured.
  */
 #ifndef FHDCIPHER_H
 #define FHDCIPHER_H
@@ -102,6 +107,25 @@ int encrypt_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void 
 /* Decrypt `count` frames: the inverse of encrypt_frames given each frame's
  * transmitted digest (read from frames[i].digest). */
 int decrypt_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream);
+
+/* As encrypt_frames / decrypt_frames, with two CUDA events (cudaEvent_t
+ * passed as void*) that order only the chaining step between calls: the
+ * kernel that advances the streams' chaining state (LHCS_m) first waits on
+ * the n_wait events in wait_events (may be NULL / 0), and `master_done` (may
+ * be NULL) is recorded on `stream` right after it.  A caller can issue the
+ * next frames of a stream on another CUDA stream, passing this call's
+ * master_done as a wait event: the digests, keystreams and permutations of
+ * consecutive frames then overlap while their chaining stays in order. */
+int encrypt_frames_ex(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream,
+                      void *const *wait_events, uint32_t n_wait, void *master_done);
+int decrypt_frames_ex(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream,
+                      void *const *wait_events, uint32_t n_wait, void *master_done);
+
+/* Pre-allocate at least `bytes` of scratch for calls on CUDA stream `stream`
+ * (synchronises that stream), so that later calls on it never allocate.
+ * frame_scratch_bytes() gives the scratch one frame needs. */
+int cipher_reserve(fhd_cipher *c, void *stream, uint64_t bytes);
+uint64_t fhd_frame_scratch_bytes(uint32_t n_workers, uint32_t height, uint32_t width, uint32_t channels);
 
 /* Copy a stream's chaining state (FHD_STATE_BYTES bytes) to host memory
  * after synchronising the handle's last CUDA stream; for exact resume. */

@@ -33,7 +33,8 @@ EXPORTS = (
     "encrypt_frames", "decrypt_frames", "cipher_export_state", "cipher_import_state", "cipher_sync_status",
     "cipher_last_error", "cipher_destroy", "fhd_frame_digest", "fhd_master", "fhd_keystream",
     "fhd_permute_encrypt", "fhd_permute_decrypt", "fhd_strip_width", "fhd_set_strip_width", "fhd_version",
-    "cipher_profile", "cipher_profile_read", "fhd_launch_count",
+    "cipher_profile", "cipher_profile_read", "fhd_launch_count", "encrypt_frames_ex", "decrypt_frames_ex",
+    "cipher_reserve", "fhd_frame_scratch_bytes",
 )
 KERNEL_KINDS = ("sha", "master", "keystream", "encrypt", "decrypt")
 
@@ -91,6 +92,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "cipher_profile": (i32, [P, i32]),
             "cipher_profile_read": (i32, [P, P, P]),
             "fhd_launch_count": (ctypes.c_uint64, []),
+            "encrypt_frames_ex": (i32, [P, u32, P, P, P, u32, P]),
+            "decrypt_frames_ex": (i32, [P, u32, P, P, P, u32, P]),
+            "cipher_reserve": (i32, [P, P, u64]),
+            "fhd_frame_scratch_bytes": (u64, [u32, u32, u32, u32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -191,15 +196,37 @@ class Cipher:
             arr[k] = FhdFrame(sid, h, w, c, src.data_ptr(), dst.data_ptr(), digest.data_ptr())
         return arr, len(items)
 
-    def encrypt_frames(self, items: Iterable, stream=None):
-        """items: (stream_id, src, dst, digest) tuples; digest (32 B) is written."""
+    def _run(self, plain, ex, items, stream, master_event, wait_events):
         arr, n = self._frames(items)
-        _check(load().encrypt_frames(self._handle(), n, arr, _stream_ptr(stream)), self._h)
+        if master_event is None and not wait_events:
+            _check(plain(self._handle(), n, arr, _stream_ptr(stream)), self._h)
+            return
+        for ev in wait_events:
+            if not ev.cuda_event:
+                raise ValueError("wait event was never recorded")
+        waits = (ctypes.c_void_p * max(len(wait_events), 1))(*[ev.cuda_event for ev in wait_events])
+        if master_event is not None and not master_event.cuda_event:
+            # torch creates the CUDA event on first record; the library re-records it after LHCS_m.
+            master_event.record(stream if stream is not None else torch.cuda.current_stream())
+        md = ctypes.c_void_p(master_event.cuda_event) if master_event is not None else ctypes.c_void_p()
+        _check(ex(self._handle(), n, arr, _stream_ptr(stream), waits, len(wait_events), md), self._h)
 
-    def decrypt_frames(self, items: Iterable, stream=None):
+    def encrypt_frames(self, items: Iterable, stream=None, master_event=None, wait_events=()):
+        """items: (stream_id, src, dst, digest) tuples; digest (32 B) is written.
+
+        The chaining-state kernel first waits on ``wait_events`` and
+        ``master_event`` is recorded right after it (torch.cuda.Event's)."""
+        lib = load()
+        self._run(lib.encrypt_frames, lib.encrypt_frames_ex, items, stream, master_event, list(wait_events))
+
+    def decrypt_frames(self, items: Iterable, stream=None, master_event=None, wait_events=()):
         """items: (stream_id, src, dst, digest) tuples; digest (32 B) is read."""
-        arr, n = self._frames(items)
-        _check(load().decrypt_frames(self._handle(), n, arr, _stream_ptr(stream)), self._h)
+        lib = load()
+        self._run(lib.decrypt_frames, lib.decrypt_frames_ex, items, stream, master_event, list(wait_events))
+
+    def reserve(self, nbytes: int, stream=None):
+        """Pre-size this CUDA stream's scratch so later calls on it never allocate."""
+        _check(load().cipher_reserve(self._handle(), _stream_ptr(stream), int(nbytes)), self._h)
 
     def encrypt(self, sid: int, src: torch.Tensor, stream=None):
         dst = torch.empty_like(src)
@@ -316,6 +343,10 @@ def fhd_strip_width(height: int, width: int, channels: int) -> int:
 
 def fhd_set_strip_width(height: int, width: int, channels: int, P: int):
     _check(load().fhd_set_strip_width(height, width, channels, P))
+
+
+def fhd_frame_scratch_bytes(n_workers: int, height: int, width: int, channels: int) -> int:
+    return int(load().fhd_frame_scratch_bytes(n_workers, height, width, channels))
 
 
 def fhd_launch_count() -> int:

@@ -27,8 +27,10 @@ struct fhd_cipher {
     StreamState *d_states = nullptr;
     size_t cap_states = 0;
     unsigned *d_status = nullptr;
-    uint8_t *d_scratch = nullptr;
-    size_t scratch_cap = 0;
+    // Scratch (sub-frame digests, LHCS_m iterates, D, B) per CUDA stream, so
+    // that calls on different CUDA streams can run concurrently.
+    struct Scratch { cudaStream_t stream; uint8_t *ptr; size_t cap; };
+    std::vector<Scratch> scratch;
     cudaStream_t last_stream = nullptr;
     std::string err;
     bool prof = false;
@@ -107,6 +109,26 @@ void key_to_ic(const uint8_t key[32], const uint32_t u[4], double ic[5]) {
 
 uint64_t align16(uint64_t x) { return (x + 15) & ~15ull; }
 
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone;
+}
+
+// Wait for every CUDA stream this handle has used.
+cudaError_t sync_all(fhd_cipher *c) {
+    cudaError_t e = cudaSuccess;
+    for (auto &sc : c->scratch) {
+        cudaError_t e2 = cudaStreamSynchronize(sc.stream);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (c->last_stream) {
+        cudaError_t e2 = cudaStreamSynchronize(c->last_stream);
+        if (e == cudaSuccess) e = e2;
+    }
+    return e;
+}
+
+
 std::mutex g_prep_mu;
 bool g_prepared[64] = {};
 
@@ -163,8 +185,7 @@ int open_with_ic(fhd_cipher *c, const double ic[5], uint32_t *id) {
         cudaError_t e = cudaMalloc(&d, cap * sizeof(StreamState));
         if (e != cudaSuccess) return fail(c, FHD_ERR_OOM, std::string("cudaMalloc states: ") + cudaGetErrorString(e));
         if (c->d_states) {
-            if (c->last_stream) cudaStreamSynchronize(c->last_stream);
-            cudaDeviceSynchronize();
+            sync_all(c);
             e = cudaMemcpy(d, c->d_states, c->cap_states * sizeof(StreamState), cudaMemcpyDeviceToDevice);
             cudaFree(c->d_states);
             if (e != cudaSuccess) { cudaFree(d); c->d_states = nullptr; c->cap_states = 0;
@@ -181,7 +202,7 @@ int open_with_ic(fhd_cipher *c, const double ic[5], uint32_t *id) {
     for (int m = 0; m < 4; ++m) st.v[m] = ic[m];
     st.gamma = ic[4];
     st.frames = 0;
-    if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+    sync_all(c);
     cudaError_t e = cudaMemcpy(c->d_states + slot, &st, sizeof st, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(c, e, "upload state");
     c->mirror[slot] = st;
@@ -190,20 +211,32 @@ int open_with_ic(fhd_cipher *c, const double ic[5], uint32_t *id) {
     return FHD_OK;
 }
 
-int ensure_scratch(fhd_cipher *c, size_t need) {
-    if (need <= c->scratch_cap) return FHD_OK;
-    if (c->last_stream) cudaStreamSynchronize(c->last_stream);
-    cudaDeviceSynchronize();
-    cudaFree(c->d_scratch);
-    c->d_scratch = nullptr;
-    c->scratch_cap = 0;
+// Scratch of at least `need` bytes for CUDA stream s.  Growing it waits for
+// the stream's earlier work, so it is refused while the stream is being
+// captured into a CUDA graph (make one uncaptured call of the same batch first).
+int ensure_scratch(fhd_cipher *c, cudaStream_t s, size_t need, uint8_t **out) {
+    fhd_cipher::Scratch *slot = nullptr;
+    for (auto &sc : c->scratch)
+        if (sc.stream == s) slot = &sc;
+    if (slot && need <= slot->cap) { *out = slot->ptr; return FHD_OK; }
+    if (capturing(s))
+        return fail(c, FHD_ERR_STATE, "scratch too small during CUDA graph capture: run the batch once uncaptured first");
+    if (!slot) {
+        c->scratch.push_back({s, nullptr, 0});
+        slot = &c->scratch.back();
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(slot->ptr);
+    slot->ptr = nullptr;
+    slot->cap = 0;
     size_t cap = need + need / 8;
-    cudaError_t e = cudaMalloc(&c->d_scratch, cap);
+    cudaError_t e = cudaMalloc(&slot->ptr, cap);
     if (e != cudaSuccess) {
-        c->d_scratch = nullptr;
+        slot->ptr = nullptr;
         return fail(c, FHD_ERR_OOM, std::string("cudaMalloc scratch: ") + cudaGetErrorString(e));
     }
-    c->scratch_cap = cap;
+    slot->cap = cap;
+    *out = slot->ptr;
     return FHD_OK;
 }
 
@@ -212,7 +245,8 @@ uint64_t frame_scratch(uint32_t n, uint32_t h, uint32_t w, uint32_t C) {
     return align16(32ull * n) + align16(64ull * n) + align16(2ull * C * (h + w)) + align16((uint64_t)h * w * C);
 }
 
-int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream, bool encrypt) {
+int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream, bool encrypt,
+               void *const *wait_events = nullptr, uint32_t n_wait = 0, cudaEvent_t master_done = nullptr) {
     if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
     if (count == 0) return FHD_OK;
     if (!frames) return fail(c, FHD_ERR_INVALID_ARG, "null frames");
@@ -245,9 +279,9 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
             const fhd_frame &f = frames[base + k];
             need += frame_scratch(c->n, f.height, f.width, f.channels);
         }
-        int rc = ensure_scratch(c, need);
+        uint8_t *p = nullptr;
+        int rc = ensure_scratch(c, s, need, &p);
         if (rc != FHD_OK) return rc;
-        uint8_t *p = c->d_scratch;
         uint32_t ctas = 0;
         for (uint32_t k = 0; k < m; ++k) {
             const fhd_frame &f = frames[base + k];
@@ -286,8 +320,14 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
         b.group_begin[b.groups] = (uint16_t)pos;
         if (encrypt && (e = timed(c, FHD_K_SHA, s, [&] { return fhd::launch_sha_subframes(b, s); })) != cudaSuccess)
             return cuda_fail(c, e, "sha launch");
+        if (base == 0)
+            for (uint32_t k = 0; k < n_wait; ++k)
+                if (wait_events[k] && (e = cudaStreamWaitEvent(s, (cudaEvent_t)wait_events[k], 0)) != cudaSuccess)
+                    return cuda_fail(c, e, "wait event");
         if ((e = timed(c, FHD_K_MASTER, s, [&] { return fhd::launch_master(b, c->d_states, encrypt, c->d_status, s); })) != cudaSuccess)
             return cuda_fail(c, e, "master launch");
+        if (master_done && base + m >= count && (e = cudaEventRecord(master_done, s)) != cudaSuccess)
+            return cuda_fail(c, e, "record master event");
         if ((e = timed(c, FHD_K_KEYSTREAM, s, [&] { return fhd::launch_keystream(b, s); })) != cudaSuccess)
             return cuda_fail(c, e, "keystream launch");
         if ((e = timed(c, encrypt ? FHD_K_ENCRYPT : FHD_K_DECRYPT, s, [&] { return fhd::launch_permute(b, encrypt, s); })) != cudaSuccess)
@@ -352,11 +392,33 @@ int decrypt_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void 
     return run_frames(c, count, frames, stream, false);
 }
 
+int encrypt_frames_ex(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream,
+                      void *const *wait_events, uint32_t n_wait, void *master_done) {
+    if (n_wait && !wait_events) return fail(c, FHD_ERR_INVALID_ARG, "null wait_events");
+    return run_frames(c, count, frames, stream, true, wait_events, n_wait, (cudaEvent_t)master_done);
+}
+
+int decrypt_frames_ex(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream,
+                      void *const *wait_events, uint32_t n_wait, void *master_done) {
+    if (n_wait && !wait_events) return fail(c, FHD_ERR_INVALID_ARG, "null wait_events");
+    return run_frames(c, count, frames, stream, false, wait_events, n_wait, (cudaEvent_t)master_done);
+}
+
+int cipher_reserve(fhd_cipher *c, void *stream, uint64_t bytes) {
+    if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
+    uint8_t *p = nullptr;
+    return ensure_scratch(c, (cudaStream_t)stream, bytes, &p);
+}
+
+uint64_t fhd_frame_scratch_bytes(uint32_t n_workers, uint32_t height, uint32_t width, uint32_t channels) {
+    return frame_scratch(n_workers ? n_workers : 32, height, width, channels);
+}
+
 int cipher_export_state(fhd_cipher *c, uint32_t stream_id, void *buf, size_t len) {
     if (!c || !buf) return fail(c, FHD_ERR_INVALID_ARG, "null argument");
     if (len < FHD_STATE_BYTES) return fail(c, FHD_ERR_INVALID_ARG, "buffer shorter than FHD_STATE_BYTES");
     if (stream_id >= c->open.size() || !c->open[stream_id]) return fail(c, FHD_ERR_BAD_STREAM, "stream not open");
-    cudaError_t e = c->last_stream ? cudaStreamSynchronize(c->last_stream) : cudaDeviceSynchronize();
+    cudaError_t e = sync_all(c);
     if (e == cudaSuccess) e = cudaMemcpy(buf, c->d_states + stream_id, FHD_STATE_BYTES, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "export state");
     return FHD_OK;
@@ -368,7 +430,7 @@ int cipher_import_state(fhd_cipher *c, uint32_t stream_id, const void *buf, size
     if (stream_id >= c->open.size() || !c->open[stream_id]) return fail(c, FHD_ERR_BAD_STREAM, "stream not open");
     StreamState st;
     std::memcpy(&st, buf, sizeof st);
-    cudaError_t e = c->last_stream ? cudaStreamSynchronize(c->last_stream) : cudaDeviceSynchronize();
+    cudaError_t e = sync_all(c);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_states + stream_id, &st, sizeof st, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(c, e, "import state");
     c->mirror[stream_id] = st;
@@ -421,7 +483,7 @@ void cipher_destroy(fhd_cipher *c) {
     cudaDeviceSynchronize();
     for (auto &r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->pool) cudaEventDestroy(e);
-    cudaFree(c->d_scratch);
+    for (auto &sc : c->scratch) cudaFree(sc.ptr);
     cudaFree(c->d_states);
     cudaFree(c->d_status);
     delete c;

@@ -1,0 +1,123 @@
+"""Batched mixed-resolution launches, CUDA-graph replay and the serving loop.
+
+Each frame's result must be the same alone and in the mix: graph replays of a
+mixed batch are compared with the CPU oracle stream by stream, and every
+frame the continuous-batching server produced is compared (by a digest of the
+ciphertext) with the same stream encrypted alone, one frame per call."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth_inputs as si
+from gpu_util import dev, host, to_dev
+
+pytestmark = pytest.mark.gpu
+
+fhd = pytest.importorskip("paper_2505_07158_gb300")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2505_07158_gb300 import batching, serving  # noqa: E402
+
+
+def test_graphed_mixed_batch_matches_oracle():
+    shapes = [(48, 64, 3), (30, 50, 3), (64, 64, 1), (20, 36, 4), (72, 40, 3), (16, 16, 3)]
+    keys = [si.key(200 + k) for k in range(len(shapes))]
+    frames = [to_dev(si.uniform_frame(*s, seed=300 + k)) for k, s in enumerate(shapes)]
+    enc = fhd.Cipher(si.key(1))
+    enc_items, dec_items, dec = batching.mixed_batch(shapes, keys, enc, frames)
+    g_enc = batching.GraphedCall(enc, enc_items, encrypt=True)
+    g_dec = batching.GraphedCall(dec, dec_items, encrypt=False)
+    refs = [oracle.Stream.from_key(k) for k in keys]
+    for rep in range(2):            # two replays = the first two frames of every stream
+        g_enc.replay()
+        g_dec.replay()
+        torch.cuda.synchronize()
+        for k, (sid, F, E, H) in enumerate(enc_items):
+            E_ref, H_ref = refs[k].encrypt(host(F))
+            assert np.array_equal(host(E), E_ref), (rep, k)
+            assert bytes(host(H)) == H_ref
+            assert np.array_equal(host(dec_items[k][2]), host(F))
+
+
+def test_concurrent_cuda_streams_share_one_handle():
+    keys = [si.key(400 + k) for k in range(4)]
+    c = fhd.Cipher(keys[0])
+    sids = [c.open_stream(k) for k in keys]
+    lanes = [torch.cuda.Stream() for _ in range(2)]
+    frames = [[to_dev(si.gradient_frame(40, 64, 3, t=t, seed=k)) for t in range(3)] for k in range(4)]
+    outs = [[None] * 3 for _ in range(4)]
+    for t in range(3):
+        for k in range(4):
+            E = torch.empty_like(frames[k][t])
+            H = torch.empty(32, dtype=torch.uint8, device=dev())
+            lane = lanes[k % 2]
+            c.encrypt_frames([(sids[k], frames[k][t], E, H)], stream=lane)
+            outs[k][t] = E
+    torch.cuda.synchronize()
+    for k in range(4):
+        ref = oracle.Stream.from_key(keys[k])
+        for t in range(3):
+            E_ref, _ = ref.encrypt(host(frames[k][t]))
+            assert np.array_equal(host(outs[k][t]), E_ref)
+
+
+def test_served_results_equal_alone():
+    shapes_avail = [(64, 96, 3), (48, 64, 3), (32, 48, 1)]
+    nstreams = 8
+    g = si.rng(7)
+    shapes = [shapes_avail[int(g.integers(3))] for _ in range(nstreams)]
+    keys = [si.key(500 + k) for k in range(nstreams)]
+    pool = {s: [to_dev(si.gradient_frame(*s, t=t, seed=9)) for t in range(5)] for s in set(shapes)}
+    stats, srv = serving.run(keys, shapes, pool, fps=60.0, duration=1.5, seed=3, n_workers=8, fingerprint=True)
+    assert stats["completed_frames"] == stats["offered_frames"] > 0
+    assert stats["p99_ms"] >= stats["p50_ms"] > 0
+    srv.close()
+    # the same streams alone, one frame per call
+    alone = fhd.Cipher(keys[0], n_workers=8)
+    for s in range(nstreams):
+        sid = alone.open_stream(keys[s])
+        seqs = sorted(q for (st, q) in srv.prints if st == s)
+        assert seqs == list(range(len(seqs)))
+        for q in seqs:
+            src = pool[shapes[s]][(s * 7 + q) % 5]
+            E, _ = alone.encrypt(sid, src)
+            d = bytes(host(fhd.fhd_frame_digest(E.view(-1), n=256)).reshape(-1))
+            assert d == srv.prints[(s, q)], (s, q)
+
+
+def test_budget_admission_limits_in_flight_bytes():
+    shapes = [(64, 64, 3)] * 4
+    keys = [si.key(600 + k) for k in range(4)]
+    pool = {(64, 64, 3): [to_dev(si.uniform_frame(64, 64, 3, seed=1))]}
+    one = serving.frame_footprint(64, 64, 3, 8)
+    stats, srv = serving.run(keys, shapes, pool, fps=200.0, duration=0.5, seed=1, n_workers=8,
+                             budget_bytes=2 * one)
+    assert srv.peak <= 2 * one
+    assert stats["completed_frames"] == stats["offered_frames"]
+    srv.close()
+
+
+def test_event_ordered_frames_across_cuda_streams():
+    """Consecutive frames of one stream on alternating CUDA streams, ordered only
+    at the chaining step with events, equal the oracle's sequential encryption."""
+    key = si.key(700)
+    c = fhd.Cipher(key, n_workers=6)
+    sid = c.open_stream()
+    lanes = [torch.cuda.Stream() for _ in range(3)]
+    frames = [to_dev(si.gradient_frame(56, 72, 3, t=t, seed=70)) for t in range(7)]
+    outs, last = [], None
+    for t, F in enumerate(frames):
+        E = torch.empty_like(F)
+        H = torch.empty(32, dtype=torch.uint8, device=dev())
+        ev = torch.cuda.Event()
+        c.encrypt_frames([(sid, F, E, H)], stream=lanes[t % 3], master_event=ev,
+                         wait_events=[last] if last is not None else [])
+        last = ev
+        outs.append((E, H))
+    torch.cuda.synchronize()
+    ref = oracle.Stream.from_key(key, n=6)
+    for F, (E, H) in zip(frames, outs):
+        E_ref, H_ref = ref.encrypt(host(F))
+        assert np.array_equal(host(E), E_ref) and bytes(host(H)) == H_ref
