@@ -153,6 +153,25 @@ void cipher_destroy(fhd_cipher *c);
 int fhd_frame_digest(const uint8_t *data, uint64_t nbytes, uint32_t n, uint32_t count,
                      uint8_t *digest, void *stream);
 
+/* fhd_frame_digest for callers that cannot allocate device memory (no
+ * counterpart in the paper).  Some callers may not call cudaMalloc or any
+ * allocating routine: a capture/encode loop on a real-time path, where an
+ * allocator call can block or synchronise the whole device and stall work
+ * already in flight, or a host framework that reserves all device memory up
+ * front.  This entry point allocates nothing: the count * n sub-frame digests
+ * live in a fixed device array of FHD_NOALLOC_MAX_SUBFRAMES x 32 bytes (2 MiB)
+ * that every GPU loading the library holds until the process exits.
+ * Same arguments and result as fhd_frame_digest.  count * n above
+ * FHD_NOALLOC_MAX_SUBFRAMES returns FHD_ERR_TOO_LARGE and enqueues nothing.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, once per device, with that device current); make
+ * that first call before any stream capture.  All calls share the one array:
+ * calls that overlap on the GPU (e.g. on two CUDA streams without ordering)
+ * race and may return wrong digests. */
+#define FHD_NOALLOC_MAX_SUBFRAMES 65536u
+int fhd_frame_digest_noalloc(const uint8_t *data, uint64_t nbytes, uint32_t n, uint32_t count,
+                             uint8_t *digest, void *stream);
+
 /* Sec. II-A and Algorithm 1: reconstruct x, y, z, w from state[0..3] and the
  * 32-byte digest H, iterate LHCS_m 2n times with gamma = state[4]; write the
  * iterates to IR (2n x 4 binary64, row t = state after step t+1) and the last

@@ -34,7 +34,7 @@ EXPORTS = (
     "cipher_last_error", "cipher_destroy", "fhd_frame_digest", "fhd_master", "fhd_keystream",
     "fhd_permute_encrypt", "fhd_permute_decrypt", "fhd_strip_width", "fhd_set_strip_width", "fhd_version",
     "cipher_profile", "cipher_profile_read", "fhd_launch_count", "encrypt_frames_ex", "decrypt_frames_ex",
-    "cipher_reserve", "fhd_frame_scratch_bytes",
+    "cipher_reserve", "fhd_frame_scratch_bytes", "fhd_frame_digest_noalloc",
 )
 KERNEL_KINDS = ("sha", "master", "keystream", "encrypt", "decrypt")
 
@@ -82,6 +82,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "cipher_last_error": (ctypes.c_char_p, [P]),
             "cipher_destroy": (None, [P]),
             "fhd_frame_digest": (i32, [P, u64, u32, u32, P, P]),
+            "fhd_frame_digest_noalloc": (i32, [P, u64, u32, u32, P, P]),
             "fhd_master": (i32, [P, P, P, P, P]),
             "fhd_keystream": (i32, [P, dbl, P, u32, u32, u32, P, P, P]),
             "fhd_permute_encrypt": (i32, [P, P, u32, u32, u32, P, P, P]),
@@ -291,6 +292,19 @@ def fhd_frame_digest(data: torch.Tensor, n: int = 32, count: int = 1, out: torch
     ptr = data.data_ptr() if data.numel() else 0
     _check(load().fhd_frame_digest(ctypes.c_void_p(ptr), nbytes, n, count, ctypes.c_void_p(out.data_ptr()),
                                    _stream_ptr(stream)))
+    return out
+
+
+def fhd_frame_digest_noalloc(data: torch.Tensor, out: torch.Tensor, n: int = 32, count: int = 1, stream=None):
+    """fhd_frame_digest into a caller-provided ``out`` (count x 32 bytes); the library allocates nothing."""
+    if not data.is_cuda or data.dtype != torch.uint8 or not data.is_contiguous():
+        raise ValueError("data must be a contiguous CUDA uint8 tensor")
+    if not out.is_cuda or out.dtype != torch.uint8 or not out.is_contiguous() or out.numel() < 32 * count:
+        raise ValueError("out must be a contiguous CUDA uint8 tensor of count x 32 bytes")
+    nbytes = data.numel() // max(count, 1)
+    ptr = data.data_ptr() if data.numel() else 0
+    _check(load().fhd_frame_digest_noalloc(ctypes.c_void_p(ptr), nbytes, n, count, ctypes.c_void_p(out.data_ptr()),
+                                           _stream_ptr(stream)))
     return out
 
 

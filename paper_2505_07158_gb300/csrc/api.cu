@@ -505,6 +505,32 @@ int fhd_frame_digest(const uint8_t *data, uint64_t nbytes, uint32_t n, uint32_t 
     return FHD_OK;
 }
 
+// fhd_frame_digest without any allocation: the sub-frame digests go to a
+// fixed device array instead of memory from cudaMallocAsync.  For callers
+// that may not allocate device memory -- e.g. a capture/encode loop on a
+// real-time path, where an allocator call can block or synchronise the device
+// and stall the work already in flight, or a host framework that reserves all
+// device memory up front.  Limits and sharing rules are in the header.
+int fhd_frame_digest_noalloc(const uint8_t *data, uint64_t nbytes, uint32_t n, uint32_t count, uint8_t *digest,
+                             void *stream) {
+    if ((!data && nbytes) || !digest) return fail(nullptr, FHD_ERR_INVALID_ARG, "null argument");
+    if (n == 0 || n > FHD_MAX_WORKERS) return fail(nullptr, FHD_ERR_INVALID_ARG, "n must be 1..FHD_MAX_WORKERS");
+    if (count == 0) return FHD_OK;
+    if ((uint64_t)count * n > fhd::noalloc_max_digests())
+        return fail(nullptr, FHD_ERR_TOO_LARGE,
+                    "count * n exceeds FHD_NOALLOC_MAX_SUBFRAMES (the fixed sub-frame digest array)");
+    uint8_t *part = nullptr;
+    cudaError_t e = fhd::noalloc_scratch(&part);
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    cudaStream_t s = (cudaStream_t)stream;
+    // Every digest slot the fold reads is written by the hash kernel of this
+    // same call, so nothing left by an earlier call needs clearing.
+    e = timed(nullptr, FHD_K_SHA, s, [&] { return fhd::launch_sha_plain(data, nbytes, n, count, part, s); });
+    if (e == cudaSuccess) e = timed(nullptr, FHD_K_SHA, s, [&] { return fhd::launch_fold(part, n, count, digest, s); });
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("digest launch: ") + cudaGetErrorString(e));
+    return FHD_OK;
+}
+
 int fhd_master(double *state, const uint8_t *H, const fhd_params *params, double *IR, void *stream) {
     if (!state || !H || !IR) return fail(nullptr, FHD_ERR_INVALID_ARG, "null argument");
     uint32_t n, u[4];

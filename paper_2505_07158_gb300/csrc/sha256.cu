@@ -11,6 +11,8 @@
 // multiple of 16) and byte loads otherwise; the next block is loaded while
 // the current one is compressed.  Rotations are funnel shifts, the three-input
 // boolean functions map onto LOP3.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace fhd {
@@ -180,7 +182,37 @@ __global__ void fold_kernel(const uint8_t *part, uint32_t n, uint32_t count, uin
     reinterpret_cast<uint32_t *>(digest + 32ull * k)[lane] = acc;
 }
 
+// Scratch of fhd_frame_digest_noalloc: the per-sub-frame digests of one call,
+// in a fixed device array so that the call allocates nothing.  Every GPU that
+// loads the library holds it (2 MiB) until the process exits.
+constexpr uint32_t kNoAllocMaxDigests = 1u << 16;
+static __device__ __align__(256) uint8_t g_noalloc_part[32u * kNoAllocMaxDigests];
+
 }  // namespace
+
+uint32_t noalloc_max_digests() { return kNoAllocMaxDigests; }
+
+// Device address of g_noalloc_part for the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress -- once per device, on the first call made while that
+// device is current -- and cached.
+cudaError_t noalloc_scratch(uint8_t **out) {
+    static std::mutex mu;
+    static void *addr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_part);
+        if (e != cudaSuccess) return e;
+        addr[dev] = p;
+    }
+    *out = static_cast<uint8_t *>(addr[dev]);
+    return cudaSuccess;
+}
 
 cudaError_t launch_sha_subframes(const Batch &b, cudaStream_t s) {
     uint32_t threads = b.count * b.n;
