@@ -5,12 +5,15 @@
 // digest is H = h_1 xor ... xor h_n.  Sub-frame i is the byte range
 // [floor(i*N/n), floor((i+1)*N/n)).  SHA-256 follows FIPS 180-4.
 //
-// GPU mapping: one thread per sub-frame message (a message is inherently
-// sequential).  The 64-byte blocks are read with 16-byte vector loads when the
-// message start is 16-byte aligned (true for every video size whose N/n is a
-// multiple of 16) and byte loads otherwise; the next block is loaded while
-// the current one is compressed.  Rotations are funnel shifts, the three-input
-// boolean functions map onto LOP3.
+// GPU mapping: a message is inherently sequential, and with n = 32 a frame has
+// only 32 of them, so the time of one message is the time of the frame.  Each
+// message therefore gets two threads in two warps of one CTA: a producer lane
+// loads the 64-byte blocks (16-byte vector loads when the message start is
+// 16-byte aligned, byte loads otherwise), expands the message schedule and
+// stores W[t] + K[t] into a double-buffered shared-memory ring; the consumer
+// lane runs only the 64 compression rounds of the previous block.  The two
+// warps meet at one named barrier per block.  Rotations are funnel shifts,
+// the three-input boolean functions map onto LOP3.
 #include <mutex>
 
 #include "common.cuh"
@@ -82,93 +85,165 @@ __device__ __forceinline__ void block_words(const uint4 q[4], uint32_t w[16]) {
     }
 }
 
-// SHA-256 of len bytes at p (device memory); digest as 8 big-endian-valued words.
-__device__ void sha256_message(const uint8_t *p, uint64_t len, uint32_t out[8]) {
-    ShaState st;
-    st.init();
-    uint64_t full = len >> 6;
-    uint32_t w[16];
-    if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
-        if (full) {
-            uint4 cur[4], nxt[4];
-            load_block16(p, cur);
-            for (uint64_t b = 0; b < full; ++b) {
-                if (b + 1 < full) load_block16(p + 64 * (b + 1), nxt);
-                block_words(cur, w);
-                st.compress(w);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
-            }
-        }
-    } else {
-        for (uint64_t b = 0; b < full; ++b) {
-            const uint8_t *q = p + 64 * b;
-#pragma unroll
-            for (int k = 0; k < 16; ++k)
-                w[k] = ((uint32_t)q[4 * k] << 24) | ((uint32_t)q[4 * k + 1] << 16) |
-                       ((uint32_t)q[4 * k + 2] << 8) | (uint32_t)q[4 * k + 3];
-            st.compress(w);
-        }
-    }
-    // Padding (FIPS 180-4 Sec. 5.1.1): 0x80, zeros, 64-bit big-endian bit length.
-    uint32_t rem = (uint32_t)(len & 63);
-    const uint8_t *tail = p + 64 * full;
-    uint64_t bits = len * 8;
-    uint32_t nblk = (rem + 9 <= 64) ? 1 : 2;
-    for (uint32_t blk = 0; blk < nblk; ++blk) {
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            uint32_t word = 0;
-#pragma unroll
-            for (int byte = 0; byte < 4; ++byte) {
-                uint32_t pos = blk * 64 + 4 * k + byte;
-                uint32_t v = 0;
-                if (pos < rem) v = tail[pos];
-                else if (pos == rem) v = 0x80u;
-                word = (word << 8) | v;
-            }
-            w[k] = word;
-        }
-        if (blk == nblk - 1) {
-            w[14] = (uint32_t)(bits >> 32);
-            w[15] = (uint32_t)bits;
-        }
-        st.compress(w);
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) out[k] = st.h[k];
-}
-
 __device__ __forceinline__ void store_digest(uint8_t *dst, const uint32_t h[8]) {
     uint32_t *d = reinterpret_cast<uint32_t *>(dst);   // 32-byte slots, 4-byte aligned
 #pragma unroll
     for (int k = 0; k < 8; ++k) d[k] = bswap(h[k]);
 }
 
-// One thread per (frame, sub-frame) of a batch.
-__global__ void __launch_bounds__(64) sha_subframes_kernel(const __grid_constant__ Batch b) {
-    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t n = b.n;
-    if (t >= b.count * n) return;
-    const FrameDesc &fd = b.f[t / n];
-    uint32_t i = t % n;
-    uint64_t lo = (uint64_t)(((unsigned __int128)fd.N * i) / n);
-    uint64_t hi = (uint64_t)(((unsigned __int128)fd.N * (i + 1)) / n);
-    uint32_t h[8];
-    sha256_message(fd.src + lo, hi - lo, h);
-    store_digest(fd.part + 32 * i, h);
+constexpr int kMsgPerCta = 32;
+
+// Blocks of a padded message of len bytes (FIPS 180-4 Sec. 5.1.1).
+__device__ __forceinline__ uint64_t padded_blocks(uint64_t len) { return (len >> 6) + ((len & 63) + 9 <= 64 ? 1 : 2); }
+
+// Block b of the padded message (p, len) as 16 big-endian words.  cur holds
+// block b's raw bytes when it is a full block on the aligned path.
+__device__ __forceinline__ void message_block(const uint8_t *p, uint64_t len, uint64_t b, bool aligned16,
+                                              const uint4 cur[4], uint32_t w[16]) {
+    const uint64_t full = len >> 6;
+    if (b < full) {
+        if (aligned16) {
+            block_words(cur, w);
+        } else {
+            const uint8_t *q = p + 64 * b;
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                w[k] = ((uint32_t)q[4 * k] << 24) | ((uint32_t)q[4 * k + 1] << 16) | ((uint32_t)q[4 * k + 2] << 8) |
+                       (uint32_t)q[4 * k + 3];
+        }
+        return;
+    }
+    const uint32_t rem = (uint32_t)(len & 63);
+    const uint32_t blk = (uint32_t)(b - full);           // 0 or 1 within the tail
+    const uint8_t *tail = p + 64 * full;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int byte = 0; byte < 4; ++byte) {
+            const uint32_t pos = blk * 64 + 4 * k + byte;
+            uint32_t v = 0;
+            if (pos < rem) v = tail[pos];
+            else if (pos == rem) v = 0x80u;
+            word = (word << 8) | v;
+        }
+        w[k] = word;
+    }
+    if (b == padded_blocks(len) - 1) {
+        const uint64_t bits = len * 8;
+        w[14] = (uint32_t)(bits >> 32);
+        w[15] = (uint32_t)bits;
+    }
 }
 
+__device__ __forceinline__ void named_barrier_64() {
+    __syncwarp();
+    asm volatile("bar.sync 1, 64;" ::: "memory");
+}
+
+// 32 messages per CTA: warp 0 compresses, warp 1 produces W + K.  Message k of
+// the CTA is (p[k], len[k]); its digest goes to out[k] (32 bytes).
+template <class Locate>
+__device__ void sha_pipeline(Locate locate, uint32_t nmsg) {
+    __shared__ uint32_t wk[2][64][kMsgPerCta];
+    const int lane = threadIdx.x & 31;
+    const bool producer = threadIdx.x >= 32;
+    const uint32_t m = blockIdx.x * kMsgPerCta + lane;
+    const bool active = m < nmsg;
+    const uint8_t *p = nullptr;
+    uint64_t len = 0;
+    uint8_t *out = nullptr;
+    if (active) locate(m, p, len, out);
+    const uint64_t nb = active ? padded_blocks(len) : 0;
+    const uint64_t NB = __reduce_max_sync(0xffffffffu, (unsigned)nb);   // < 2^32 blocks per message
+    if (producer) {
+        const bool al = (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
+        const uint64_t full = len >> 6;
+        uint4 cur[4], nxt[4];
+        if (active && al && full) load_block16(p, cur);
+        for (uint64_t b = 0; b < NB; ++b) {
+            if (b < nb) {
+                if (al && b + 1 < full) load_block16(p + 64 * (b + 1), nxt);
+                uint32_t w[16];
+                message_block(p, len, b, al, cur, w);
+                uint32_t(*dst)[kMsgPerCta] = wk[b & 1];
+#pragma unroll
+                for (int t = 0; t < 64; ++t) {
+                    uint32_t wt;
+                    if (t < 16) {
+                        wt = w[t];
+                    } else {
+                        const uint32_t w15 = w[(t - 15) & 15], w2 = w[(t - 2) & 15];
+                        const uint32_t s0 = rotr(w15, 7) ^ rotr(w15, 18) ^ (w15 >> 3);
+                        const uint32_t s1 = rotr(w2, 17) ^ rotr(w2, 19) ^ (w2 >> 10);
+                        wt = w[t & 15] + s0 + w[(t - 7) & 15] + s1;
+                        w[t & 15] = wt;
+                    }
+                    dst[t][lane] = wt + kK[t];
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
+            }
+            named_barrier_64();                 // block b is ready; block b-1 has been consumed
+        }
+        named_barrier_64();                     // pairs with the consumer's last wait
+    } else {
+        ShaState st;
+        st.init();
+        named_barrier_64();                     // block 0 ready
+        for (uint64_t b = 0; b < NB; ++b) {
+            if (b < nb) {
+                const uint32_t(*src)[kMsgPerCta] = wk[b & 1];
+                uint32_t a = st.h[0], bb = st.h[1], c = st.h[2], d = st.h[3];
+                uint32_t e = st.h[4], f = st.h[5], g = st.h[6], hh = st.h[7];
+#pragma unroll
+                for (int t = 0; t < 64; ++t) {
+                    const uint32_t S1 = rotr(e, 6) ^ rotr(e, 11) ^ rotr(e, 25);
+                    const uint32_t ch = (e & f) ^ (~e & g);
+                    const uint32_t t1 = hh + S1 + ch + src[t][lane];
+                    const uint32_t S0 = rotr(a, 2) ^ rotr(a, 13) ^ rotr(a, 22);
+                    const uint32_t mj = (a & bb) ^ (a & c) ^ (bb & c);
+                    hh = g; g = f; f = e; e = d + t1;
+                    d = c; c = bb; bb = a; a = t1 + S0 + mj;
+                }
+                st.h[0] += a; st.h[1] += bb; st.h[2] += c; st.h[3] += d;
+                st.h[4] += e; st.h[5] += f; st.h[6] += g; st.h[7] += hh;
+            }
+            named_barrier_64();                 // done with block b; block b+1 ready
+        }
+        if (active) store_digest(out, st.h);
+    }
+}
+
+// Sub-frame messages of a batch: message m is sub-frame m % n of frame m / n.
+__global__ void __launch_bounds__(64) sha_subframes_kernel(const __grid_constant__ Batch b) {
+    const uint32_t n = b.n;
+    sha_pipeline(
+        [&](uint32_t m, const uint8_t *&p, uint64_t &len, uint8_t *&out) {
+            const FrameDesc &fd = b.f[m / n];
+            const uint32_t i = m % n;
+            const uint64_t lo = (uint64_t)(((unsigned __int128)fd.N * i) / n);
+            const uint64_t hi = (uint64_t)(((unsigned __int128)fd.N * (i + 1)) / n);
+            p = fd.src + lo;
+            len = hi - lo;
+            out = fd.part + 32ull * i;
+        },
+        b.count * n);
+}
+
+// `count` buffers of nbytes laid end to end, n sub-frames each.
 __global__ void __launch_bounds__(64) sha_plain_kernel(const uint8_t *data, uint64_t nbytes, uint32_t n,
                                                        uint32_t count, uint8_t *part) {
-    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= count * n) return;
-    uint32_t k = t / n, i = t % n;
-    uint64_t lo = (uint64_t)(((unsigned __int128)nbytes * i) / n);
-    uint64_t hi = (uint64_t)(((unsigned __int128)nbytes * (i + 1)) / n);
-    uint32_t h[8];
-    sha256_message(data + k * nbytes + lo, hi - lo, h);
-    store_digest(part + 32ull * t, h);
+    sha_pipeline(
+        [&](uint32_t m, const uint8_t *&p, uint64_t &len, uint8_t *&out) {
+            const uint32_t k = m / n, i = m % n;
+            const uint64_t lo = (uint64_t)(((unsigned __int128)nbytes * i) / n);
+            const uint64_t hi = (uint64_t)(((unsigned __int128)nbytes * (i + 1)) / n);
+            p = data + k * nbytes + lo;
+            len = hi - lo;
+            out = part + 32ull * m;
+        },
+        count * n);
 }
 
 // digest[k] = XOR over i of part[k*n + i]; one warp per buffer, lane = byte-word.
@@ -215,20 +290,17 @@ cudaError_t noalloc_scratch(uint8_t **out) {
 }
 
 cudaError_t launch_sha_subframes(const Batch &b, cudaStream_t s) {
-    uint32_t threads = b.count * b.n;
-    if (!threads) return cudaSuccess;
-    // Small blocks spread the (few, long) message threads over many SMs.
-    uint32_t bs = threads >= 152u * 64u ? 64 : 32;
-    sha_subframes_kernel<<<(threads + bs - 1) / bs, bs, 0, s>>>(b);
+    const uint32_t msgs = b.count * b.n;
+    if (!msgs) return cudaSuccess;
+    sha_subframes_kernel<<<(msgs + kMsgPerCta - 1) / kMsgPerCta, 64, 0, s>>>(b);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sha_plain(const uint8_t *data, uint64_t nbytes, uint32_t n, uint32_t count, uint8_t *part,
                              cudaStream_t s) {
-    uint32_t threads = count * n;
-    if (!threads) return cudaSuccess;
-    uint32_t bs = 32;
-    sha_plain_kernel<<<(threads + bs - 1) / bs, bs, 0, s>>>(data, nbytes, n, count, part);
+    const uint32_t msgs = count * n;
+    if (!msgs) return cudaSuccess;
+    sha_plain_kernel<<<(msgs + kMsgPerCta - 1) / kMsgPerCta, 64, 0, s>>>(data, nbytes, n, count, part);
     return cudaGetLastError();
 }
 
