@@ -46,6 +46,11 @@ HBM_PEAK_FALLBACK = 6800.0
 # 2.07 GHz maximum SM clock.
 FP64_PEAK_TOPS = 1.684 * 152 * 2.07e9 / 1e12
 RK4_FP64_OPS = 104      # per chain step: 4 x 13 (Eq. 1) + 3 x 8 (stages) + 4 x 7 (combination)
+# DRAM bytes (read + write) per 1080p frame of one launch, from the ncu capture summarised in
+# profiles/ncu_hot_kernels_clip1080p_4frames.md (4 frames per launch, scaled by frames);
+# None where the kernel changed after that capture.
+TRAFFIC_PER_FRAME = {"keystream": 30720 / 4, "encrypt": (49876992 + 1781248) / 4, "sha": 24926464 / 4,
+                     "master": 18944 / 4, "decrypt": None}
 
 
 def parse():
@@ -270,6 +275,7 @@ def run_ours(args):
         barrier()
     launches = fhd.fhd_launch_count() - l0
     ms_total = ev0.elapsed_time(ev1)
+    from paper_2505_07158_gb300 import replicas
     prof = {}
     for c in (enc, dec):
         for k, (ms, n) in c.profile_read().items():
@@ -278,12 +284,9 @@ def run_ours(args):
             a[1] += n
     enc.profile(False)
     dec.profile(False)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = replicas.max_over_ranks(ms_total, device=dev)
     ms_step = ms_total / args.steps
-    value = world * FRAMES / (ms_step / 1000.0)
+    value = replicas.job_throughput(FRAMES * args.steps, ms_total, world)
 
     # ---- end to end through the public API with pinned host buffers
     host_out = torch.empty_like(host).pin_memory()
@@ -308,10 +311,7 @@ def run_ours(args):
     ev1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max(ev0.elapsed_time(ev1), 1000 * (time.perf_counter() - t0)) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = replicas.max_over_ranks(e2e_ms, device=dev)
     e2e_ok = torch.equal(host_out, host)
 
     # ---- plain path: one call per frame (the paper's per-frame loop)
@@ -341,15 +341,18 @@ def run_ours(args):
     def fp64_roof(k, steps_per_launch):
         ms = kern[k]["avg_launch_ms"]
         ach = steps_per_launch * RK4_FP64_OPS / (ms / 1000.0) / 1e12
+        tpf = TRAFFIC_PER_FRAME.get(k)
         return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TOPS, "traffic": None,
+                "frac": ach / FP64_PEAK_TOPS, "traffic": tpf * per_step_frames if tpf is not None else None,
                 "peak_source": "binary64 pipe: measured 1.684 lane-op/clk/SM x 152 SMs x 2.07 GHz",
                 "per_launch_units": f"{steps_per_launch} RK4 chain steps x {RK4_FP64_OPS} binary64 ops"}
 
     def hbm_roof(k):
         ms = kern[k]["avg_launch_ms"]
         ach = 2 * N * per_step_frames / (ms / 1000.0) / 1e9
-        return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+        tpf = TRAFFIC_PER_FRAME.get(k)
+        return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": tpf * per_step_frames if tpf is not None else None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback",
                 "per_launch_units": f"{per_step_frames} frames x 2N bytes (one frame read + one frame written)"}
 
