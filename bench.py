@@ -63,7 +63,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
     ap.add_argument("--frames", type=int, default=30, help="frames per step (30 = the clip; smaller for ncu)")
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="length of each serving run (60 s = full config)")
-    ap.add_argument("--no-extras", action="store_true", help="skip the mixed-batch and serving measurements")
+    ap.add_argument("--no-extras", action="store_true", help="skip the mixed-batch, serving and stress measurements")
+    ap.add_argument("--no-stress", action="store_true", help="skip the 256 x 8K stress round trip")
     return ap.parse_args()
 
 
@@ -483,7 +484,87 @@ def run_extras(args, rank, fhd, torch):
     out["serving"] = {"workload": f"32 streams, resolutions uniform over 640x480 / 1280x720 / 1920x1080 x3, "
                                   f"Poisson arrivals, 20 GB HBM budget, {args.serve_seconds:g} s per rate "
                                   f"(plain: one frame per call, one CUDA stream)", **serve}
+    del pool
+    torch.cuda.empty_cache()
+    if not args.no_stress:
+        out["stress_8k"] = run_stress(rank, fhd, torch)
     return out
+
+
+def run_stress(rank, fhd, torch, frames=256):
+    """256 frames of 7680x4320x3 (uniform and gradient+noise halves, generated on the device), one stream,
+    encrypt then decrypt in one call each; round trip, sampled digests vs the oracle, permutation rooflines."""
+    import oracle
+    from paper_2505_07158_gb300 import autotune
+    dev = torch.device("cuda", torch.cuda.current_device())
+    h, w, C = 4320, 7680, 3
+    autotune.tune([(h, w, C)])
+    g = torch.Generator(device=dev)
+    g.manual_seed(8000 + rank)
+    src = []
+    ii = torch.arange(h, device=dev, dtype=torch.float32)[:, None]
+    jj = torch.arange(w, device=dev, dtype=torch.float32)[None, :]
+    for t in range(frames):
+        if t < frames // 2:
+            src.append(torch.randint(0, 256, (h, w, C), dtype=torch.uint8, device=dev, generator=g))
+        else:
+            chans = []
+            for c in range(C):
+                a = (c + 1) / (C + 1)
+                base = 255.0 * (a * ii / h + (1 - a) * torch.remainder(jj + 2 * t, w) / w)
+                noisy = base + 8.0 * torch.randn((h, w), device=dev, generator=g)
+                chans.append(torch.clamp(torch.round(noisy), 0, 255).to(torch.uint8))
+            src.append(torch.stack(chans, dim=-1).contiguous())
+    key = si.key(9000 + rank)
+    enc, dec = fhd.Cipher(key, n_workers=N_WORKERS), fhd.Cipher(key, n_workers=N_WORKERS)
+    sid, rid = enc.open_stream(), dec.open_stream()
+    E = [torch.empty_like(x) for x in src]
+    R = [torch.empty_like(x) for x in src]
+    Hd = torch.empty((frames, 32), dtype=torch.uint8, device=dev)
+    # scratch for the batch is sized by a first call on a throwaway stream of the same handles
+    tmp_s, tmp_r = enc.open_stream(), dec.open_stream()
+    enc.encrypt_frames([(tmp_s, src[k], E[k], Hd[k]) for k in range(min(frames, 128))])
+    dec.decrypt_frames([(tmp_r, E[k], R[k], Hd[k]) for k in range(min(frames, 128))])
+    torch.cuda.synchronize()
+    enc.profile(True)
+    dec.profile(True)
+    a, b, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    a.record()
+    enc.encrypt_frames([(sid, src[k], E[k], Hd[k]) for k in range(frames)])
+    b.record()
+    dec.decrypt_frames([(rid, E[k], R[k], Hd[k]) for k in range(frames)])
+    c2.record()
+    c2.synchronize()
+    pe, pd = enc.profile_read(), dec.profile_read()
+    enc.profile(False)
+    dec.profile(False)
+    ok = all(torch.equal(R[k], src[k]) for k in range(frames))
+    N = h * w * C
+    digest_ok = all(bytes(Hd[k].cpu().numpy()) == oracle.frame_digest(src[k].cpu().numpy(), N_WORKERS)
+                    for k in (0, frames - 1))
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", HBM_PEAK_FALLBACK)
+    enc_ms, dec_ms = a.elapsed_time(b), b.elapsed_time(c2)
+    perm_e, perm_d = pe["encrypt"][0], pd["decrypt"][0]
+    res = {"workload": f"{frames} x 7680x4320x3 uint8 (uniform / gradient+noise halves, device-generated), one stream, "
+                       "encrypt then decrypt, one call each",
+           "round_trip_ok": bool(ok), "sampled_digests_match_oracle": bool(digest_ok),
+           "encrypt_ms": enc_ms, "decrypt_ms": dec_ms,
+           "frames_per_s_round_trip": frames / ((enc_ms + dec_ms) / 1000.0),
+           "kernel_ms": {"encrypt": {k: v[0] for k, v in pe.items() if v[1]},
+                         "decrypt": {k: v[0] for k, v in pd.items() if v[1]}},
+           "permute_encrypt_roofline": {"bound": "hbm", "achieved": 2 * N * frames / (perm_e / 1000.0) / 1e9,
+                                        "peak": hbm, "unit": "GB/s",
+                                        "frac": 2 * N * frames / (perm_e / 1000.0) / 1e9 / hbm},
+           "permute_decrypt_roofline": {"bound": "hbm", "achieved": 2 * N * frames / (perm_d / 1000.0) / 1e9,
+                                        "peak": hbm, "unit": "GB/s",
+                                        "frac": 2 * N * frames / (perm_d / 1000.0) / 1e9 / hbm},
+           "strip_width": fhd.fhd_strip_width(h, w, C)}
+    enc.close()
+    dec.close()
+    del src, E, R
+    torch.cuda.empty_cache()
+    return res
 
 
 def main():
