@@ -13,7 +13,7 @@
  *
  * Conventions for every entry point:
  *  - Frames are H x W x C uint8, C-contiguous, channel fastest (HWC), with
- *    1 <= C <= 4, 1 <= H <= 12288, 1 <= W <= 32768.  Frame, digest, D and B pointers are
+ *    1 <= C <= 4, 1 <= H <= 12288, 1 <= W <= 16384.  Frame, digest, D and B pointers are
  *    DEVICE pointers owned by the caller; the library never frees them.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream).  Work is enqueued asynchronously; a return of FHD_OK means the
@@ -50,7 +50,7 @@ enum {
     FHD_ERR_TOO_LARGE = -8    /* request exceeds a documented maximum */
 };
 
-#define FHD_MAX_DIM 32768u    /* frame width limit */
+#define FHD_MAX_DIM 16384u    /* frame width limit: a band of whole rows lives in shared memory */
 #define FHD_MAX_HEIGHT 12288u /* frame height limit: a full-height strip lives in shared memory */
 #define FHD_MAX_WORKERS 1024u
 #define FHD_STATE_BYTES 48u /* x, y, z, w, gamma (binary64) + frame counter (uint64) */

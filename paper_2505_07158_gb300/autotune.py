@@ -1,7 +1,7 @@
 """Autotuner for the strip width of the fused permutation kernels.
 
-The confusion + XOR kernels give each CTA a full-height strip of P pixel
-columns held in shared memory.  Wide strips amortise the per-row gather
+The column pass of the confusion + XOR gives each CTA a full-height strip of
+P pixel columns held in shared memory.  Wide strips amortise the per-row gather
 overhead; narrow strips let two or more CTAs share an SM and hide memory
 latency.  The best P depends on the frame shape, so it is measured: for each
 (height, width, channels) every power-of-two P whose strip fits shared memory
@@ -29,7 +29,7 @@ def candidates(h: int, w: int, C: int):
     out = []
     P = 1
     while P <= 128:
-        smem = ((h * (P + 1) * C + 15) & ~15) + ((2 * C * h + 15) & ~15)
+        smem = (h * P * C + 15) & ~15
         if smem <= SMEM_LIMIT and (P == 1 or P // 2 < w):
             out.append(P)
         P *= 2

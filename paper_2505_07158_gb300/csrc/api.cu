@@ -148,6 +148,7 @@ bool check_dims(uint32_t h, uint32_t w, uint32_t C, std::string &why) {
     if (C > 4) { why = "channels must be 1..4"; return false; }
     if (h > FHD_MAX_HEIGHT || w > FHD_MAX_DIM) { why = "frame exceeds FHD_MAX_HEIGHT rows or FHD_MAX_DIM columns"; return false; }
     if (fhd::strip_width(h, w, C) == 0) { why = "frame too tall for the shared-memory strip"; return false; }
+    if (fhd::row_smem_bytes(w, C, 1) > 232448) { why = "frame rows too wide for the shared-memory row band"; return false; }
     return true;
 }
 
@@ -240,9 +241,10 @@ int ensure_scratch(fhd_cipher *c, cudaStream_t s, size_t need, uint8_t **out) {
     return FHD_OK;
 }
 
-// Per-frame scratch: n sub-frame digests, 2n LHCS_m iterates, D, B.
+// Per-frame scratch: n sub-frame digests, 2n LHCS_m iterates, D, B, and the
+// frame between the two permutation passes.
 uint64_t frame_scratch(uint32_t n, uint32_t h, uint32_t w, uint32_t C) {
-    return align16(32ull * n) + align16(64ull * n) + align16(2ull * C * (h + w)) + align16((uint64_t)h * w * C);
+    return align16(32ull * n) + align16(64ull * n) + align16(2ull * C * (h + w)) + 2 * align16((uint64_t)h * w * C);
 }
 
 int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream, bool encrypt,
@@ -282,7 +284,7 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
         uint8_t *p = nullptr;
         int rc = ensure_scratch(c, s, need, &p);
         if (rc != FHD_OK) return rc;
-        uint32_t ctas = 0;
+        uint32_t ctas = 0, rctas = 0;
         for (uint32_t k = 0; k < m; ++k) {
             const fhd_frame &f = frames[base + k];
             FrameDesc &d = b.f[k];
@@ -299,11 +301,16 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
             d.IR = reinterpret_cast<double *>(p); p += align16(64ull * c->n);
             d.D = reinterpret_cast<uint16_t *>(p); p += align16(2ull * d.C * (d.h + d.w));
             d.B = p; p += align16(d.N);
+            d.G = p; p += align16(d.N);
             d.P = fhd::strip_width(d.h, d.w, d.C);
             d.cta0 = ctas;
             ctas += fhd::permute_strips(d.w, d.P);
+            d.RB = fhd::row_band(d.w, d.C);
+            d.rcta0 = rctas;
+            rctas += (d.h + d.RB - 1) / d.RB;
         }
         b.perm_ctas = ctas;
+        b.row_ctas = rctas;
         // Group frames by stream (stable): each master CTA walks one stream in order.
         std::vector<uint32_t> seen;
         uint32_t pos = 0;
@@ -597,8 +604,14 @@ static int permute_one(const uint8_t *src, uint8_t *dst, uint32_t height, uint32
     d.P = fhd::strip_width(height, width, channels);
     d.cta0 = 0;
     b.perm_ctas = fhd::permute_strips(width, d.P);
-    e = timed(nullptr, encrypt ? FHD_K_ENCRYPT : FHD_K_DECRYPT, (cudaStream_t)stream,
-              [&] { return fhd::launch_permute(b, encrypt, (cudaStream_t)stream); });
+    d.RB = fhd::row_band(width, channels);
+    d.rcta0 = 0;
+    b.row_ctas = (height + d.RB - 1) / d.RB;
+    cudaStream_t s = (cudaStream_t)stream;
+    e = cudaMallocAsync(&d.G, N, s);
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+    e = timed(nullptr, encrypt ? FHD_K_ENCRYPT : FHD_K_DECRYPT, s, [&] { return fhd::launch_permute(b, encrypt, s); });
+    cudaFreeAsync(d.G, s);
     if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("permute launch: ") + cudaGetErrorString(e));
     return FHD_OK;
 }

