@@ -211,6 +211,14 @@ __global__ void __launch_bounds__(kStripThreads, 1) strip_kernel(const __grid_co
 // Row pass over a band of RB whole rows.  Encrypt: G = left rotation of each
 // channel row of F by s_h bits.  Decrypt: output = right rotation of each
 // channel row of G by s_h bits.
+//
+// Interleaved RGB rows with w % 4 == 0 take a planar route: each group of 4
+// pixels (three 32-bit words) is split into one word per channel with
+// __byte_perm, a channel plane of w/4 words (plus one wrapped word) is
+// rotated four bytes at a time -- the five source bytes sit in two adjacent
+// words, so one 64-to-32-bit funnel shift by 8*(byte offset) + bit shift gives
+// the four rotated bytes -- and the words are interleaved back.  Other shapes
+// take the byte-wise route.
 template <bool kEnc>
 __global__ void __launch_bounds__(kRowThreads) row_kernel(const __grid_constant__ Batch b) {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -222,9 +230,10 @@ __global__ void __launch_bounds__(kRowThreads) row_kernel(const __grid_constant_
     const uint32_t pitch = (rowB + 15) & ~15u;
     const uint8_t *src = (kEnc ? fd.src : fd.G) + (uint64_t)i0 * rowB;
     uint8_t *dst = (kEnc ? fd.G : fd.dst) + (uint64_t)i0 * rowB;
-    uint8_t *In = smem;
-    uint8_t *Out = smem + (size_t)RB * pitch;
-    uint32_t *sh = reinterpret_cast<uint32_t *>(smem + 2 * (size_t)RB * pitch);   // [r * C + c]
+    uint8_t *In = smem;                                          // RB rows
+    uint8_t *Out = smem + (size_t)RB * pitch;                    // RB rows (byte-wise route)
+    // shifts after the input rows and two plane buffers of RB * (pitch + 16) bytes each
+    uint32_t *sh = reinterpret_cast<uint32_t *>(smem + 3 * (size_t)RB * pitch + 32 * (size_t)RB);   // [r * C + c]
     const FastMod modW8(8 * w);
 
     // ---- load the band (rows are contiguous in global memory)
@@ -248,7 +257,59 @@ __global__ void __launch_bounds__(kRowThreads) row_kernel(const __grid_constant_
     }
     __syncthreads();
 
-    // ---- four output bytes of one channel per thread, one funnel shift each
+    if (C == 3 && (w & 3) == 0 && v16) {
+        // ---- planar route.  Planes: [r][c][W4 + 1] words (RB * (rowB + 12)
+        // bytes per set), input planes after the rows, output planes after them.
+        const uint32_t W4 = w >> 2, PW = W4 + 1;
+        uint32_t *Pin = reinterpret_cast<uint32_t *>(smem + (size_t)RB * pitch);
+        uint32_t *Pout = Pin + (size_t)RB * 3 * PW;
+        const uint32_t groups = nr * W4;
+        for (uint32_t k = threadIdx.x; k < groups; k += blockDim.x) {
+            const uint32_t r = k / W4, g = k - r * W4;
+            const uint32_t *wp = reinterpret_cast<const uint32_t *>(In + (size_t)r * pitch) + 3 * g;
+            const uint32_t w0 = wp[0], w1 = wp[1], w2 = wp[2];
+            uint32_t *pl = Pin + (size_t)r * 3 * PW;
+            const uint32_t R = __byte_perm(__byte_perm(w0, w1, 0x0630), w2, 0x5210);
+            const uint32_t G = __byte_perm(__byte_perm(w0, w1, 0x0741), w2, 0x6210);
+            const uint32_t B = __byte_perm(__byte_perm(w0, w1, 0x0052), w2, 0x7410);
+            pl[g] = R; pl[PW + g] = G; pl[2 * PW + g] = B;
+            if (g == 0) { pl[W4] = R; pl[PW + W4] = G; pl[2 * PW + W4] = B; }   // wrapped word
+        }
+        __syncthreads();
+        const uint32_t words = nr * 3 * W4;
+        for (uint32_t k = threadIdx.x; k < words; k += blockDim.x) {
+            const uint32_t rc = k / W4, m = k - rc * W4;
+            const uint32_t s = sh[rc];
+            const uint32_t a = s >> 3, rr = s & 7;
+            // first source byte of the plane: 4m - a - 1 (encrypt) or 4m + a (decrypt), mod w
+            int si = kEnc ? (int)(4 * m) - (int)a - 1 : (int)(4 * m + a);
+            if (si < 0) si += (int)w;
+            if (si >= (int)w) si -= (int)w;
+            const uint32_t u = (uint32_t)si >> 2, o = (uint32_t)si & 3;
+            const uint32_t *pl = Pin + (size_t)rc * PW;
+            Pout[(size_t)rc * PW + m] = __funnelshift_rc(pl[u], pl[u + 1], kEnc ? 8 * o + 8 - rr : 8 * o + rr);
+        }
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < groups; k += blockDim.x) {
+            const uint32_t r = k / W4, g = k - r * W4;
+            const uint32_t *pl = Pout + (size_t)r * 3 * PW;
+            const uint32_t R = pl[g], G = pl[PW + g], B = pl[2 * PW + g];
+            uint32_t *wp = reinterpret_cast<uint32_t *>(In + (size_t)r * pitch) + 3 * g;
+            wp[0] = __byte_perm(__byte_perm(R, G, 0x1040), B, 0x3410);
+            wp[1] = __byte_perm(__byte_perm(G, R, 0x2601), B, 0x3250);
+            wp[2] = __byte_perm(__byte_perm(B, R, 0x3072), G, 0x3710);
+        }
+        __syncthreads();
+        const uint32_t nvr = rowB / 16;
+        for (uint32_t k = threadIdx.x; k < nr * nvr; k += blockDim.x) {
+            const uint32_t r = k / nvr, v = k - r * nvr;
+            *reinterpret_cast<uint4 *>(dst + (uint64_t)r * rowB + 16 * v) =
+                *reinterpret_cast<const uint4 *>(In + (size_t)r * pitch + 16 * v);
+        }
+        return;
+    }
+
+    // ---- byte-wise route: four output bytes of one channel per thread, one funnel shift each
     const uint32_t nq = (w + 3) >> 2;
     for (uint32_t rc = 0; rc < nr * C; ++rc) {
         const uint32_t r = rc / C, c = rc - r * C;
@@ -307,15 +368,17 @@ size_t strip_smem_bytes(uint32_t h, uint32_t P, uint32_t C) { return ((size_t)h 
 
 uint32_t row_band(uint32_t w, uint32_t C) {
     const size_t pitch = ((size_t)w * C + 15) & ~(size_t)15;
-    size_t rb = kRowSmemTarget / (2 * pitch + 64);
+    size_t rb = kRowSmemTarget / (3 * pitch + 32 + 16);
     if (rb < 1) rb = 1;
     if (rb > 16) rb = 16;
     return (uint32_t)rb;
 }
 
+// Three row-sized buffers per row (input, then planes in and out, or the
+// byte-wise output) and the row shifts.
 size_t row_smem_bytes(uint32_t w, uint32_t C, uint32_t RB) {
     const size_t pitch = ((size_t)w * C + 15) & ~(size_t)15;
-    return 2 * (size_t)RB * pitch + 4 * (size_t)RB * C;
+    return 3 * (size_t)RB * pitch + 32 * (size_t)RB + 4 * (size_t)RB * C;
 }
 
 uint32_t permute_strips(uint32_t w, uint32_t P) { return (w + P - 1) / P; }
