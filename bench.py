@@ -486,9 +486,41 @@ def run_extras(args, rank, fhd, torch):
                                   f"(plain: one frame per call, one CUDA stream)", **serve}
     del pool
     torch.cuda.empty_cache()
+    out["worker_count_sweep"] = run_n_sweep(rank, fhd, torch)
     if not args.no_stress:
         out["stress_8k"] = run_stress(rank, fhd, torch)
     return out
+
+
+def run_n_sweep(rank, fhd, torch, ns=(32, 128, 512), steps=3):
+    """The same 30-frame 1080p round trip with other worker counts n.  n is a protocol parameter both ends
+    must share (Sec. V): more workers mean more, shorter sub-frame messages and chaotic chains."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    clip = torch.from_numpy(si.clip(FRAMES, HGT, WID, CH, seed=rank + 3)).to(dev)
+    res = {}
+    for n in ns:
+        key = si.key(700 + n)
+        enc, dec = fhd.Cipher(key, n_workers=n), fhd.Cipher(key, n_workers=n)
+        sid, rid = enc.open_stream(), dec.open_stream()
+        E = torch.empty_like(clip)
+        R = torch.empty_like(clip)
+        H = torch.empty((FRAMES, 32), dtype=torch.uint8, device=dev)
+        ei = [(sid, clip[t], E[t], H[t]) for t in range(FRAMES)]
+        di = [(rid, E[t], R[t], H[t]) for t in range(FRAMES)]
+        enc.encrypt_frames(ei); dec.decrypt_frames(di)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            enc.encrypt_frames(ei)
+            dec.decrypt_frames(di)
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b) / steps
+        res[str(n)] = {"frames_per_s": FRAMES / (ms / 1000.0), "ms_per_step": ms,
+                       "round_trip_ok": bool(torch.equal(R, clip))}
+        enc.close(); dec.close()
+    return {"workload": "30-frame 1080p clip round trip (as the headline) with n workers", **res}
 
 
 def run_stress(rank, fhd, torch, frames=256):

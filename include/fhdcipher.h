@@ -127,6 +127,14 @@ int decrypt_frames_ex(fhd_cipher *c, uint32_t count, const fhd_frame *frames, vo
 int cipher_reserve(fhd_cipher *c, void *stream, uint64_t bytes);
 uint64_t fhd_frame_scratch_bytes(uint32_t n_workers, uint32_t height, uint32_t width, uint32_t channels);
 
+/* Receiver-side integrity check (the paper transmits the digests with the
+ * frames, Sec. V): recompute H over frames[i].dst (the decrypted frames) with
+ * the cipher's n and compare it with frames[i].digest; ok[i] (device, one
+ * byte per frame) becomes 1 when they match and 0 otherwise.  A corrupted
+ * ciphertext, digest or chaining state gives 0 with overwhelming probability.
+ * Does not touch any stream's chaining state. */
+int cipher_verify_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, uint8_t *ok, void *stream);
+
 /* Copy a stream's chaining state (FHD_STATE_BYTES bytes) to host memory
  * after synchronising the handle's last CUDA stream; for exact resume. */
 int cipher_export_state(fhd_cipher *c, uint32_t stream_id, void *buf, size_t len);

@@ -34,7 +34,7 @@ EXPORTS = (
     "cipher_last_error", "cipher_destroy", "fhd_frame_digest", "fhd_master", "fhd_keystream",
     "fhd_permute_encrypt", "fhd_permute_decrypt", "fhd_strip_width", "fhd_set_strip_width", "fhd_version",
     "cipher_profile", "cipher_profile_read", "fhd_launch_count", "encrypt_frames_ex", "decrypt_frames_ex",
-    "cipher_reserve", "fhd_frame_scratch_bytes", "fhd_frame_digest_noalloc",
+    "cipher_reserve", "fhd_frame_scratch_bytes", "fhd_frame_digest_noalloc", "cipher_verify_frames",
 )
 KERNEL_KINDS = ("sha", "master", "keystream", "encrypt", "decrypt")
 
@@ -96,6 +96,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "encrypt_frames_ex": (i32, [P, u32, P, P, P, u32, P]),
             "decrypt_frames_ex": (i32, [P, u32, P, P, P, u32, P]),
             "cipher_reserve": (i32, [P, P, u64]),
+            "cipher_verify_frames": (i32, [P, u32, P, P, P]),
             "fhd_frame_scratch_bytes": (u64, [u32, u32, u32, u32]),
         }
         for name, (res, args) in sig.items():
@@ -224,6 +225,14 @@ class Cipher:
         """items: (stream_id, src, dst, digest) tuples; digest (32 B) is read."""
         lib = load()
         self._run(lib.decrypt_frames, lib.decrypt_frames_ex, items, stream, master_event, list(wait_events))
+
+    def verify_frames(self, items: Iterable, stream=None) -> torch.Tensor:
+        """Receiver-side check: 1 per frame whose decrypted ``dst`` re-hashes to its ``digest``."""
+        arr, n = self._frames(items)
+        ok = torch.zeros(max(n, 1), dtype=torch.uint8, device=torch.device("cuda", torch.cuda.current_device()))
+        _check(load().cipher_verify_frames(self._handle(), n, arr, ctypes.c_void_p(ok.data_ptr()),
+                                           _stream_ptr(stream)), self._h)
+        return ok[:n]
 
     def reserve(self, nbytes: int, stream=None):
         """Pre-size this CUDA stream's scratch so later calls on it never allocate."""

@@ -411,6 +411,45 @@ int decrypt_frames_ex(fhd_cipher *c, uint32_t count, const fhd_frame *frames, vo
     return run_frames(c, count, frames, stream, false, wait_events, n_wait, (cudaEvent_t)master_done);
 }
 
+int cipher_verify_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, uint8_t *ok, void *stream) {
+    if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
+    if (count == 0) return FHD_OK;
+    if (!frames || !ok) return fail(c, FHD_ERR_INVALID_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (uint32_t k = 0; k < count; ++k) {
+        const fhd_frame &f = frames[k];
+        std::string why;
+        if (!f.dst || !f.digest) return fail(c, FHD_ERR_INVALID_ARG, "frame " + std::to_string(k) + ": null pointer");
+        if (!check_dims(f.height, f.width, f.channels, why)) return fail(c, FHD_ERR_INVALID_ARG, why);
+    }
+    static thread_local Batch b;
+    for (uint32_t base = 0; base < count; base += fhd::kMaxBatch) {
+        const uint32_t m = count - base < (uint32_t)fhd::kMaxBatch ? count - base : (uint32_t)fhd::kMaxBatch;
+        std::memset(&b, 0, sizeof b);
+        b.count = m;
+        b.n = c->n;
+        uint8_t *p = nullptr;
+        int rc = ensure_scratch(c, s, (uint64_t)m * 32ull * c->n, &p);
+        if (rc != FHD_OK) return rc;
+        for (uint32_t k = 0; k < m; ++k) {
+            const fhd_frame &f = frames[base + k];
+            FrameDesc &d = b.f[k];
+            d.dst = f.dst;
+            d.digest = f.digest;
+            d.h = f.height;
+            d.w = f.width;
+            d.C = f.channels;
+            d.N = (uint64_t)f.height * f.width * f.channels;
+            d.part = p + 32ull * c->n * k;
+            d.slot = base + k;   // index into ok[]
+        }
+        cudaError_t e = timed(c, FHD_K_SHA, s, [&] { return fhd::launch_verify(b, ok, s); });
+        if (e != cudaSuccess) return cuda_fail(c, e, "verify launch");
+    }
+    c->last_stream = s;
+    return FHD_OK;
+}
+
 int cipher_reserve(fhd_cipher *c, void *stream, uint64_t bytes) {
     if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
     uint8_t *p = nullptr;

@@ -61,6 +61,7 @@ enum : unsigned {
 
 // Launchers (one per kernel family); each returns the launch error.
 cudaError_t launch_sha_subframes(const Batch &b, cudaStream_t s);
+cudaError_t launch_verify(const Batch &b, uint8_t *ok, cudaStream_t s);   // ok[f.slot] per frame
 cudaError_t launch_sha_plain(const uint8_t *data, uint64_t nbytes, uint32_t n, uint32_t count,
                              uint8_t *part, cudaStream_t s);
 cudaError_t launch_fold(const uint8_t *part, uint32_t n, uint32_t count, uint8_t *digest, cudaStream_t s);

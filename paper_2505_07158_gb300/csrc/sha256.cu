@@ -246,6 +246,39 @@ __global__ void __launch_bounds__(64) sha_plain_kernel(const uint8_t *data, uint
         count * n);
 }
 
+// Sub-frame messages of the decrypted frames (dst) of a batch, for the
+// receiver-side check; digests go to part (n per frame).
+__global__ void __launch_bounds__(64) sha_dst_kernel(const __grid_constant__ Batch b) {
+    const uint32_t n = b.n;
+    sha_pipeline(
+        [&](uint32_t m, const uint8_t *&p, uint64_t &len, uint8_t *&out) {
+            const FrameDesc &fd = b.f[m / n];
+            const uint32_t i = m % n;
+            const uint64_t lo = (uint64_t)(((unsigned __int128)fd.N * i) / n);
+            const uint64_t hi = (uint64_t)(((unsigned __int128)fd.N * (i + 1)) / n);
+            p = fd.dst + lo;
+            len = hi - lo;
+            out = fd.part + 32ull * i;
+        },
+        b.count * n);
+}
+
+// ok[k] = (XOR over i of frame k's sub-frame digests) == frame k's digest.
+__global__ void verify_kernel(const __grid_constant__ Batch b, uint8_t *ok) {
+    const uint32_t k = blockIdx.x, lane = threadIdx.x;
+    if (k >= b.count) return;
+    const FrameDesc &fd = b.f[k];
+    uint32_t diff = 0;
+    if (lane < 8) {
+        const uint32_t *p = reinterpret_cast<const uint32_t *>(fd.part);
+        uint32_t acc = 0;
+        for (uint32_t i = 0; i < b.n; ++i) acc ^= p[8 * i + lane];
+        diff = acc ^ reinterpret_cast<const uint32_t *>(fd.digest)[lane];
+    }
+    diff = __reduce_or_sync(0xffffffffu, diff);
+    if (lane == 0) ok[fd.slot] = diff == 0 ? 1 : 0;
+}
+
 // digest[k] = XOR over i of part[k*n + i]; one warp per buffer, lane = byte-word.
 __global__ void fold_kernel(const uint8_t *part, uint32_t n, uint32_t count, uint8_t *digest) {
     uint32_t k = blockIdx.x;
@@ -293,6 +326,16 @@ cudaError_t launch_sha_subframes(const Batch &b, cudaStream_t s) {
     const uint32_t msgs = b.count * b.n;
     if (!msgs) return cudaSuccess;
     sha_subframes_kernel<<<(msgs + kMsgPerCta - 1) / kMsgPerCta, 64, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_verify(const Batch &b, uint8_t *ok, cudaStream_t s) {
+    const uint32_t msgs = b.count * b.n;
+    if (!msgs) return cudaSuccess;
+    sha_dst_kernel<<<(msgs + kMsgPerCta - 1) / kMsgPerCta, 64, 0, s>>>(b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    verify_kernel<<<b.count, 32, 0, s>>>(b, ok);
     return cudaGetLastError();
 }
 

@@ -250,3 +250,23 @@ def test_edge_cases_and_errors():
         b = fhd.Cipher(key)
         assert np.array_equal(host(b.decrypt(b.open_stream(), E, H)), F)
     c.sync_status()
+
+
+def test_receiver_side_verification():
+    """The decrypted frame re-hashes to the transmitted digest; a flipped
+    ciphertext byte or a wrong digest is caught."""
+    key = si.key(31)
+    frames = [si.gradient_frame(48, 64, 3, t=t, seed=31) for t in range(3)]
+    enc, dec = fhd.Cipher(key, n_workers=6), fhd.Cipher(key, n_workers=6)
+    sid, rid = enc.open_stream(), dec.open_stream()
+    srcs = [to_dev(f) for f in frames]
+    E = [torch.empty_like(s) for s in srcs]
+    R = [torch.empty_like(s) for s in srcs]
+    H = [torch.empty(32, dtype=torch.uint8, device=dev()) for _ in srcs]
+    enc.encrypt_frames([(sid, s, e, h) for s, e, h in zip(srcs, E, H)])
+    E[1].view(-1)[100] ^= 1                      # damage frame 1 in transit
+    dec.decrypt_frames([(rid, e, r, h) for e, r, h in zip(E, R, H)])
+    Hbad = H[2].clone()
+    Hbad[0] ^= 0x80
+    ok = dec.verify_frames([(rid, e, r, h) for e, r, h in zip(E, R, [H[0], H[1], Hbad])])
+    assert host(ok).tolist() == [1, 0, 0]
