@@ -121,6 +121,28 @@ int encrypt_frames_ex(fhd_cipher *c, uint32_t count, const fhd_frame *frames, vo
 int decrypt_frames_ex(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream,
                       void *const *wait_events, uint32_t n_wait, void *master_done);
 
+/* Sender side with an early digest event: as encrypt_frames_ex, and
+ * `digests_done` (may be NULL) is recorded on `stream` once every frame's
+ * digest H (Algorithm 1: the XOR fold of the sub-frame digests) is in
+ * frames[i].digest, before LHCS_m runs.  A receiver on the same device can
+ * wait on it to start its own chaotic stage while the sender's keystream and
+ * permutation are still running.  For more than 128 frames it is recorded
+ * after the digests of the last group of 128. */
+int encrypt_frames_split(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream,
+                         void *const *wait_events, uint32_t n_wait, void *digests_done, void *master_done);
+
+/* Receiver side with the ciphertext still in flight: as decrypt_frames_ex,
+ * and the first kernel that reads frames[i].src (the inverse permutation of
+ * Algorithm 2) also waits on the n_data events in data_events (may be NULL /
+ * 0).  key_waits gate LHCS_m, which reads frames[i].digest; so a receiver can
+ * run the chaotic stage (Sec. II-B: master and workers) of a batch as soon as
+ * its digests are on the device, while the ciphertext is still being produced
+ * or copied, and the permutation starts once data_events have fired.  Events
+ * are cudaEvent_t passed as void*; master_done as in decrypt_frames_ex. */
+int decrypt_frames_split(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream,
+                         void *const *key_waits, uint32_t n_key_waits, void *const *data_events,
+                         uint32_t n_data, void *master_done);
+
 /* Pre-allocate at least `bytes` of scratch for calls on CUDA stream `stream`
  * (synchronises that stream), so that later calls on it never allocate.
  * frame_scratch_bytes() gives the scratch one frame needs. */

@@ -35,6 +35,7 @@ EXPORTS = (
     "fhd_permute_encrypt", "fhd_permute_decrypt", "fhd_strip_width", "fhd_set_strip_width", "fhd_version",
     "cipher_profile", "cipher_profile_read", "fhd_launch_count", "encrypt_frames_ex", "decrypt_frames_ex",
     "cipher_reserve", "fhd_frame_scratch_bytes", "fhd_frame_digest_noalloc", "cipher_verify_frames",
+    "decrypt_frames_split", "encrypt_frames_split",
 )
 KERNEL_KINDS = ("sha", "master", "keystream", "encrypt", "decrypt")
 
@@ -95,6 +96,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "fhd_launch_count": (ctypes.c_uint64, []),
             "encrypt_frames_ex": (i32, [P, u32, P, P, P, u32, P]),
             "decrypt_frames_ex": (i32, [P, u32, P, P, P, u32, P]),
+            "decrypt_frames_split": (i32, [P, u32, P, P, P, u32, P, u32, P]),
+            "encrypt_frames_split": (i32, [P, u32, P, P, P, u32, P, P]),
             "cipher_reserve": (i32, [P, P, u64]),
             "cipher_verify_frames": (i32, [P, u32, P, P, P]),
             "fhd_frame_scratch_bytes": (u64, [u32, u32, u32, u32]),
@@ -198,33 +201,62 @@ class Cipher:
             arr[k] = FhdFrame(sid, h, w, c, src.data_ptr(), dst.data_ptr(), digest.data_ptr())
         return arr, len(items)
 
-    def _run(self, plain, ex, items, stream, master_event, wait_events):
-        arr, n = self._frames(items)
-        if master_event is None and not wait_events:
-            _check(plain(self._handle(), n, arr, _stream_ptr(stream)), self._h)
-            return
-        for ev in wait_events:
+    @staticmethod
+    def _events(events):
+        for ev in events:
             if not ev.cuda_event:
                 raise ValueError("wait event was never recorded")
-        waits = (ctypes.c_void_p * max(len(wait_events), 1))(*[ev.cuda_event for ev in wait_events])
-        if master_event is not None and not master_event.cuda_event:
-            # torch creates the CUDA event on first record; the library re-records it after LHCS_m.
-            master_event.record(stream if stream is not None else torch.cuda.current_stream())
-        md = ctypes.c_void_p(master_event.cuda_event) if master_event is not None else ctypes.c_void_p()
+        return (ctypes.c_void_p * max(len(events), 1))(*[ev.cuda_event for ev in events])
+
+    @staticmethod
+    def _out_event(ev, stream):
+        if ev is None:
+            return ctypes.c_void_p()
+        if not ev.cuda_event:
+            # torch creates the CUDA event on first record; the library re-records it.
+            ev.record(stream if stream is not None else torch.cuda.current_stream())
+        return ctypes.c_void_p(ev.cuda_event)
+
+    def _run(self, plain, ex, items, stream, master_event, wait_events, data_events=(), digest_event=None):
+        arr, n = self._frames(items)
+        if master_event is None and not wait_events and not data_events and digest_event is None:
+            _check(plain(self._handle(), n, arr, _stream_ptr(stream)), self._h)
+            return
+        waits = self._events(wait_events)
+        md = self._out_event(master_event, stream)
+        if digest_event is not None:
+            dd = self._out_event(digest_event, stream)
+            _check(load().encrypt_frames_split(self._handle(), n, arr, _stream_ptr(stream), waits, len(wait_events),
+                                               dd, md), self._h)
+            return
+        if data_events:
+            data = self._events(data_events)
+            _check(load().decrypt_frames_split(self._handle(), n, arr, _stream_ptr(stream), waits, len(wait_events),
+                                               data, len(data_events), md), self._h)
+            return
         _check(ex(self._handle(), n, arr, _stream_ptr(stream), waits, len(wait_events), md), self._h)
 
-    def encrypt_frames(self, items: Iterable, stream=None, master_event=None, wait_events=()):
+    def encrypt_frames(self, items: Iterable, stream=None, master_event=None, wait_events=(), digest_event=None):
         """items: (stream_id, src, dst, digest) tuples; digest (32 B) is written.
 
         The chaining-state kernel first waits on ``wait_events`` and
-        ``master_event`` is recorded right after it (torch.cuda.Event's)."""
+        ``master_event`` is recorded right after it; ``digest_event`` is
+        recorded once the digests are written, before the chaining-state
+        kernel (all torch.cuda.Event's)."""
         lib = load()
-        self._run(lib.encrypt_frames, lib.encrypt_frames_ex, items, stream, master_event, list(wait_events))
+        self._run(lib.encrypt_frames, lib.encrypt_frames_ex, items, stream, master_event, list(wait_events),
+                  digest_event=digest_event)
 
-    def decrypt_frames(self, items: Iterable, stream=None, master_event=None, wait_events=()):
-        """items: (stream_id, src, dst, digest) tuples; digest (32 B) is read."""
+    def decrypt_frames(self, items: Iterable, stream=None, master_event=None, wait_events=(), data_events=()):
+        """items: (stream_id, src, dst, digest) tuples; digest (32 B) is read.
+
+        ``wait_events`` gate the chaining-state kernel (it reads the digests);
+        ``data_events`` gate the inverse permutation, the first kernel that
+        reads the ciphertext ``src``, so the chaotic stage can run while the
+        ciphertext is still being produced."""
         lib = load()
-        self._run(lib.decrypt_frames, lib.decrypt_frames_ex, items, stream, master_event, list(wait_events))
+        self._run(lib.decrypt_frames, lib.decrypt_frames_ex, items, stream, master_event, list(wait_events),
+                  list(data_events))
 
     def verify_frames(self, items: Iterable, stream=None) -> torch.Tensor:
         """Receiver-side check: 1 per frame whose decrypted ``dst`` re-hashes to its ``digest``."""

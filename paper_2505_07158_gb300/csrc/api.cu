@@ -44,6 +44,14 @@ namespace {
 thread_local std::string g_err;   // last error of the handle-less entry points
 std::atomic<uint64_t> g_launches{0};
 
+}  // namespace
+
+namespace fhd {
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace fhd
+
+namespace {
+
 cudaEvent_t take_event(fhd_cipher *c) {
     if (!c->pool.empty()) { cudaEvent_t e = c->pool.back(); c->pool.pop_back(); return e; }
     cudaEvent_t e = nullptr;
@@ -58,7 +66,6 @@ cudaError_t timed(fhd_cipher *c, int kind, cudaStream_t s, F &&launch) {
     cudaEvent_t a = nullptr, b = nullptr;
     if (c && c->prof) { a = take_event(c); b = take_event(c); cudaEventRecord(a, s); }
     cudaError_t e = launch();
-    g_launches.fetch_add(1, std::memory_order_relaxed);
     if (c && c->prof) { cudaEventRecord(b, s); c->recs.push_back({kind, a, b}); }
     return e;
 }
@@ -248,7 +255,8 @@ uint64_t frame_scratch(uint32_t n, uint32_t h, uint32_t w, uint32_t C) {
 }
 
 int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream, bool encrypt,
-               void *const *wait_events = nullptr, uint32_t n_wait = 0, cudaEvent_t master_done = nullptr) {
+               void *const *wait_events = nullptr, uint32_t n_wait = 0, cudaEvent_t master_done = nullptr,
+               void *const *data_events = nullptr, uint32_t n_data = 0, cudaEvent_t digests_done = nullptr) {
     if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
     if (count == 0) return FHD_OK;
     if (!frames) return fail(c, FHD_ERR_INVALID_ARG, "null frames");
@@ -325,18 +333,29 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
                 if (b.f[k2].slot == sid) b.order[pos++] = (uint16_t)k2;
         }
         b.group_begin[b.groups] = (uint16_t)pos;
-        if (encrypt && (e = timed(c, FHD_K_SHA, s, [&] { return fhd::launch_sha_subframes(b, s); })) != cudaSuccess)
-            return cuda_fail(c, e, "sha launch");
+        if (encrypt) {
+            if ((e = timed(c, FHD_K_SHA, s, [&] {
+                     cudaError_t r = fhd::launch_sha_subframes(b, s);
+                     return r == cudaSuccess ? fhd::launch_fold_batch(b, s) : r;
+                 })) != cudaSuccess)
+                return cuda_fail(c, e, "sha launch");
+            if (digests_done && base + m >= count && (e = cudaEventRecord(digests_done, s)) != cudaSuccess)
+                return cuda_fail(c, e, "record digest event");
+        }
         if (base == 0)
             for (uint32_t k = 0; k < n_wait; ++k)
                 if (wait_events[k] && (e = cudaStreamWaitEvent(s, (cudaEvent_t)wait_events[k], 0)) != cudaSuccess)
                     return cuda_fail(c, e, "wait event");
-        if ((e = timed(c, FHD_K_MASTER, s, [&] { return fhd::launch_master(b, c->d_states, encrypt, c->d_status, s); })) != cudaSuccess)
+        if ((e = timed(c, FHD_K_MASTER, s, [&] { return fhd::launch_master(b, c->d_states, c->d_status, s); })) != cudaSuccess)
             return cuda_fail(c, e, "master launch");
         if (master_done && base + m >= count && (e = cudaEventRecord(master_done, s)) != cudaSuccess)
             return cuda_fail(c, e, "record master event");
         if ((e = timed(c, FHD_K_KEYSTREAM, s, [&] { return fhd::launch_keystream(b, s); })) != cudaSuccess)
             return cuda_fail(c, e, "keystream launch");
+        if (base == 0)   // the first reader of frames[].src after the digest stage
+            for (uint32_t k = 0; k < n_data; ++k)
+                if (data_events[k] && (e = cudaStreamWaitEvent(s, (cudaEvent_t)data_events[k], 0)) != cudaSuccess)
+                    return cuda_fail(c, e, "wait data event");
         if ((e = timed(c, encrypt ? FHD_K_ENCRYPT : FHD_K_DECRYPT, s, [&] { return fhd::launch_permute(b, encrypt, s); })) != cudaSuccess)
             return cuda_fail(c, e, "permute launch");
     }
@@ -409,6 +428,22 @@ int decrypt_frames_ex(fhd_cipher *c, uint32_t count, const fhd_frame *frames, vo
                       void *const *wait_events, uint32_t n_wait, void *master_done) {
     if (n_wait && !wait_events) return fail(c, FHD_ERR_INVALID_ARG, "null wait_events");
     return run_frames(c, count, frames, stream, false, wait_events, n_wait, (cudaEvent_t)master_done);
+}
+
+int encrypt_frames_split(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream,
+                         void *const *wait_events, uint32_t n_wait, void *digests_done, void *master_done) {
+    if (n_wait && !wait_events) return fail(c, FHD_ERR_INVALID_ARG, "null wait_events");
+    return run_frames(c, count, frames, stream, true, wait_events, n_wait, (cudaEvent_t)master_done, nullptr, 0,
+                      (cudaEvent_t)digests_done);
+}
+
+int decrypt_frames_split(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream,
+                         void *const *key_waits, uint32_t n_key_waits, void *const *data_events,
+                         uint32_t n_data, void *master_done) {
+    if (n_key_waits && !key_waits) return fail(c, FHD_ERR_INVALID_ARG, "null key_waits");
+    if (n_data && !data_events) return fail(c, FHD_ERR_INVALID_ARG, "null data_events");
+    return run_frames(c, count, frames, stream, false, key_waits, n_key_waits, (cudaEvent_t)master_done,
+                      data_events, n_data);
 }
 
 int cipher_verify_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, uint8_t *ok, void *stream) {

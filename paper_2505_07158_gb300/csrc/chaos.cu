@@ -10,17 +10,31 @@
 // are bit-identical to a plain C implementation.  2 k is an exact doubling
 // done on the bit pattern.
 //
-// GPU mapping.  On this GPU a binary64 warp instruction occupies the SM
+// GPU mapping.  On this GPU a binary64 instruction occupies the SM
 // sub-partition's FP64 pipe for ~64 cycles whatever the number of active
-// lanes, and every chain is strictly sequential, so the time per step is set
-// by the binary64 instructions one warp issues per step.  A warp carries 32
-// independent chains and one chain's four variables are spread over four
-// warps on four sub-partitions: a CTA is 4 warps, warp v owns variable v
-// (x, y, z, w) of 32 chains (lane = chain), and the stage inputs are exchanged
-// through shared memory with one barrier per RK4 stage.  (Measured on GB300:
-// ~3.5k cycles per step; one warp per 8 chains with lane-local variables and
-// shuffles, and moving off-path operations to exact integer emulation, were
-// both slower.)
+// lanes, one after another (no overlap, dependent or not), and handing a
+// binary64 result to another unit (shuffle, shared memory, integer select)
+// costs ~15-40 more cycles per hand-off; every chain is strictly sequential.
+// So the time per step is the binary64 instructions one warp issues per step
+// plus its hand-offs.  A warp carries six chains, one variable per lane
+// (lane = 4 chain + v, v = x, y, z, w), and every component of Eq. (1) is the
+// same four fused multiply-adds with per-lane operands:
+//   p = fma(Pa, Pb, -Pc); q = fma(Qa, Qb, -0); p2 = fma(p, B2, -P2); k = fma(q, kS, p2)
+//   v = x: p = Y*1 - X, q = W*1, p2 = sigma p,     k = q + p2  = sigma (y - x) + w
+//   v = y: p = X rho,   q = X Z, p2 = p*1 - Y,     k = p2 - q  = (rho x - y) - x z
+//   v = z: p = Z beta,  q = X Y, p2 = -p,          k = q + p2  = x y - beta z
+//   v = w: p = W gamma, q = Y Z, p2 = p,           k = p2 - q  = gamma w - y z
+// Each fma rounds once, a product with addend -0 or a sum with a factor of
+// +-1, so k is bit-identical to the dmul/dadd/dsub sequence of the plain
+// definition.  The variable operands Pa, Pc, Qa, Qb, P2 arrive by five warp
+// shuffles per stage; a constant operand (the 1 of v = x, the 0 addends) is
+// shuffled from lane 24 (+0) or lane 25 (1.0), which stay fixed points of the
+// update because their own k is +0.  No selects and no barriers remain: a
+// step takes 27 binary64 instructions and ~2.0k cycles on GB300 (the earlier
+// mapping, one warp per variable with a shared-memory exchange and one barrier
+// per stage, took ~3.5k).  In the combination, acc + 2 k is one fma(k, 2, acc):
+// 2 k is exact, so it equals the separate doubling and add whenever 2 k is
+// finite (an overflowing 2 k makes the definition's state non-finite anyway).
 #include "common.cuh"
 
 namespace fhd {
@@ -30,56 +44,68 @@ constexpr double kSigma = 10.0;
 constexpr double kRho = 28.0;
 constexpr double kBeta = 8.0 / 3.0;
 
-// Exact 2*k on the IEEE-754 encoding (zero, subnormal and normal inputs).
-__device__ __forceinline__ double twice(double k) {
-    unsigned long long b = (unsigned long long)__double_as_longlong(k);
-    unsigned long long mag = b & 0x7fffffffffffffffull;
-    if (mag == 0) return k;
-    if (mag < (1ull << 52)) return __longlong_as_double((long long)((b & 0x8000000000000000ull) | (mag << 1)));
-    if (mag >= 0x7fe0000000000000ull) return __dmul_rn(2.0, k);   // overflow, inf, nan: hardware
-    return __longlong_as_double((long long)(b + (1ull << 52)));
-}
-
-// Component v of Eq. (1) at (x, y, z, w); v is warp-uniform.
-__device__ __forceinline__ double lhcs_f(int v, double x, double y, double z, double w, double gamma) {
-    switch (v) {
-        case 0: return __dadd_rn(__dmul_rn(kSigma, __dsub_rn(y, x)), w);
-        case 1: return __dsub_rn(__dsub_rn(__dmul_rn(kRho, x), y), __dmul_rn(x, z));
-        case 2: return __dsub_rn(__dmul_rn(x, y), __dmul_rn(kBeta, z));
-        default: return __dsub_rn(__dmul_rn(gamma, w), __dmul_rn(y, z));
-    }
-}
-
 struct Rk4 {
     double h, hh, h6;
 };
 
-// One RK4 step of 32 chains by 4 cooperating warps.  On entry buf[0][*][lane]
-// holds every variable of the current state (visible to all warps); on exit
-// buf[0] holds the new state and `s` this warp's component of it.
-__device__ __forceinline__ void rk4_step_coop(double &s, int v, int lane, double gamma, const Rk4 &c,
-                                              double (*buf)[4][32]) {
-    double k, acc, t;
-    k = lhcs_f(v, buf[0][0][lane], buf[0][1][lane], buf[0][2][lane], buf[0][3][lane], gamma);
-    acc = k;
-    t = __dadd_rn(s, __dmul_rn(c.hh, k));
-    buf[1][v][lane] = t;
-    __syncthreads();
-    k = lhcs_f(v, buf[1][0][lane], buf[1][1][lane], buf[1][2][lane], buf[1][3][lane], gamma);
-    t = __dadd_rn(s, __dmul_rn(c.hh, k));
-    acc = __dadd_rn(acc, twice(k));
-    buf[0][v][lane] = t;
-    __syncthreads();
-    k = lhcs_f(v, buf[0][0][lane], buf[0][1][lane], buf[0][2][lane], buf[0][3][lane], gamma);
-    t = __dadd_rn(s, __dmul_rn(c.h, k));
-    acc = __dadd_rn(acc, twice(k));
-    buf[1][v][lane] = t;
-    __syncthreads();
-    k = lhcs_f(v, buf[1][0][lane], buf[1][1][lane], buf[1][2][lane], buf[1][3][lane], gamma);
-    acc = __dadd_rn(acc, k);
-    s = __dadd_rn(s, __dmul_rn(c.h6, acc));
-    buf[0][v][lane] = s;
-    __syncthreads();
+constexpr int kChainsPerWarp = 6;   // lanes 0..23
+constexpr int kPairsPerWarp = 3;
+constexpr int kLaneZero = 24;       // holds +0
+constexpr int kLaneOne = 25;        // holds 1.0
+
+// Per-lane operand sources and coefficients of the component template.
+struct LaneRole {
+    double Pb, B2, kS;
+    int sPa, sPc, sQa, sQb, sP2;
+};
+
+__device__ __forceinline__ LaneRole lane_role(int lane, double gamma) {
+    LaneRole r;
+    const int v = lane & 3, base = lane & ~3;
+    if (lane >= 4 * kChainsPerWarp) {   // constant lanes: every operand +0, k = +0
+        r.Pb = r.B2 = r.kS = 0.0;
+        r.sPa = r.sPc = r.sQa = r.sQb = r.sP2 = kLaneZero;
+        return r;
+    }
+    r.Pb = v == 0 ? 1.0 : v == 1 ? kRho : v == 2 ? kBeta : gamma;
+    r.B2 = v == 0 ? kSigma : v == 2 ? -1.0 : 1.0;
+    r.kS = (v == 0 || v == 2) ? 1.0 : -1.0;
+    r.sPa = base + (v == 0 ? 1 : v == 1 ? 0 : v);                 // Y, X, Z, W
+    r.sPc = v == 0 ? base : kLaneZero;                            // X, +0, +0, +0
+    r.sQa = base + (v == 0 ? 3 : v == 3 ? 1 : 0);                 // W, X, X, Y
+    r.sQb = v == 0 ? kLaneOne : base + (v == 2 ? 1 : 2);          // 1, Z, Y, Z
+    r.sP2 = v == 1 ? base + 1 : kLaneZero;                        // +0, Y, +0, +0
+    return r;
+}
+
+// Initial value of a lane: the chain variable, or the constant a constant lane holds.
+__device__ __forceinline__ double lane_init(int lane, double chain_value) {
+    return lane < 4 * kChainsPerWarp ? chain_value : (lane == kLaneOne ? 1.0 : 0.0);
+}
+
+// One RK4 step of the warp's six chains; s is this lane's variable.  All 32
+// lanes of the warp must call it together.
+__device__ __forceinline__ void rk4_step_lanes(double &s, const LaneRole &r, const Rk4 &c) {
+    double tin = s, acc = 0.0;
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+        const double Pa = __shfl_sync(0xffffffffu, tin, r.sPa);
+        const double Pc = __shfl_sync(0xffffffffu, tin, r.sPc);
+        const double Qa = __shfl_sync(0xffffffffu, tin, r.sQa);
+        const double Qb = __shfl_sync(0xffffffffu, tin, r.sQb);
+        const double P2 = __shfl_sync(0xffffffffu, tin, r.sP2);
+        const double p = __fma_rn(Pa, r.Pb, -Pc);
+        const double q = __fma_rn(Qa, Qb, -0.0);
+        const double p2 = __fma_rn(p, r.B2, -P2);
+        const double k = __fma_rn(q, r.kS, p2);
+        if (st < 3) {
+            tin = __dadd_rn(s, __dmul_rn(st == 2 ? c.h : c.hh, k));
+            acc = st == 0 ? k : __fma_rn(k, 2.0, acc);
+        } else {
+            acc = __dadd_rn(acc, k);
+            s = __dadd_rn(s, __dmul_rn(c.h6, acc));
+        }
+    }
 }
 
 // Sec. II-A, Fig. 1a: reconstruct one initial condition from 8 digest bytes
@@ -104,72 +130,61 @@ __device__ __forceinline__ double reconstruct(double v, const uint8_t *hb, uint3
 
 __device__ __forceinline__ bool finite(double x) { return isfinite(x); }
 
-// Reconstruct from (state, H), run LHCS_m 2n steps writing IR, return the
-// last iterate in `s` (this warp's component).  All lanes carry the chain.
-__device__ void master_frame(double &s, int v, int lane, double gamma, const uint8_t *H_smem,
-                             const uint32_t *u, uint32_t n, const Rk4 &c, double *IR, double (*buf)[4][32]) {
-    s = reconstruct(s, H_smem + 8 * v, u[v]);
-    buf[0][v][lane] = s;
-    __syncthreads();
+// Reconstruct from (state, H), run LHCS_m 2n steps writing IR.  The chain
+// lives in lanes 0..3 of the warp (lane = variable); s is this lane's value.
+__device__ void master_frame(double &s, int lane, const LaneRole &role, const uint8_t *H_smem, const uint32_t *u,
+                             uint32_t n, const Rk4 &c, double *IR) {
+    if (lane < 4) s = reconstruct(s, H_smem + 8 * lane, u[lane]);
+    __syncwarp();
     for (uint32_t t = 0; t < 2 * n; ++t) {
-        rk4_step_coop(s, v, lane, gamma, c, buf);
-        if (lane == 0) IR[4 * t + v] = s;
+        rk4_step_lanes(s, role, c);
+        if (lane < 4) IR[4 * t + lane] = s;
     }
 }
 
-// K2a: one CTA per stream of the batch; the stream's frames in call order.
-__global__ void __launch_bounds__(128) master_kernel(const __grid_constant__ Batch b, StreamState *states,
-                                                     int encrypt, unsigned *status) {
-    __shared__ double buf[2][4][32];
+// K2a: one warp per stream of the batch; the stream's frames in call order.
+__global__ void __launch_bounds__(32) master_kernel(const __grid_constant__ Batch b, StreamState *states,
+                                                    unsigned *status) {
     __shared__ __align__(16) uint8_t H[32];
-    const int v = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lane = threadIdx.x;
     const uint32_t g = blockIdx.x;
     if (g >= b.groups) return;
     const Rk4 c{b.hstep, b.hhalf, b.hsixth};
     const uint32_t first = b.group_begin[g], last = b.group_begin[g + 1];
     const uint32_t slot = b.f[b.order[first]].slot;
     StreamState *st = states + slot;
-    double s = st->v[v];
     const double gamma = b.f[b.order[first]].gamma;
+    const LaneRole role = lane_role(lane, gamma);
+    double s = lane_init(lane, lane < 4 ? st->v[lane] : 0.0);
     for (uint32_t k = first; k < last; ++k) {
         const FrameDesc &fd = b.f[b.order[k]];
-        if (threadIdx.x < 8) {
-            uint32_t word;
-            if (encrypt) {
-                const uint32_t *p = reinterpret_cast<const uint32_t *>(fd.part);
-                word = 0;
-                for (uint32_t i = 0; i < b.n; ++i) word ^= p[8 * i + threadIdx.x];
-                reinterpret_cast<uint32_t *>(fd.digest)[threadIdx.x] = word;
-            } else {
-                word = reinterpret_cast<const uint32_t *>(fd.digest)[threadIdx.x];
-            }
-            reinterpret_cast<uint32_t *>(H)[threadIdx.x] = word;
-        }
-        __syncthreads();
-        master_frame(s, v, lane, gamma, H, b.u, b.n, c, fd.IR, buf);
-        __syncthreads();
+        if (lane < 8)   // the frame's digest: folded by the digest stage, or the transmitted one
+            reinterpret_cast<uint32_t *>(H)[lane] = reinterpret_cast<const uint32_t *>(fd.digest)[lane];
+        __syncwarp();
+        master_frame(s, lane, role, H, b.u, b.n, c, fd.IR);
+        __syncwarp();
     }
-    if (lane == 0) {
-        st->v[v] = s;
+    if (lane < 4) {
+        st->v[lane] = s;
         if (!finite(s)) atomicOr(status, kStatusNonFinite);
-        if (v == 0) st->frames += (last - first);
+        if (lane == 0) st->frames += (last - first);
     }
 }
 
-// fhd_master: one CTA, one state of 5 doubles (x, y, z, w, gamma).
-__global__ void __launch_bounds__(128) master_raw_kernel(double *state5, const uint8_t *Hg, uint32_t n,
-                                                         Rk4 c, uint4 u4, double *IR, unsigned *status) {
-    __shared__ double buf[2][4][32];
+// fhd_master: one warp, one state of 5 doubles (x, y, z, w, gamma).
+__global__ void __launch_bounds__(32) master_raw_kernel(double *state5, const uint8_t *Hg, uint32_t n, Rk4 c,
+                                                        uint4 u4, double *IR, unsigned *status) {
     __shared__ __align__(16) uint8_t H[32];
-    const int v = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x < 32) H[threadIdx.x] = Hg[threadIdx.x];
-    __syncthreads();
+    const int lane = threadIdx.x;
+    H[lane] = Hg[lane];
+    __syncwarp();
     const uint32_t u[4] = {u4.x, u4.y, u4.z, u4.w};
-    double s = state5[v];
     const double gamma = state5[4];
-    master_frame(s, v, lane, gamma, H, u, n, c, IR, buf);
-    if (lane == 0) {
-        state5[v] = s;
+    const LaneRole role = lane_role(lane, gamma);
+    double s = lane_init(lane, lane < 4 ? state5[lane] : 0.0);
+    master_frame(s, lane, role, H, u, n, c, IR);
+    if (lane < 4) {
+        state5[lane] = s;
         if (!finite(s) && status) atomicOr(status, kStatusNonFinite);
     }
 }
@@ -187,13 +202,19 @@ __device__ __forceinline__ WorkerSlice worker_slice(uint64_t LD, uint64_t LB, ui
     return w;
 }
 
-constexpr uint32_t kPairsPerCta = 16;   // 32 chains = 16 worker pairs
-
-__device__ void keystream_cta(const FrameDesc &fd, uint32_t n, uint32_t pg, double gamma, const Rk4 &c,
-                              double (*buf)[4][32]) {
-    const int v = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t p = pg * kPairsPerCta + (lane >> 1);
-    const bool active = p < n;
+// K2b: one warp carries three worker pairs (six chains) of one frame for the
+// frame's uniform trip count; lane 4c + v holds variable v of chain c, chains
+// 2q and 2q + 1 are pair q, so the partner of a lane is lane ^ 4.
+__global__ void __launch_bounds__(32) keystream_kernel(const __grid_constant__ Batch b) {
+    const uint32_t wpf = (b.n + kPairsPerWarp - 1) / kPairsPerWarp;
+    const uint32_t f = blockIdx.x / wpf, pg = blockIdx.x % wpf;
+    if (f >= b.count) return;
+    const FrameDesc &fd = b.f[f];
+    const uint32_t n = b.n;
+    const Rk4 c{b.hstep, b.hhalf, b.hsixth};
+    const int lane = threadIdx.x, v = lane & 3, ch = lane >> 2;
+    const uint32_t p = pg * kPairsPerWarp + (ch >> 1);
+    const bool active = lane < 4 * kChainsPerWarp && p < n;
     const uint64_t LD = (uint64_t)fd.C * (fd.h + fd.w);
     const uint64_t LB = fd.N;
     WorkerSlice ws{0, 0, 0, 0};
@@ -202,24 +223,22 @@ __device__ void keystream_cta(const FrameDesc &fd, uint32_t n, uint32_t pg, doub
     // Uniform trip count: the longest slice of the frame.
     const uint64_t need_max = 2 * ((LD + n - 1) / n) + (LB + n - 1) / n;
     const uint64_t T = (need_max + 23) / 24;
-    double s = active ? fd.IR[4 * (2 * p + (lane & 1)) + v] : 0.0;
-    buf[0][v][lane] = s;
-    __syncthreads();
+    const LaneRole role = lane_role(lane, fd.gamma);
+    double s = lane_init(lane, active ? fd.IR[4 * (2 * p + (ch & 1)) + v] : 0.0);
     uint8_t *Dbytes = reinterpret_cast<uint8_t *>(fd.D) + 2 * ws.d0;
     uint8_t *Bp = fd.B + ws.b0;
     const uint64_t ndb = 2 * ws.nd;
-    const int half = (lane & 1) * 3;
+    const int half = (ch & 1) * 3;
     for (uint64_t t = 0; t < T; ++t) {
-        rk4_step_coop(s, v, lane, gamma, c, buf);
-        unsigned long long mine = (unsigned long long)__double_as_longlong(s) & 0xffffffffffffull;
-        unsigned long long other = __shfl_xor_sync(0xffffffffu, mine, 1);
-        unsigned long long x = mine ^ other;
-        uint64_t pos0 = 24 * t + 6 * v;
+        rk4_step_lanes(s, role, c);
+        const unsigned long long mine = (unsigned long long)__double_as_longlong(s) & 0xffffffffffffull;
+        const unsigned long long x = mine ^ __shfl_xor_sync(0xffffffffu, mine, 4);
+        const uint64_t pos0 = 24 * t + 6 * v;
         if (active && pos0 < need) {
 #pragma unroll
             for (int bb = 0; bb < 3; ++bb) {
-                uint64_t pos = pos0 + half + bb;
-                uint8_t byte = (uint8_t)(x >> (8 * (half + bb)));
+                const uint64_t pos = pos0 + half + bb;
+                const uint8_t byte = (uint8_t)(x >> (8 * (half + bb)));
                 if (pos < ndb) Dbytes[pos] = byte;
                 else if (pos < need) Bp[pos - ndb] = byte;
             }
@@ -227,36 +246,28 @@ __device__ void keystream_cta(const FrameDesc &fd, uint32_t n, uint32_t pg, doub
     }
 }
 
-// K2b: ceil(n/16) CTAs per frame, each 16 worker pairs of one frame.
-__global__ void __launch_bounds__(128) keystream_kernel(const __grid_constant__ Batch b) {
-    __shared__ double buf[2][4][32];
-    const uint32_t cpf = (b.n + kPairsPerCta - 1) / kPairsPerCta;
-    const uint32_t f = blockIdx.x / cpf, pg = blockIdx.x % cpf;
-    if (f >= b.count) return;
-    const FrameDesc &fd = b.f[f];
-    const Rk4 c{b.hstep, b.hhalf, b.hsixth};
-    keystream_cta(fd, b.n, pg, fd.gamma, c, buf);
-}
-
 }  // namespace
 
-cudaError_t launch_master(const Batch &b, StreamState *states, bool encrypt, unsigned *status, cudaStream_t s) {
+cudaError_t launch_master(const Batch &b, StreamState *states, unsigned *status, cudaStream_t s) {
     if (!b.groups) return cudaSuccess;
-    master_kernel<<<b.groups, 128, 0, s>>>(b, states, encrypt ? 1 : 0, status);
+    master_kernel<<<b.groups, 32, 0, s>>>(b, states, status);
+    note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_master_raw(double *state5, const uint8_t *H, uint32_t n, double hstep, const uint32_t u[4],
                               double *IR, unsigned *status, cudaStream_t s) {
     Rk4 c{hstep, hstep / 2.0, hstep / 6.0};   // host arithmetic: IEEE round-to-nearest
-    master_raw_kernel<<<1, 128, 0, s>>>(state5, H, n, c, make_uint4(u[0], u[1], u[2], u[3]), IR, status);
+    master_raw_kernel<<<1, 32, 0, s>>>(state5, H, n, c, make_uint4(u[0], u[1], u[2], u[3]), IR, status);
+    note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_keystream(const Batch &b, cudaStream_t s) {
     if (!b.count) return cudaSuccess;
-    const uint32_t cpf = (b.n + kPairsPerCta - 1) / kPairsPerCta;
-    keystream_kernel<<<b.count * cpf, 128, 0, s>>>(b);
+    const uint32_t wpf = (b.n + kPairsPerWarp - 1) / kPairsPerWarp;
+    keystream_kernel<<<b.count * wpf, 32, 0, s>>>(b);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -65,9 +65,12 @@ cudaError_t launch_verify(const Batch &b, uint8_t *ok, cudaStream_t s);   // ok[
 cudaError_t launch_sha_plain(const uint8_t *data, uint64_t nbytes, uint32_t n, uint32_t count,
                              uint8_t *part, cudaStream_t s);
 cudaError_t launch_fold(const uint8_t *part, uint32_t n, uint32_t count, uint8_t *digest, cudaStream_t s);
+cudaError_t launch_fold_batch(const Batch &b, cudaStream_t s);
+// Counts one kernel launch of this library (read by fhd_launch_count).
+void note_launch();
 cudaError_t noalloc_scratch(uint8_t **out);   // fixed sub-frame digest array of fhd_frame_digest_noalloc
 uint32_t noalloc_max_digests();
-cudaError_t launch_master(const Batch &b, StreamState *states, bool encrypt, unsigned *status, cudaStream_t s);
+cudaError_t launch_master(const Batch &b, StreamState *states, unsigned *status, cudaStream_t s);
 cudaError_t launch_master_raw(double *state5, const uint8_t *H, uint32_t n, double hstep, const uint32_t u[4],
                               double *IR, unsigned *status, cudaStream_t s);
 cudaError_t launch_keystream(const Batch &b, cudaStream_t s);

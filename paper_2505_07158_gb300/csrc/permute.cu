@@ -436,14 +436,18 @@ cudaError_t launch_permute(const Batch &b, bool encrypt, cudaStream_t s) {
     }
     if (encrypt) {
         row_kernel<true><<<b.row_ctas, kRowThreads, rsm, s>>>(b);
+        note_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         strip_kernel<true><<<b.perm_ctas, kStripThreads, ssm, s>>>(b);
+        note_launch();
     } else {
         strip_kernel<false><<<b.perm_ctas, kStripThreads, ssm, s>>>(b);
+        note_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         row_kernel<false><<<b.row_ctas, kRowThreads, rsm, s>>>(b);
+        note_launch();
     }
     return cudaGetLastError();
 }

@@ -12,7 +12,9 @@
 // 16-byte aligned, byte loads otherwise), expands the message schedule and
 // stores W[t] + K[t] into a double-buffered shared-memory ring; the consumer
 // lane runs only the 64 compression rounds of the previous block.  The two
-// warps meet at one named barrier per block.  Rotations are funnel shifts,
+// warps meet at one named barrier per block.  The producer also prefetches
+// each message 8 blocks ahead into L2: without it every other block (two per
+// 128-byte line) waited a full DRAM round trip.  Rotations are funnel shifts,
 // the three-input boolean functions map onto LOP3.
 #include <mutex>
 
@@ -92,6 +94,7 @@ __device__ __forceinline__ void store_digest(uint8_t *dst, const uint32_t h[8]) 
 }
 
 constexpr int kMsgPerCta = 32;
+constexpr uint64_t kPrefetchBlocks = 8;
 
 // Blocks of a padded message of len bytes (FIPS 180-4 Sec. 5.1.1).
 __device__ __forceinline__ uint64_t padded_blocks(uint64_t len) { return (len >> 6) + ((len & 63) + 9 <= 64 ? 1 : 2); }
@@ -163,6 +166,9 @@ __device__ void sha_pipeline(Locate locate, uint32_t nmsg) {
         if (active && al && full) load_block16(p, cur);
         for (uint64_t b = 0; b < NB; ++b) {
             if (b < nb) {
+                // Keep the message's bytes kPrefetchBlocks ahead on their way into L2, so the
+                // register prefetch of the next block below finds them there rather than in DRAM.
+                if (b + kPrefetchBlocks < full) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + 64 * (b + kPrefetchBlocks)));
                 if (al && b + 1 < full) load_block16(p + 64 * (b + 1), nxt);
                 uint32_t w[16];
                 message_block(p, len, b, al, cur, w);
@@ -194,13 +200,17 @@ __device__ void sha_pipeline(Locate locate, uint32_t nmsg) {
         for (uint64_t b = 0; b < NB; ++b) {
             if (b < nb) {
                 const uint32_t(*src)[kMsgPerCta] = wk[b & 1];
+                // all 64 W+K words into registers first: the rounds never wait on shared memory
+                uint32_t wkr[64];
+#pragma unroll
+                for (int t = 0; t < 64; ++t) wkr[t] = src[t][lane];
                 uint32_t a = st.h[0], bb = st.h[1], c = st.h[2], d = st.h[3];
                 uint32_t e = st.h[4], f = st.h[5], g = st.h[6], hh = st.h[7];
 #pragma unroll
                 for (int t = 0; t < 64; ++t) {
                     const uint32_t S1 = rotr(e, 6) ^ rotr(e, 11) ^ rotr(e, 25);
                     const uint32_t ch = (e & f) ^ (~e & g);
-                    const uint32_t t1 = hh + S1 + ch + src[t][lane];
+                    const uint32_t t1 = hh + S1 + ch + wkr[t];
                     const uint32_t S0 = rotr(a, 2) ^ rotr(a, 13) ^ rotr(a, 22);
                     const uint32_t mj = (a & bb) ^ (a & c) ^ (bb & c);
                     hh = g; g = f; f = e; e = d + t1;
@@ -290,6 +300,18 @@ __global__ void fold_kernel(const uint8_t *part, uint32_t n, uint32_t count, uin
     reinterpret_cast<uint32_t *>(digest + 32ull * k)[lane] = acc;
 }
 
+// The digest of every frame of a batch: H = h_1 xor ... xor h_n over the
+// frame's n sub-frame digests (Algorithm 1), written to the frame's digest.
+__global__ void fold_batch_kernel(const __grid_constant__ Batch b) {
+    const uint32_t k = blockIdx.x, lane = threadIdx.x;
+    if (k >= b.count || lane >= 8) return;
+    const FrameDesc &fd = b.f[k];
+    const uint32_t *p = reinterpret_cast<const uint32_t *>(fd.part);
+    uint32_t acc = 0;
+    for (uint32_t i = 0; i < b.n; ++i) acc ^= p[8 * i + lane];
+    reinterpret_cast<uint32_t *>(fd.digest)[lane] = acc;
+}
+
 // Scratch of fhd_frame_digest_noalloc: the per-sub-frame digests of one call,
 // in a fixed device array so that the call allocates nothing.  Every GPU that
 // loads the library holds it (2 MiB) until the process exits.
@@ -326,6 +348,7 @@ cudaError_t launch_sha_subframes(const Batch &b, cudaStream_t s) {
     const uint32_t msgs = b.count * b.n;
     if (!msgs) return cudaSuccess;
     sha_subframes_kernel<<<(msgs + kMsgPerCta - 1) / kMsgPerCta, 64, 0, s>>>(b);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -333,9 +356,11 @@ cudaError_t launch_verify(const Batch &b, uint8_t *ok, cudaStream_t s) {
     const uint32_t msgs = b.count * b.n;
     if (!msgs) return cudaSuccess;
     sha_dst_kernel<<<(msgs + kMsgPerCta - 1) / kMsgPerCta, 64, 0, s>>>(b);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     verify_kernel<<<b.count, 32, 0, s>>>(b, ok);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -344,12 +369,21 @@ cudaError_t launch_sha_plain(const uint8_t *data, uint64_t nbytes, uint32_t n, u
     const uint32_t msgs = count * n;
     if (!msgs) return cudaSuccess;
     sha_plain_kernel<<<(msgs + kMsgPerCta - 1) / kMsgPerCta, 64, 0, s>>>(data, nbytes, n, count, part);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold_batch(const Batch &b, cudaStream_t s) {
+    if (!b.count) return cudaSuccess;
+    fold_batch_kernel<<<b.count, 32, 0, s>>>(b);
+    note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_fold(const uint8_t *part, uint32_t n, uint32_t count, uint8_t *digest, cudaStream_t s) {
     if (!count) return cudaSuccess;
     fold_kernel<<<count, 32, 0, s>>>(part, n, count, digest);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -121,3 +121,59 @@ def test_event_ordered_frames_across_cuda_streams():
     for F, (E, H) in zip(frames, outs):
         E_ref, H_ref = ref.encrypt(host(F))
         assert np.array_equal(host(E), E_ref) and bytes(host(H)) == H_ref
+
+
+def test_receiver_starts_before_ciphertext_arrives():
+    """decrypt_frames(data_events=...): the chaotic stage runs on the digests while the
+    ciphertext is still on its way; the inverse permutation waits for the data event.  The
+    sender's stream delays the ciphertext copy behind a fixed-length sleep kernel, so a
+    permutation that did not wait would read the zero-filled receive buffer."""
+    shapes = [(96, 128, 3), (60, 100, 3)]
+    key = si.key(610)
+    frames = [to_dev(si.gradient_frame(*s, t=t, seed=611)) for t, s in enumerate(shapes)]
+    snd, rcv = fhd.Cipher(key), fhd.Cipher(key)
+    sid, rid = snd.open_stream(), rcv.open_stream()
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    E = [torch.empty_like(f) for f in frames]
+    wire = [torch.zeros_like(f) for f in frames]       # the receiver's ciphertext buffers
+    H = torch.empty((len(frames), 32), dtype=torch.uint8, device=dev())
+    R = [torch.empty_like(f) for f in frames]
+    digests_ready, data_ready = torch.cuda.Event(), torch.cuda.Event()
+    torch.cuda.synchronize()
+    snd.encrypt_frames([(sid, frames[k], E[k], H[k]) for k in range(len(frames))], stream=sa,
+                       digest_event=digests_ready)
+    with torch.cuda.stream(sa):
+        torch.cuda._sleep(20_000_000)                   # ~10 ms: the ciphertext is late
+        for k in range(len(frames)):
+            wire[k].copy_(E[k])
+        data_ready.record(sa)
+    rcv.decrypt_frames([(rid, wire[k], R[k], H[k]) for k in range(len(frames))], stream=sb,
+                       wait_events=[digests_ready], data_events=[data_ready])
+    torch.cuda.synchronize()
+    ref = oracle.Stream.from_key(key)
+    for k in range(len(frames)):
+        E_ref, H_ref = ref.encrypt(host(frames[k]))
+        assert np.array_equal(host(E[k]), E_ref), k
+        assert bytes(host(H[k])) == H_ref
+        assert torch.equal(R[k], frames[k]), k
+    with pytest.raises(ValueError):
+        rcv.decrypt_frames([(rid, wire[0], R[0], H[0])], stream=sb, data_events=[torch.cuda.Event()])
+
+
+def test_launch_count_per_call():
+    """fhd_launch_count counts every kernel: digest (SHA + fold), LHCS_m, workers, and the two
+    permutation passes on encryption; LHCS_m, workers and the two passes on decryption."""
+    key = si.key(620)
+    F = to_dev(si.uniform_frame(40, 56, 3, seed=621))
+    snd, rcv = fhd.Cipher(key), fhd.Cipher(key)
+    sid, rid = snd.open_stream(), rcv.open_stream()
+    E, R = torch.empty_like(F), torch.empty_like(F)
+    H = torch.empty(32, dtype=torch.uint8, device=dev())
+    l0 = fhd.fhd_launch_count()
+    snd.encrypt_frames([(sid, F, E, H)])
+    l1 = fhd.fhd_launch_count()
+    rcv.decrypt_frames([(rid, E, R, H)])
+    l2 = fhd.fhd_launch_count()
+    torch.cuda.synchronize()
+    assert (l1 - l0, l2 - l1) == (6, 4)
+    assert torch.equal(R, F)
