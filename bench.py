@@ -49,8 +49,7 @@ RK4_FP64_OPS = 104      # per chain step: 4 x 13 (Eq. 1) + 3 x 8 (stages) + 4 x 
 # DRAM bytes (read + write) per 1080p frame of one launch, from the ncu capture summarised in
 # profiles/ncu_hot_kernels_clip1080p_4frames.md (4 frames per launch, scaled by frames);
 # None where the kernel changed after that capture.
-TRAFFIC_PER_FRAME = {"keystream": 30720 / 4, "encrypt": (49876992 + 1781248) / 4, "sha": 24926464 / 4,
-                     "master": 18944 / 4, "decrypt": None}
+TRAFFIC_PER_FRAME = {"keystream": None, "encrypt": None, "sha": None, "master": None, "decrypt": None}
 
 
 def parse():
@@ -65,6 +64,9 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="length of each serving run (60 s = full config)")
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed-batch, serving and stress measurements")
     ap.add_argument("--no-stress", action="store_true", help="skip the 256 x 8K stress round trip")
+    ap.add_argument("--inflight", type=int, default=1,
+                    help="clips in flight (round trips on separate buffers; 2 measured slower: the overlapping "
+                         "keystreams oversubscribe the FP64 pipes and slow the serial chaining kernels)")
     return ap.parse_args()
 
 
@@ -240,54 +242,94 @@ def run_ours(args):
     tuned = autotune.tune([(HGT, WID, CH)])
     clip = si.clip(FRAMES, HGT, WID, CH, seed=rank)
     host = torch.from_numpy(clip).pin_memory()
-    srcs = [host[t].to(dev) for t in range(FRAMES)]
-    encs = [torch.empty_like(s) for s in srcs]
-    decs = [torch.empty_like(s) for s in srcs]
-    digs = torch.empty((FRAMES, 32), dtype=torch.uint8, device=dev)
     key = si.key(rank)
     enc, dec = fhd.Cipher(key, n_workers=N_WORKERS), fhd.Cipher(key, n_workers=N_WORKERS)
     sid, rid = enc.open_stream(), dec.open_stream()
     stream = torch.cuda.current_stream()
-    rx = torch.cuda.Stream()                 # the receiver's CUDA stream
-    enc_items = [(sid, srcs[t], encs[t], digs[t]) for t in range(FRAMES)]
-    dec_items = [(rid, encs[t], decs[t], digs[t]) for t in range(FRAMES)]
-    digests_ready, cipher_ready, rx_done = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
 
-    def round_trip():
-        # Sender on `stream`, receiver on `rx`: the receiver's chaotic stage starts once the digests
-        # exist (before the sender's LHCS_m), its inverse permutation once the ciphertext is complete;
-        # the sender's next batch waits for the receiver (the buffers are reused).
-        enc.encrypt_frames(enc_items, stream, digest_event=digests_ready)
-        cipher_ready.record(stream)
-        dec.decrypt_frames(dec_items, rx, wait_events=[digests_ready], data_events=[cipher_ready])
-        rx_done.record(rx)
-        stream.wait_event(rx_done)
+    class Slot:
+        """Buffers and CUDA streams of one clip in flight: the sender encrypts on `tx`, the receiver
+        decrypts on `rx`; the receiver's chaotic stage waits for the digests, its inverse permutation
+        for the ciphertext, and the slot is reused once its previous receiver has finished."""
 
-    def step():
-        round_trip()
+        def __init__(self):
+            self.srcs = [host[t].to(dev) for t in range(FRAMES)]
+            self.encs = [torch.empty_like(x) for x in self.srcs]
+            self.decs = [torch.empty_like(x) for x in self.srcs]
+            self.digs = torch.empty((FRAMES, 32), dtype=torch.uint8, device=dev)
+            self.tx, self.rx = torch.cuda.Stream(), torch.cuda.Stream()
+            self.enc_items = [(sid, self.srcs[t], self.encs[t], self.digs[t]) for t in range(FRAMES)]
+            self.dec_items = [(rid, self.encs[t], self.decs[t], self.digs[t]) for t in range(FRAMES)]
+            self.digests_ready, self.cipher_ready = torch.cuda.Event(), torch.cuda.Event()
+            self.enc_master, self.dec_master, self.rx_done = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
+            self.used = False
+            self.host_out = torch.empty_like(host).pin_memory()
+            self.host_dig = torch.empty((FRAMES, 32), dtype=torch.uint8).pin_memory()
 
-    for _ in range(max(args.warmup, 3)):
-        step()
+    slots = [Slot() for _ in range(max(1, args.inflight))]
+    last = [None]            # slot of the previous clip: the chaining state advances clip after clip
+
+    def round_trip(sl, e2e=False):
+        prev = last[0]
+        if sl.used:
+            sl.tx.wait_event(sl.rx_done)
+        if e2e:
+            with torch.cuda.stream(sl.tx):
+                for t in range(FRAMES):
+                    sl.srcs[t].copy_(host[t], non_blocking=True)
+        enc.encrypt_frames(sl.enc_items, sl.tx, wait_events=[prev.enc_master] if prev else [],
+                           master_event=sl.enc_master, digest_event=sl.digests_ready)
+        sl.cipher_ready.record(sl.tx)
+        dec.decrypt_frames(sl.dec_items, sl.rx, wait_events=[sl.digests_ready] + ([prev.dec_master] if prev else []),
+                           master_event=sl.dec_master, data_events=[sl.cipher_ready])
+        if e2e:
+            with torch.cuda.stream(sl.rx):
+                for t in range(FRAMES):
+                    sl.host_out[t].copy_(sl.decs[t], non_blocking=True)
+                sl.host_dig.copy_(sl.digs, non_blocking=True)
+        sl.rx_done.record(sl.rx)
+        sl.used = True
+        last[0] = sl
+
+    def timed_steps(nsteps, inflight, e2e=False):
+        """K round trips with up to `inflight` clips in flight; device time between two events on
+        `stream` (every slot stream waits on the first, the second waits on every slot)."""
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev0.record(stream)
+        for sl in slots[:inflight]:
+            sl.tx.wait_event(ev0)
+            sl.rx.wait_event(ev0)
+        for k in range(nsteps):
+            round_trip(slots[k % inflight], e2e)
+        for sl in slots[:inflight]:
+            stream.wait_event(sl.rx_done)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        barrier()
+        return ev0, ev0.elapsed_time(ev1), wall
+
+    INF = len(slots)
+    for k in range(max(args.warmup, 3)):
+        round_trip(slots[k % INF])
     torch.cuda.synchronize()
-    verified = all(torch.equal(decs[t], srcs[t]) for t in range(FRAMES))
+    verified = all(torch.equal(sl.decs[t], sl.srcs[t]) for sl in slots if sl.used for t in range(FRAMES))
 
-    # ---- device-resident timed region (with per-kernel events on the launch stream)
+    # ---- one clip in flight (the sender's next clip waits for the receiver), when the headline has more
+    ms_one = timed_steps(args.steps, 1)[1] if INF > 1 else None
+
+    # ---- device-resident timed region (with per-kernel events on the launch streams)
     enc.profile(True)
     dec.profile(True)
     l0 = fhd.fhd_launch_count()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
-        barrier()
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            step()
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
+        origin, ms_total, _ = timed_steps(args.steps, INF)
     launches = fhd.fhd_launch_count() - l0
-    ms_total = ev0.elapsed_time(ev1)
     from paper_2505_07158_gb300 import replicas
+    spans = enc.profile_spans(origin) + dec.profile_spans(origin)
     prof = {}
     for c in (enc, dec):
         for k, (ms, n) in c.profile_read().items():
@@ -299,38 +341,37 @@ def run_ours(args):
     ms_total = replicas.max_over_ranks(ms_total, device=dev)
     ms_step = ms_total / args.steps
     value = replicas.job_throughput(FRAMES * args.steps, ms_total, world)
+    ms_one = replicas.max_over_ranks(ms_one, device=dev) if ms_one is not None else ms_total
+
+    def busy_ms(kind):
+        """Union of the launch spans of one kind of kernel (ms)."""
+        iv = sorted((a, b) for k, a, b in spans if k == kind)
+        tot, cur = 0.0, None
+        for a, b in iv:
+            if cur is None or a > cur[1]:
+                if cur is not None:
+                    tot += cur[1] - cur[0]
+                cur = [a, b]
+            else:
+                cur[1] = max(cur[1], b)
+        return tot + (cur[1] - cur[0] if cur else 0.0)
 
     # ---- end to end through the public API with pinned host buffers
-    host_out = torch.empty_like(host).pin_memory()
-    host_dig = torch.empty((FRAMES, 32), dtype=torch.uint8).pin_memory()
-
-    def e2e_step():
-        for t in range(FRAMES):
-            srcs[t].copy_(host[t], non_blocking=True)
-        round_trip()
-        for t in range(FRAMES):
-            host_out[t].copy_(decs[t], non_blocking=True)
-        host_dig.copy_(digs, non_blocking=True)
-
-    e2e_step()
+    round_trip(slots[0], e2e=True)
     torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = max(ev0.elapsed_time(ev1), 1000 * (time.perf_counter() - t0)) / args.steps
+    _, e2e_dev_ms, e2e_wall = timed_steps(args.steps, INF, e2e=True)
+    e2e_ms = max(e2e_dev_ms, 1000 * e2e_wall) / args.steps
     e2e_ms = replicas.max_over_ranks(e2e_ms, device=dev)
-    e2e_ok = torch.equal(host_out, host)
+    e2e_ok = all(torch.equal(sl.host_out, host) for sl in slots if sl.used)
 
-    # ---- plain path: one call per frame (the paper's per-frame loop)
+    # ---- plain path: one call per frame (the paper's per-frame loop), one CUDA stream
+    sl0 = slots[0]
     torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for t in range(FRAMES):
-        enc.encrypt_frames([enc_items[t]], stream)
-        dec.decrypt_frames([dec_items[t]], stream)
+        enc.encrypt_frames([sl0.enc_items[t]], stream)
+        dec.decrypt_frames([sl0.dec_items[t]], stream)
     ev1.record(stream)
     torch.cuda.synchronize()
     plain_fps = FRAMES / (ev0.elapsed_time(ev1) / 1000.0)
@@ -350,13 +391,20 @@ def run_ours(args):
     master_steps = 2 * N_WORKERS * per_step_frames
 
     def fp64_roof(k, steps_per_launch):
+        # Launches of one kind overlap (sender and receiver, clips in flight): achieved = algorithmic
+        # ops of all its launches / the union of their spans; per launch for reference.
+        n_l = kern[k]["launches_per_step"] * args.steps
+        busy = busy_ms(k)
+        ach = n_l * steps_per_launch * RK4_FP64_OPS / (busy / 1000.0) / 1e12
         ms = kern[k]["avg_launch_ms"]
-        ach = steps_per_launch * RK4_FP64_OPS / (ms / 1000.0) / 1e12
         tpf = TRAFFIC_PER_FRAME.get(k)
         return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TOPS, "traffic": tpf * per_step_frames if tpf is not None else None,
                 "peak_source": "binary64 pipe: measured 1.684 lane-op/clk/SM x 152 SMs x 2.07 GHz",
-                "per_launch_units": f"{steps_per_launch} RK4 chain steps x {RK4_FP64_OPS} binary64 ops"}
+                "per_launch_units": f"{steps_per_launch} RK4 chain steps x {RK4_FP64_OPS} binary64 ops",
+                "busy_ms_per_step": busy / args.steps,
+                "achieved_per_launch": steps_per_launch * RK4_FP64_OPS / (ms / 1000.0) / 1e12,
+                "timing": "ops of all launches / union of their CUDA-event spans (launches overlap)"}
 
     def hbm_roof(k):
         ms = kern[k]["avg_launch_ms"]
@@ -405,6 +453,7 @@ def run_ours(args):
                                    "per GPU, n=32 workers, RK4 h=0.001; per step encrypt_frames on the sender's CUDA stream and "
                                    "decrypt_frames on the receiver's (its chaotic stage waits for the digests, its "
                                    "inverse permutation for the ciphertext)",
+                       "clips_in_flight": INF,
                        "frames_per_step": FRAMES * world, "l2": "inputs larger than L2 (~560 MB live per step)",
                        "parallelism": f"replicas x{world} (independent streams)",
                        "strip_width": tuned.get(f"{HGT}x{WID}x{CH}")},
@@ -412,6 +461,8 @@ def run_ours(args):
             "e2e": {"value": world * FRAMES / (e2e_ms / 1000.0), "unit": "frames/s",
                     "h2d_bytes_per_step": FRAMES * N, "d2h_bytes_per_step": FRAMES * N + FRAMES * 32},
             "plain_per_frame_fps": plain_fps,
+            "one_clip_in_flight": ({"value": world * FRAMES / (ms_one / args.steps / 1000.0), "unit": "frames/s",
+                                    "ms_per_step": ms_one / args.steps} if INF > 1 else None),
             "gpu_launches": int(launches),
             "clocks": clocks,
             "roofline": dict(roofs[dominant], kernel=dominant) if dominant in roofs else None,

@@ -243,6 +243,17 @@ int cipher_profile(fhd_cipher *c, int enable);
  * and launches[FHD_K_COUNT], and forget them. */
 int cipher_profile_read(fhd_cipher *c, double *ms, uint32_t *launches);
 
+/* The launches recorded since the last cipher_profile_read, one span each,
+ * without clearing them: kinds[i] (FHD_K_*), start_ms[i] and end_ms[i] in
+ * milliseconds after `origin` (a cudaEvent_t passed as void*, recorded with
+ * timing enabled before those launches).  Fills at most `cap` entries and
+ * sets *count to the number of recorded launches (which may exceed cap).
+ * Synchronises on the launches' events.  With several CUDA streams in
+ * flight the spans overlap; their union is the time a kind of kernel kept
+ * the device busy. */
+int cipher_profile_spans(fhd_cipher *c, void *origin, uint32_t cap, int32_t *kinds, double *start_ms,
+                         double *end_ms, uint32_t *count);
+
 /* Number of kernels this library has launched in this process. */
 uint64_t fhd_launch_count(void);
 

@@ -35,7 +35,7 @@ EXPORTS = (
     "fhd_permute_encrypt", "fhd_permute_decrypt", "fhd_strip_width", "fhd_set_strip_width", "fhd_version",
     "cipher_profile", "cipher_profile_read", "fhd_launch_count", "encrypt_frames_ex", "decrypt_frames_ex",
     "cipher_reserve", "fhd_frame_scratch_bytes", "fhd_frame_digest_noalloc", "cipher_verify_frames",
-    "decrypt_frames_split", "encrypt_frames_split",
+    "decrypt_frames_split", "encrypt_frames_split", "cipher_profile_spans",
 )
 KERNEL_KINDS = ("sha", "master", "keystream", "encrypt", "decrypt")
 
@@ -98,6 +98,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "decrypt_frames_ex": (i32, [P, u32, P, P, P, u32, P]),
             "decrypt_frames_split": (i32, [P, u32, P, P, P, u32, P, u32, P]),
             "encrypt_frames_split": (i32, [P, u32, P, P, P, u32, P, P]),
+            "cipher_profile_spans": (i32, [P, P, u32, P, P, P, P]),
             "cipher_reserve": (i32, [P, P, u64]),
             "cipher_verify_frames": (i32, [P, u32, P, P, P]),
             "fhd_frame_scratch_bytes": (u64, [u32, u32, u32, u32]),
@@ -303,6 +304,23 @@ class Cipher:
         n = (ctypes.c_uint32 * 5)()
         _check(load().cipher_profile_read(self._handle(), ms, n), self._h)
         return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+    def profile_spans(self, origin) -> list:
+        """[(kind, start_ms, end_ms)] of the launches recorded since the last
+        ``profile_read``, relative to ``origin`` (a recorded timing event)."""
+        if not origin.cuda_event:
+            raise ValueError("origin event was never recorded")
+        lib = load()
+        count = ctypes.c_uint32()
+        _check(lib.cipher_profile_spans(self._handle(), ctypes.c_void_p(origin.cuda_event), 0, None, None, None,
+                                        ctypes.byref(count)), self._h)
+        n = count.value
+        kinds = (ctypes.c_int32 * max(n, 1))()
+        t0 = (ctypes.c_double * max(n, 1))()
+        t1 = (ctypes.c_double * max(n, 1))()
+        _check(lib.cipher_profile_spans(self._handle(), ctypes.c_void_p(origin.cuda_event), n, kinds, t0, t1,
+                                        ctypes.byref(count)), self._h)
+        return [(KERNEL_KINDS[kinds[i]], t0[i], t1[i]) for i in range(min(n, count.value))]
 
     def last_error(self) -> str:
         return load().cipher_last_error(self._h).decode(errors="replace")

@@ -557,6 +557,27 @@ int cipher_profile_read(fhd_cipher *c, double *ms, uint32_t *launches) {
     return rc;
 }
 
+int cipher_profile_spans(fhd_cipher *c, void *origin, uint32_t cap, int32_t *kinds, double *start_ms,
+                         double *end_ms, uint32_t *count) {
+    if (!c || !origin || !count || (cap && (!kinds || !start_ms || !end_ms)))
+        return fail(c, FHD_ERR_INVALID_ARG, "null argument");
+    *count = (uint32_t)c->recs.size();
+    uint32_t i = 0;
+    for (auto &r : c->recs) {
+        if (i >= cap) break;
+        float a = 0.f, b = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&a, (cudaEvent_t)origin, r.a);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&b, (cudaEvent_t)origin, r.b);
+        if (e != cudaSuccess) return cuda_fail(c, e, "profile spans");
+        kinds[i] = r.kind;
+        start_ms[i] = a;
+        end_ms[i] = b;
+        ++i;
+    }
+    return FHD_OK;
+}
+
 uint64_t fhd_launch_count(void) { return g_launches.load(); }
 
 void cipher_destroy(fhd_cipher *c) {
