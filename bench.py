@@ -64,9 +64,9 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="length of each serving run (60 s = full config)")
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed-batch, serving and stress measurements")
     ap.add_argument("--no-stress", action="store_true", help="skip the 256 x 8K stress round trip")
-    ap.add_argument("--inflight", type=int, default=1,
-                    help="clips in flight (round trips on separate buffers; 2 measured slower: the overlapping "
-                         "keystreams oversubscribe the FP64 pipes and slow the serial chaining kernels)")
+    ap.add_argument("--inflight", type=int, default=2,
+                    help="clips in flight on separate buffers: the next clip's digest stage overlaps this clip's "
+                         "keystreams; its chaotic stage waits for this clip")
     return ap.parse_args()
 
 
@@ -277,10 +277,13 @@ def run_ours(args):
             with torch.cuda.stream(sl.tx):
                 for t in range(FRAMES):
                     sl.srcs[t].copy_(host[t], non_blocking=True)
-        enc.encrypt_frames(sl.enc_items, sl.tx, wait_events=[prev.enc_master] if prev else [],
+        # The digest stage (integer work) of this clip runs at once, during the previous clip's keystreams
+        # (binary64 work); this clip's LHCS_m waits for the previous clip's sender (chaining order and
+        # ciphertext done) and receiver, so at most one clip's keystreams share the FP64 pipes.
+        enc.encrypt_frames(sl.enc_items, sl.tx, wait_events=[prev.enc_master, prev.cipher_ready] if prev else [],
                            master_event=sl.enc_master, digest_event=sl.digests_ready)
         sl.cipher_ready.record(sl.tx)
-        dec.decrypt_frames(sl.dec_items, sl.rx, wait_events=[sl.digests_ready] + ([prev.dec_master] if prev else []),
+        dec.decrypt_frames(sl.dec_items, sl.rx, wait_events=[sl.digests_ready] + ([prev.rx_done] if prev else []),
                            master_event=sl.dec_master, data_events=[sl.cipher_ready])
         if e2e:
             with torch.cuda.stream(sl.rx):
@@ -361,6 +364,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     _, e2e_dev_ms, e2e_wall = timed_steps(args.steps, INF, e2e=True)
     e2e_ms = max(e2e_dev_ms, 1000 * e2e_wall) / args.steps
+    e2e_parts = {"device_ms_per_step": e2e_dev_ms / args.steps, "wall_ms_per_step": 1000 * e2e_wall / args.steps}
     e2e_ms = replicas.max_over_ranks(e2e_ms, device=dev)
     e2e_ok = all(torch.equal(sl.host_out, host) for sl in slots if sl.used)
 
@@ -459,7 +463,7 @@ def run_ours(args):
                        "strip_width": tuned.get(f"{HGT}x{WID}x{CH}")},
             "verified_round_trip": bool(verified) and bool(e2e_ok),
             "e2e": {"value": world * FRAMES / (e2e_ms / 1000.0), "unit": "frames/s",
-                    "h2d_bytes_per_step": FRAMES * N, "d2h_bytes_per_step": FRAMES * N + FRAMES * 32},
+                    "h2d_bytes_per_step": FRAMES * N, "d2h_bytes_per_step": FRAMES * N + FRAMES * 32, **e2e_parts},
             "plain_per_frame_fps": plain_fps,
             "one_clip_in_flight": ({"value": world * FRAMES / (ms_one / args.steps / 1000.0), "unit": "frames/s",
                                     "ms_per_step": ms_one / args.steps} if INF > 1 else None),

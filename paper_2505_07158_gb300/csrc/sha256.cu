@@ -8,14 +8,13 @@
 // GPU mapping: a message is inherently sequential, and with n = 32 a frame has
 // only 32 of them, so the time of one message is the time of the frame.  Each
 // message therefore gets two threads in two warps of one CTA: a producer lane
-// loads the 64-byte blocks (16-byte vector loads when the message start is
-// 16-byte aligned, byte loads otherwise), expands the message schedule and
-// stores W[t] + K[t] into a double-buffered shared-memory ring; the consumer
-// lane runs only the 64 compression rounds of the previous block.  The two
-// warps meet at one named barrier per block.  The producer also prefetches
-// each message 8 blocks ahead into L2: without it every other block (two per
-// 128-byte line) waited a full DRAM round trip.  Rotations are funnel shifts,
-// the three-input boolean functions map onto LOP3.
+// brings the 64-byte blocks in (cp.async into a four-block shared-memory ring
+// when the message start is 16-byte aligned, byte loads otherwise; an L2
+// prefetch runs eight blocks ahead), expands the message schedule and stores
+// W[t] + K[t] into a double-buffered shared-memory ring; the consumer lane
+// runs only the 64 compression rounds of the previous block.  The two warps
+// meet at one named barrier per block.  Rotations are funnel shifts, the
+// three-input boolean functions map onto LOP3.
 #include <mutex>
 
 #include "common.cuh"
@@ -42,40 +41,7 @@ struct ShaState {
         h[0] = 0x6a09e667u; h[1] = 0xbb67ae85u; h[2] = 0x3c6ef372u; h[3] = 0xa54ff53au;
         h[4] = 0x510e527fu; h[5] = 0x9b05688cu; h[6] = 0x1f83d9abu; h[7] = 0x5be0cd19u;
     }
-    // One FIPS 180-4 compression; w[] holds the block as big-endian words.
-    __device__ __forceinline__ void compress(uint32_t w[16]) {
-        uint32_t a = h[0], b = h[1], c = h[2], d = h[3], e = h[4], f = h[5], g = h[6], hh = h[7];
-#pragma unroll
-        for (int t = 0; t < 64; ++t) {
-            uint32_t wt;
-            if (t < 16) {
-                wt = w[t];
-            } else {
-                uint32_t w15 = w[(t - 15) & 15], w2 = w[(t - 2) & 15];
-                uint32_t s0 = rotr(w15, 7) ^ rotr(w15, 18) ^ (w15 >> 3);
-                uint32_t s1 = rotr(w2, 17) ^ rotr(w2, 19) ^ (w2 >> 10);
-                wt = w[t & 15] + s0 + w[(t - 7) & 15] + s1;
-                w[t & 15] = wt;
-            }
-            uint32_t S1 = rotr(e, 6) ^ rotr(e, 11) ^ rotr(e, 25);
-            uint32_t ch = (e & f) ^ (~e & g);
-            uint32_t t1 = hh + S1 + ch + kK[t] + wt;
-            uint32_t S0 = rotr(a, 2) ^ rotr(a, 13) ^ rotr(a, 22);
-            uint32_t mj = (a & b) ^ (a & c) ^ (b & c);
-            uint32_t t2 = S0 + mj;
-            hh = g; g = f; f = e; e = d + t1;
-            d = c; c = b; b = a; a = t1 + t2;
-        }
-        h[0] += a; h[1] += b; h[2] += c; h[3] += d;
-        h[4] += e; h[5] += f; h[6] += g; h[7] += hh;
-    }
 };
-
-__device__ __forceinline__ void load_block16(const uint8_t *p, uint4 q[4]) {
-    const uint4 *v = reinterpret_cast<const uint4 *>(p);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) q[k] = __ldg(v + k);
-}
 
 __device__ __forceinline__ void block_words(const uint4 q[4], uint32_t w[16]) {
 #pragma unroll
@@ -95,6 +61,7 @@ __device__ __forceinline__ void store_digest(uint8_t *dst, const uint32_t h[8]) 
 
 constexpr int kMsgPerCta = 32;
 constexpr uint64_t kPrefetchBlocks = 8;
+constexpr uint64_t kRing = 4;
 
 // Blocks of a padded message of len bytes (FIPS 180-4 Sec. 5.1.1).
 __device__ __forceinline__ uint64_t padded_blocks(uint64_t len) { return (len >> 6) + ((len & 63) + 9 <= 64 ? 1 : 2); }
@@ -139,6 +106,15 @@ __device__ __forceinline__ void message_block(const uint8_t *p, uint64_t len, ui
     }
 }
 
+// 16-byte asynchronous global -> shared copy (Ampere-class cp.async, L2 only), its commit and wait.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 __device__ __forceinline__ void named_barrier_64() {
     __syncwarp();
     asm volatile("bar.sync 1, 64;" ::: "memory");
@@ -160,16 +136,31 @@ __device__ void sha_pipeline(Locate locate, uint32_t nmsg) {
     const uint64_t nb = active ? padded_blocks(len) : 0;
     const uint64_t NB = __reduce_max_sync(0xffffffffu, (unsigned)nb);   // < 2^32 blocks per message
     if (producer) {
+        // Message bytes reach shared memory by cp.async, kRing - 1 blocks ahead of the block being
+        // expanded (one commit group per block, empty when the lane has nothing to copy), so no
+        // register waits on a load in flight; an L2 prefetch runs kPrefetchBlocks ahead of that.
+        __shared__ uint4 ring[kRing][4][kMsgPerCta];
         const bool al = (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
         const uint64_t full = len >> 6;
-        uint4 cur[4], nxt[4];
-        if (active && al && full) load_block16(p, cur);
+        auto issue = [&](uint64_t blk) {
+            if (active && al && blk < full) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) cp_async16(&ring[blk % kRing][q][lane], p + 64 * blk + 16 * q);
+            }
+            cp_async_commit();
+        };
+        for (uint64_t k = 0; k + 1 < kRing; ++k) issue(k);
         for (uint64_t b = 0; b < NB; ++b) {
+            // Refills the slot of block b - 1, whose bytes were consumed in the previous iteration.
+            issue(b + kRing - 1);
             if (b < nb) {
-                // Keep the message's bytes kPrefetchBlocks ahead on their way into L2, so the
-                // register prefetch of the next block below finds them there rather than in DRAM.
                 if (b + kPrefetchBlocks < full) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + 64 * (b + kPrefetchBlocks)));
-                if (al && b + 1 < full) load_block16(p + 64 * (b + 1), nxt);
+                cp_async_wait<kRing - 1>();     // block b has landed
+                uint4 cur[4];
+                if (al && b < full) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) cur[q] = ring[b % kRing][q][lane];
+                }
                 uint32_t w[16];
                 message_block(p, len, b, al, cur, w);
                 uint32_t(*dst)[kMsgPerCta] = wk[b & 1];
@@ -187,12 +178,11 @@ __device__ void sha_pipeline(Locate locate, uint32_t nmsg) {
                     }
                     dst[t][lane] = wt + kK[t];
                 }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
             }
             named_barrier_64();                 // block b is ready; block b-1 has been consumed
         }
         named_barrier_64();                     // pairs with the consumer's last wait
+        cp_async_wait<0>();
     } else {
         ShaState st;
         st.init();
@@ -206,14 +196,19 @@ __device__ void sha_pipeline(Locate locate, uint32_t nmsg) {
                 for (int t = 0; t < 64; ++t) wkr[t] = src[t][lane];
                 uint32_t a = st.h[0], bb = st.h[1], c = st.h[2], d = st.h[3];
                 uint32_t e = st.h[4], f = st.h[5], g = st.h[6], hh = st.h[7];
+                // The round written so that only Sigma1(e) and Ch(e, f, g) sit on the e -> e' chain:
+                // h + K + W and d + h + K + W use values known three rounds ahead (h = e, d = a
+                // of round t - 3), so e' = (d + h + K + W) + Sigma1 + Ch is shift, LOP3, IADD3.
 #pragma unroll
                 for (int t = 0; t < 64; ++t) {
+                    const uint32_t hk = hh + wkr[t];
+                    const uint32_t dhk = d + hk;
                     const uint32_t S1 = rotr(e, 6) ^ rotr(e, 11) ^ rotr(e, 25);
                     const uint32_t ch = (e & f) ^ (~e & g);
-                    const uint32_t t1 = hh + S1 + ch + wkr[t];
                     const uint32_t S0 = rotr(a, 2) ^ rotr(a, 13) ^ rotr(a, 22);
                     const uint32_t mj = (a & bb) ^ (a & c) ^ (bb & c);
-                    hh = g; g = f; f = e; e = d + t1;
+                    const uint32_t t1 = hk + S1 + ch;
+                    hh = g; g = f; f = e; e = dhk + S1 + ch;
                     d = c; c = bb; bb = a; a = t1 + S0 + mj;
                 }
                 st.h[0] += a; st.h[1] += bb; st.h[2] += c; st.h[3] += d;
