@@ -279,7 +279,9 @@ def run_ours(args):
                     sl.srcs[t].copy_(host[t], non_blocking=True)
         # The digest stage (integer work) of this clip runs at once, during the previous clip's keystreams
         # (binary64 work); this clip's LHCS_m waits for the previous clip's sender (chaining order and
-        # ciphertext done) and receiver, so at most one clip's keystreams share the FP64 pipes.
+        # ciphertext done) and receiver, so the FP64 pipes carry one clip's chaotic stage at a time.  (Gating
+        # LHCS_m on the previous keystreams only, so that the permutations overlap it, measured slower:
+        # LHCS_m then shares the SMs with the permutation kernels.)
         enc.encrypt_frames(sl.enc_items, sl.tx, wait_events=[prev.enc_master, prev.cipher_ready] if prev else [],
                            master_event=sl.enc_master, digest_event=sl.digests_ready)
         sl.cipher_ready.record(sl.tx)

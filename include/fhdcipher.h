@@ -127,9 +127,13 @@ int decrypt_frames_ex(fhd_cipher *c, uint32_t count, const fhd_frame *frames, vo
  * frames[i].digest, before LHCS_m runs.  A receiver on the same device can
  * wait on it to start its own chaotic stage while the sender's keystream and
  * permutation are still running.  For more than 128 frames it is recorded
- * after the digests of the last group of 128. */
+ * after the digests of the last group of 128.  `keystream_done` (may be
+ * NULL) is recorded right after the last worker kernel (Sec. II-B), before
+ * the permutation: later chaotic work gated on it does not share the FP64
+ * pipes with this call's keystream, while the permutation may overlap it. */
 int encrypt_frames_split(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream,
-                         void *const *wait_events, uint32_t n_wait, void *digests_done, void *master_done);
+                         void *const *wait_events, uint32_t n_wait, void *digests_done, void *master_done,
+                         void *keystream_done);
 
 /* Receiver side with the ciphertext still in flight: as decrypt_frames_ex,
  * and the first kernel that reads frames[i].src (the inverse permutation of
@@ -138,10 +142,11 @@ int encrypt_frames_split(fhd_cipher *c, uint32_t count, const fhd_frame *frames,
  * run the chaotic stage (Sec. II-B: master and workers) of a batch as soon as
  * its digests are on the device, while the ciphertext is still being produced
  * or copied, and the permutation starts once data_events have fired.  Events
- * are cudaEvent_t passed as void*; master_done as in decrypt_frames_ex. */
+ * are cudaEvent_t passed as void*; master_done as in decrypt_frames_ex,
+ * keystream_done as in encrypt_frames_split. */
 int decrypt_frames_split(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream,
                          void *const *key_waits, uint32_t n_key_waits, void *const *data_events,
-                         uint32_t n_data, void *master_done);
+                         uint32_t n_data, void *master_done, void *keystream_done);
 
 /* Pre-allocate at least `bytes` of scratch for calls on CUDA stream `stream`
  * (synchronises that stream), so that later calls on it never allocate.

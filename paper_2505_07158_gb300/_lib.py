@@ -96,8 +96,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "fhd_launch_count": (ctypes.c_uint64, []),
             "encrypt_frames_ex": (i32, [P, u32, P, P, P, u32, P]),
             "decrypt_frames_ex": (i32, [P, u32, P, P, P, u32, P]),
-            "decrypt_frames_split": (i32, [P, u32, P, P, P, u32, P, u32, P]),
-            "encrypt_frames_split": (i32, [P, u32, P, P, P, u32, P, P]),
+            "decrypt_frames_split": (i32, [P, u32, P, P, P, u32, P, u32, P, P]),
+            "encrypt_frames_split": (i32, [P, u32, P, P, P, u32, P, P, P]),
             "cipher_profile_spans": (i32, [P, P, u32, P, P, P, P]),
             "cipher_reserve": (i32, [P, P, u64]),
             "cipher_verify_frames": (i32, [P, u32, P, P, P]),
@@ -218,46 +218,53 @@ class Cipher:
             ev.record(stream if stream is not None else torch.cuda.current_stream())
         return ctypes.c_void_p(ev.cuda_event)
 
-    def _run(self, plain, ex, items, stream, master_event, wait_events, data_events=(), digest_event=None):
+    def _run(self, plain, ex, items, stream, master_event, wait_events, encrypt, data_events=(), digest_event=None,
+             keystream_event=None):
         arr, n = self._frames(items)
-        if master_event is None and not wait_events and not data_events and digest_event is None:
+        if master_event is None and not wait_events and not data_events and digest_event is None \
+                and keystream_event is None:
             _check(plain(self._handle(), n, arr, _stream_ptr(stream)), self._h)
             return
         waits = self._events(wait_events)
         md = self._out_event(master_event, stream)
-        if digest_event is not None:
+        kd = self._out_event(keystream_event, stream)
+        if encrypt and (digest_event is not None or keystream_event is not None):
             dd = self._out_event(digest_event, stream)
             _check(load().encrypt_frames_split(self._handle(), n, arr, _stream_ptr(stream), waits, len(wait_events),
-                                               dd, md), self._h)
+                                               dd, md, kd), self._h)
             return
-        if data_events:
+        if not encrypt and (data_events or keystream_event is not None):
             data = self._events(data_events)
             _check(load().decrypt_frames_split(self._handle(), n, arr, _stream_ptr(stream), waits, len(wait_events),
-                                               data, len(data_events), md), self._h)
+                                               data, len(data_events), md, kd), self._h)
             return
         _check(ex(self._handle(), n, arr, _stream_ptr(stream), waits, len(wait_events), md), self._h)
 
-    def encrypt_frames(self, items: Iterable, stream=None, master_event=None, wait_events=(), digest_event=None):
+    def encrypt_frames(self, items: Iterable, stream=None, master_event=None, wait_events=(), digest_event=None,
+                       keystream_event=None):
         """items: (stream_id, src, dst, digest) tuples; digest (32 B) is written.
 
         The chaining-state kernel first waits on ``wait_events`` and
         ``master_event`` is recorded right after it; ``digest_event`` is
         recorded once the digests are written, before the chaining-state
-        kernel (all torch.cuda.Event's)."""
+        kernel, and ``keystream_event`` after the worker kernel, before the
+        permutation (all torch.cuda.Event's)."""
         lib = load()
-        self._run(lib.encrypt_frames, lib.encrypt_frames_ex, items, stream, master_event, list(wait_events),
-                  digest_event=digest_event)
+        self._run(lib.encrypt_frames, lib.encrypt_frames_ex, items, stream, master_event, list(wait_events), True,
+                  digest_event=digest_event, keystream_event=keystream_event)
 
-    def decrypt_frames(self, items: Iterable, stream=None, master_event=None, wait_events=(), data_events=()):
+    def decrypt_frames(self, items: Iterable, stream=None, master_event=None, wait_events=(), data_events=(),
+                       keystream_event=None):
         """items: (stream_id, src, dst, digest) tuples; digest (32 B) is read.
 
         ``wait_events`` gate the chaining-state kernel (it reads the digests);
         ``data_events`` gate the inverse permutation, the first kernel that
         reads the ciphertext ``src``, so the chaotic stage can run while the
-        ciphertext is still being produced."""
+        ciphertext is still being produced; ``keystream_event`` is recorded
+        after the worker kernel."""
         lib = load()
-        self._run(lib.decrypt_frames, lib.decrypt_frames_ex, items, stream, master_event, list(wait_events),
-                  list(data_events))
+        self._run(lib.decrypt_frames, lib.decrypt_frames_ex, items, stream, master_event, list(wait_events), False,
+                  list(data_events), keystream_event=keystream_event)
 
     def verify_frames(self, items: Iterable, stream=None) -> torch.Tensor:
         """Receiver-side check: 1 per frame whose decrypted ``dst`` re-hashes to its ``digest``."""

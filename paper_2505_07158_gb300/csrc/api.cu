@@ -256,7 +256,8 @@ uint64_t frame_scratch(uint32_t n, uint32_t h, uint32_t w, uint32_t C) {
 
 int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream, bool encrypt,
                void *const *wait_events = nullptr, uint32_t n_wait = 0, cudaEvent_t master_done = nullptr,
-               void *const *data_events = nullptr, uint32_t n_data = 0, cudaEvent_t digests_done = nullptr) {
+               void *const *data_events = nullptr, uint32_t n_data = 0, cudaEvent_t digests_done = nullptr,
+               cudaEvent_t keystream_done = nullptr) {
     if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
     if (count == 0) return FHD_OK;
     if (!frames) return fail(c, FHD_ERR_INVALID_ARG, "null frames");
@@ -352,6 +353,8 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
             return cuda_fail(c, e, "record master event");
         if ((e = timed(c, FHD_K_KEYSTREAM, s, [&] { return fhd::launch_keystream(b, s); })) != cudaSuccess)
             return cuda_fail(c, e, "keystream launch");
+        if (keystream_done && base + m >= count && (e = cudaEventRecord(keystream_done, s)) != cudaSuccess)
+            return cuda_fail(c, e, "record keystream event");
         if (base == 0)   // the first reader of frames[].src after the digest stage
             for (uint32_t k = 0; k < n_data; ++k)
                 if (data_events[k] && (e = cudaStreamWaitEvent(s, (cudaEvent_t)data_events[k], 0)) != cudaSuccess)
@@ -431,19 +434,20 @@ int decrypt_frames_ex(fhd_cipher *c, uint32_t count, const fhd_frame *frames, vo
 }
 
 int encrypt_frames_split(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream,
-                         void *const *wait_events, uint32_t n_wait, void *digests_done, void *master_done) {
+                         void *const *wait_events, uint32_t n_wait, void *digests_done, void *master_done,
+                         void *keystream_done) {
     if (n_wait && !wait_events) return fail(c, FHD_ERR_INVALID_ARG, "null wait_events");
     return run_frames(c, count, frames, stream, true, wait_events, n_wait, (cudaEvent_t)master_done, nullptr, 0,
-                      (cudaEvent_t)digests_done);
+                      (cudaEvent_t)digests_done, (cudaEvent_t)keystream_done);
 }
 
 int decrypt_frames_split(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream,
                          void *const *key_waits, uint32_t n_key_waits, void *const *data_events,
-                         uint32_t n_data, void *master_done) {
+                         uint32_t n_data, void *master_done, void *keystream_done) {
     if (n_key_waits && !key_waits) return fail(c, FHD_ERR_INVALID_ARG, "null key_waits");
     if (n_data && !data_events) return fail(c, FHD_ERR_INVALID_ARG, "null data_events");
     return run_frames(c, count, frames, stream, false, key_waits, n_key_waits, (cudaEvent_t)master_done,
-                      data_events, n_data);
+                      data_events, n_data, nullptr, (cudaEvent_t)keystream_done);
 }
 
 int cipher_verify_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, uint8_t *ok, void *stream) {

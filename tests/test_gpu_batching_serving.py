@@ -141,15 +141,17 @@ def test_receiver_starts_before_ciphertext_arrives():
     digests_ready, data_ready = torch.cuda.Event(), torch.cuda.Event()
     torch.cuda.synchronize()
     snd.encrypt_frames([(sid, frames[k], E[k], H[k]) for k in range(len(frames))], stream=sa,
-                       digest_event=digests_ready)
+                       digest_event=digests_ready, keystream_event=torch.cuda.Event())
     with torch.cuda.stream(sa):
         torch.cuda._sleep(20_000_000)                   # ~10 ms: the ciphertext is late
         for k in range(len(frames)):
             wire[k].copy_(E[k])
         data_ready.record(sa)
+    rx_keys = torch.cuda.Event()
     rcv.decrypt_frames([(rid, wire[k], R[k], H[k]) for k in range(len(frames))], stream=sb,
-                       wait_events=[digests_ready], data_events=[data_ready])
+                       wait_events=[digests_ready], data_events=[data_ready], keystream_event=rx_keys)
     torch.cuda.synchronize()
+    assert rx_keys.query()
     ref = oracle.Stream.from_key(key)
     for k in range(len(frames)):
         E_ref, H_ref = ref.encrypt(host(frames[k]))
