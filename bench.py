@@ -47,9 +47,11 @@ HBM_PEAK_FALLBACK = 6800.0
 FP64_PEAK_TOPS = 1.684 * 152 * 2.07e9 / 1e12
 RK4_FP64_OPS = 104      # per chain step: 4 x 13 (Eq. 1) + 3 x 8 (stages) + 4 x 7 (combination)
 # DRAM bytes (read + write) per 1080p frame of one launch, from the ncu capture summarised in
-# profiles/ncu_hot_kernels_clip1080p_4frames.md (4 frames per launch, scaled by frames);
-# None where the kernel changed after that capture.
-TRAFFIC_PER_FRAME = {"keystream": None, "encrypt": None, "sha": None, "master": None, "decrypt": None}
+# profiles/ncu_hot_kernels_clip1080p_4frames.md (4 frames per launch, scaled by frames; cold caches,
+# writes still in L2 at kernel end not counted); None where the kernel changed after that capture.
+TRAFFIC_PER_FRAME = {"keystream": 24832 / 4, "encrypt": (24923136 + 13824 + 49838848 + 910592) / 4,
+                     "decrypt": (49840896 + 952576 + 24923392 + 33024) / 4, "sha": 24936192 / 4,
+                     "master": 9216 / 4}
 
 
 def parse():
@@ -262,6 +264,7 @@ def run_ours(args):
             self.dec_items = [(rid, self.encs[t], self.decs[t], self.digs[t]) for t in range(FRAMES)]
             self.digests_ready, self.cipher_ready = torch.cuda.Event(), torch.cuda.Event()
             self.enc_master, self.dec_master, self.rx_done = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
+            self.dec_done = torch.cuda.Event()
             self.used = False
             self.host_out = torch.empty_like(host).pin_memory()
             self.host_dig = torch.empty((FRAMES, 32), dtype=torch.uint8).pin_memory()
@@ -285,8 +288,9 @@ def run_ours(args):
         enc.encrypt_frames(sl.enc_items, sl.tx, wait_events=[prev.enc_master, prev.cipher_ready] if prev else [],
                            master_event=sl.enc_master, digest_event=sl.digests_ready)
         sl.cipher_ready.record(sl.tx)
-        dec.decrypt_frames(sl.dec_items, sl.rx, wait_events=[sl.digests_ready] + ([prev.rx_done] if prev else []),
+        dec.decrypt_frames(sl.dec_items, sl.rx, wait_events=[sl.digests_ready] + ([prev.dec_done] if prev else []),
                            master_event=sl.dec_master, data_events=[sl.cipher_ready])
+        sl.dec_done.record(sl.rx)             # before the copy-out: gates the next clip's receiver
         if e2e:
             with torch.cuda.stream(sl.rx):
                 for t in range(FRAMES):
