@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="length of each serving run (60 s = full config)")
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed-batch, serving and stress measurements")
     ap.add_argument("--no-stress", action="store_true", help="skip the 256 x 8K stress round trip")
+    ap.add_argument("--gate", default="chain", choices=["permute", "keystream", "chain"],
+                    help="what the next clip's LHCS_m waits for besides the chaining state (see round_trip)")
+    ap.add_argument("--no-partition", action="store_true", help="run LHCS_m on the same SMs as everything else")
+    ap.add_argument("--layout", default="throughput", choices=["latency", "throughput"], help="worker warp layout")
     ap.add_argument("--inflight", type=int, default=2,
                     help="clips in flight on separate buffers: the next clip's digest stage overlaps this clip's "
                          "keystreams; its chaotic stage waits for this clip")
@@ -246,6 +250,11 @@ def run_ours(args):
     host = torch.from_numpy(clip).pin_memory()
     key = si.key(rank)
     enc, dec = fhd.Cipher(key, n_workers=N_WORKERS), fhd.Cipher(key, n_workers=N_WORKERS)
+    if args.no_partition:
+        enc.set_partition(False)
+        dec.set_partition(False)
+    enc.set_layout(args.layout)
+    dec.set_layout(args.layout)
     sid, rid = enc.open_stream(), dec.open_stream()
     stream = torch.cuda.current_stream()
 
@@ -264,7 +273,7 @@ def run_ours(args):
             self.dec_items = [(rid, self.encs[t], self.decs[t], self.digs[t]) for t in range(FRAMES)]
             self.digests_ready, self.cipher_ready = torch.cuda.Event(), torch.cuda.Event()
             self.enc_master, self.dec_master, self.rx_done = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
-            self.dec_done = torch.cuda.Event()
+            self.dec_done, self.enc_ks, self.dec_ks = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
             self.used = False
             self.host_out = torch.empty_like(host).pin_memory()
             self.host_dig = torch.empty((FRAMES, 32), dtype=torch.uint8).pin_memory()
@@ -281,15 +290,25 @@ def run_ours(args):
                 for t in range(FRAMES):
                     sl.srcs[t].copy_(host[t], non_blocking=True)
         # The digest stage (integer work) of this clip runs at once, during the previous clip's keystreams
-        # (binary64 work); this clip's LHCS_m waits for the previous clip's sender (chaining order and
-        # ciphertext done) and receiver, so the FP64 pipes carry one clip's chaotic stage at a time.  (Gating
-        # LHCS_m on the previous keystreams only, so that the permutations overlap it, measured slower:
-        # LHCS_m then shares the SMs with the permutation kernels.)
-        enc.encrypt_frames(sl.enc_items, sl.tx, wait_events=[prev.enc_master, prev.cipher_ready] if prev else [],
-                           master_event=sl.enc_master, digest_event=sl.digests_ready)
+        # (binary64 work).  This clip's LHCS_m waits for the chaining state and, by --gate, for:
+        #   permute:   the previous clip's ciphertext and decrypted frames (all of its work);
+        #   keystream: the previous clip's two keystreams (its permutations overlap this LHCS_m);
+        #   chain:     nothing more (this clip's chaotic stage overlaps the previous clip's).
+        # With one clip in flight only `permute` applies (the same slot's events would alias).
+        gate = args.gate if prev is not None and prev is not sl else "permute"
+        if prev is None:
+            ew, dw = [], []
+        elif gate == "permute":
+            ew, dw = [prev.enc_master, prev.cipher_ready], [prev.dec_done]
+        elif gate == "keystream":
+            ew, dw = [prev.enc_master, prev.enc_ks, prev.dec_ks], [prev.dec_master, prev.enc_ks, prev.dec_ks]
+        else:
+            ew, dw = [prev.enc_master], [prev.dec_master]
+        enc.encrypt_frames(sl.enc_items, sl.tx, wait_events=ew, master_event=sl.enc_master,
+                           digest_event=sl.digests_ready, keystream_event=sl.enc_ks)
         sl.cipher_ready.record(sl.tx)
-        dec.decrypt_frames(sl.dec_items, sl.rx, wait_events=[sl.digests_ready] + ([prev.dec_done] if prev else []),
-                           master_event=sl.dec_master, data_events=[sl.cipher_ready])
+        dec.decrypt_frames(sl.dec_items, sl.rx, wait_events=[sl.digests_ready] + dw, master_event=sl.dec_master,
+                           data_events=[sl.cipher_ready], keystream_event=sl.dec_ks)
         sl.dec_done.record(sl.rx)             # before the copy-out: gates the next clip's receiver
         if e2e:
             with torch.cuda.stream(sl.rx):
@@ -463,7 +482,8 @@ def run_ours(args):
                                    "per GPU, n=32 workers, RK4 h=0.001; per step encrypt_frames on the sender's CUDA stream and "
                                    "decrypt_frames on the receiver's (its chaotic stage waits for the digests, its "
                                    "inverse permutation for the ciphertext)",
-                       "clips_in_flight": INF,
+                       "clips_in_flight": INF, "next_clip_gate": args.gate, "worker_layout": args.layout,
+                       "sm_partition": {"lhcs_m_sms": enc.partition()[0], "other_sms": enc.partition()[1]},
                        "frames_per_step": FRAMES * world, "l2": "inputs larger than L2 (~560 MB live per step)",
                        "parallelism": f"replicas x{world} (independent streams)",
                        "strip_width": tuned.get(f"{HGT}x{WID}x{CH}")},

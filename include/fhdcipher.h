@@ -236,6 +236,31 @@ int fhd_set_strip_width(uint32_t height, uint32_t width, uint32_t channels, uint
 
 /* ---- Instrumentation (not part of the cipher). ---- */
 
+/* SM partition (CUDA green contexts, on by default where the device and
+ * driver support them).  The chaining kernel LHCS_m (Algorithm 1) is one warp
+ * on a strictly sequential chain; beside the worker kernels it would share an
+ * SM's binary64 pipes with them.  With the partition on, each call forks from
+ * its CUDA stream to two internal streams, LHCS_m on a small partition of
+ * SMs (8 on GB300) and every other kernel of the call on the rest, and joins
+ * back, so results and ordering on the caller's stream are unchanged; calls
+ * on a stream that is being captured into a CUDA graph stay on that stream.
+ * cipher_set_partition(c, 0) turns it off for this handle; enabling fails
+ * with FHD_ERR_CUDA (and leaves it off) where partitioning is unavailable.
+ * cipher_get_partition reports the SM counts in use (0, 0 when off). */
+int cipher_set_partition(fhd_cipher *c, int enable);
+int cipher_get_partition(fhd_cipher *c, uint32_t *chain_sms, uint32_t *bulk_sms);
+
+/* Warp layout of the worker kernel (Sec. II-B), bit-identical results either
+ * way.  FHD_LAYOUT_LATENCY (default): six chains per warp, one variable per
+ * lane and two lanes holding constants; the shortest RK4 step (~2.0k cycles
+ * on GB300), for a batch that has the device to itself.
+ * FHD_LAYOUT_THROUGHPUT: eight chains per warp (four worker pairs) with
+ * selects instead of constant lanes; a longer step (~2.4k cycles) but 27 %
+ * fewer binary64 instructions per frame, for when several batches' workers
+ * share the FP64 pipes (clips in flight, many concurrent streams). */
+enum { FHD_LAYOUT_LATENCY = 0, FHD_LAYOUT_THROUGHPUT = 1 };
+int cipher_set_layout(fhd_cipher *c, int layout);
+
 /* Kernel kinds reported by cipher_profile_read, in this order. */
 enum { FHD_K_SHA = 0, FHD_K_MASTER = 1, FHD_K_KEYSTREAM = 2, FHD_K_ENCRYPT = 3, FHD_K_DECRYPT = 4, FHD_K_COUNT = 5 };
 

@@ -35,7 +35,8 @@ EXPORTS = (
     "fhd_permute_encrypt", "fhd_permute_decrypt", "fhd_strip_width", "fhd_set_strip_width", "fhd_version",
     "cipher_profile", "cipher_profile_read", "fhd_launch_count", "encrypt_frames_ex", "decrypt_frames_ex",
     "cipher_reserve", "fhd_frame_scratch_bytes", "fhd_frame_digest_noalloc", "cipher_verify_frames",
-    "decrypt_frames_split", "encrypt_frames_split", "cipher_profile_spans",
+    "decrypt_frames_split", "encrypt_frames_split", "cipher_profile_spans", "cipher_set_partition",
+    "cipher_get_partition", "cipher_set_layout",
 )
 KERNEL_KINDS = ("sha", "master", "keystream", "encrypt", "decrypt")
 
@@ -99,6 +100,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "decrypt_frames_split": (i32, [P, u32, P, P, P, u32, P, u32, P, P]),
             "encrypt_frames_split": (i32, [P, u32, P, P, P, u32, P, P, P]),
             "cipher_profile_spans": (i32, [P, P, u32, P, P, P, P]),
+            "cipher_set_partition": (i32, [P, i32]),
+            "cipher_get_partition": (i32, [P, P, P]),
+            "cipher_set_layout": (i32, [P, i32]),
             "cipher_reserve": (i32, [P, P, u64]),
             "cipher_verify_frames": (i32, [P, u32, P, P, P]),
             "fhd_frame_scratch_bytes": (u64, [u32, u32, u32, u32]),
@@ -328,6 +332,20 @@ class Cipher:
         _check(lib.cipher_profile_spans(self._handle(), ctypes.c_void_p(origin.cuda_event), n, kinds, t0, t1,
                                         ctypes.byref(count)), self._h)
         return [(KERNEL_KINDS[kinds[i]], t0[i], t1[i]) for i in range(min(n, count.value))]
+
+    def set_partition(self, enable: bool):
+        """Run LHCS_m on its own small SM partition (green contexts) or not."""
+        _check(load().cipher_set_partition(self._handle(), 1 if enable else 0), self._h)
+
+    def set_layout(self, layout: str):
+        """Worker warp layout: "latency" (six chains per warp) or "throughput" (eight)."""
+        _check(load().cipher_set_layout(self._handle(), {"latency": 0, "throughput": 1}[layout]), self._h)
+
+    def partition(self) -> tuple:
+        """(SMs of the LHCS_m partition, SMs of the rest); (0, 0) when off."""
+        a, b = ctypes.c_uint32(), ctypes.c_uint32()
+        _check(load().cipher_get_partition(self._handle(), ctypes.byref(a), ctypes.byref(b)), self._h)
+        return a.value, b.value
 
     def last_error(self) -> str:
         return load().cipher_last_error(self._h).decode(errors="replace")

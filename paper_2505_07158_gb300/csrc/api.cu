@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>   // driver-API types only: its entry points are fetched at run time
+
 #include "common.cuh"
 
 using fhd::Batch;
@@ -29,8 +31,20 @@ struct fhd_cipher {
     unsigned *d_status = nullptr;
     // Scratch (sub-frame digests, LHCS_m iterates, D, B) per CUDA stream, so
     // that calls on different CUDA streams can run concurrently.
-    struct Scratch { cudaStream_t stream; uint8_t *ptr; size_t cap; };
+    // With the SM partition on, a call on `stream` forks to two internal
+    // streams: `chain` in the small partition (LHCS_m) and `bulk` in the rest
+    // (digests, workers, permutation), and joins back; ev = fork, digests,
+    // master, join.
+    struct Scratch {
+        cudaStream_t stream;
+        uint8_t *ptr;
+        size_t cap;
+        cudaStream_t chain = nullptr, bulk = nullptr;
+        cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    };
     std::vector<Scratch> scratch;
+    bool partition = false;
+    int layout = FHD_LAYOUT_LATENCY;
     cudaStream_t last_stream = nullptr;
     std::string err;
     bool prof = false;
@@ -150,6 +164,124 @@ cudaError_t prepare_device() {
     return e;
 }
 
+// ---- SM partition (CUDA green contexts).  The chaining kernel (LHCS_m) is a
+// single warp on a strictly sequential chain; beside the worker kernels it
+// would share an SM sub-partition's FP64 pipe with them.  A small partition
+// of kChainSms SMs runs only LHCS_m, the rest runs everything else, so the
+// next batch's LHCS_m can overlap this batch's workers at full speed.
+constexpr unsigned kChainSms = 8;   // the minimum partition on sm_90 and later
+
+struct DriverApi {
+    CUresult (*deviceGet)(CUdevice *, int) = nullptr;
+    CUresult (*getDevResource)(CUdevice, CUdevResource *, CUdevResourceType) = nullptr;
+    CUresult (*smSplit)(CUdevResource *, unsigned *, const CUdevResource *, CUdevResource *, unsigned, unsigned) = nullptr;
+    CUresult (*genDesc)(CUdevResourceDesc *, CUdevResource *, unsigned) = nullptr;
+    CUresult (*greenCreate)(CUgreenCtx *, CUdevResourceDesc, CUdevice, unsigned) = nullptr;
+    CUresult (*greenStream)(CUstream *, CUgreenCtx, unsigned, int) = nullptr;
+    CUresult (*streamDestroy)(CUstream) = nullptr;
+};
+
+struct DevicePartition {
+    bool tried = false, ok = false;
+    CUgreenCtx chain = nullptr, bulk = nullptr;
+    unsigned chain_sms = 0, bulk_sms = 0;
+    std::string why;   // the step that failed, when !ok
+};
+
+std::mutex g_part_mu;
+DriverApi g_drv;
+bool g_drv_tried = false, g_drv_ok = false;
+DevicePartition g_part[64];
+
+std::string g_drv_why;
+
+bool load_driver_api() {
+    auto get = [](const char *name, void **fn) {
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        cudaError_t e = cudaGetDriverEntryPointByVersion(name, fn, CUDA_VERSION, cudaEnableDefault, &q);
+        if (e == cudaSuccess && q == cudaDriverEntryPointSuccess && *fn != nullptr) return true;
+        g_drv_why = std::string("driver entry point ") + name + ": " + cudaGetErrorString(e) + ", query " +
+                    std::to_string((int)q);
+        return false;
+    };
+    return get("cuDeviceGet", (void **)&g_drv.deviceGet) &&
+           get("cuDeviceGetDevResource", (void **)&g_drv.getDevResource) &&
+           get("cuDevSmResourceSplitByCount", (void **)&g_drv.smSplit) &&
+           get("cuDevResourceGenerateDesc", (void **)&g_drv.genDesc) &&
+           get("cuGreenCtxCreate", (void **)&g_drv.greenCreate) &&
+           get("cuGreenCtxStreamCreate", (void **)&g_drv.greenStream) &&
+           get("cuStreamDestroy", (void **)&g_drv.streamDestroy);
+}
+
+// The partition of device `dev`, created on first use; nullptr when the
+// device or driver cannot partition (then calls stay on the caller's stream).
+const DevicePartition *device_partition(int dev) {
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_part_mu);
+    DevicePartition &p = g_part[dev];
+    if (!p.tried) {
+        p.tried = true;
+        if (!g_drv_tried) {
+            g_drv_tried = true;
+            g_drv_ok = load_driver_api();
+        }
+        CUdevice cd;
+        CUdevResource all{}, part{}, rest{};
+        CUdevResourceDesc da = nullptr, db = nullptr;
+        unsigned nb = 1;
+        CUresult r = CUDA_SUCCESS;
+        auto step = [&](CUresult rr, const char *what) {
+            r = rr;
+            if (rr != CUDA_SUCCESS) p.why = std::string(what) + " failed with CUresult " + std::to_string((int)rr);
+            return rr == CUDA_SUCCESS;
+        };
+        if (!g_drv_ok) {
+            p.why = g_drv_why;
+        } else if (step(g_drv.deviceGet(&cd, dev), "cuDeviceGet") &&
+                   step(g_drv.getDevResource(cd, &all, CU_DEV_RESOURCE_TYPE_SM), "cuDeviceGetDevResource")) {
+            if (all.sm.smCount < 4 * kChainSms) {
+                p.why = "too few SMs to partition";
+            } else if (step(g_drv.smSplit(&part, &nb, &all, &rest, 0, kChainSms), "cuDevSmResourceSplitByCount") &&
+                       step(g_drv.genDesc(&da, &part, 1), "cuDevResourceGenerateDesc") &&
+                       step(g_drv.genDesc(&db, &rest, 1), "cuDevResourceGenerateDesc") &&
+                       step(g_drv.greenCreate(&p.chain, da, cd, CU_GREEN_CTX_DEFAULT_STREAM), "cuGreenCtxCreate") &&
+                       step(g_drv.greenCreate(&p.bulk, db, cd, CU_GREEN_CTX_DEFAULT_STREAM), "cuGreenCtxCreate")) {
+                p.ok = true;
+                p.chain_sms = part.sm.smCount;
+                p.bulk_sms = rest.sm.smCount;
+            }
+        }
+        (void)r;
+    }
+    return p.ok ? &p : nullptr;
+}
+
+// The internal streams and events of caller stream `sc` (created on first use).
+cudaError_t partition_streams(fhd_cipher *c, fhd_cipher::Scratch &sc) {
+    if (sc.chain) return cudaSuccess;
+    const DevicePartition *p = device_partition(c->device);
+    if (!p) return cudaErrorNotSupported;
+    CUstream a = nullptr, b = nullptr;
+    if (g_drv.greenStream(&a, p->chain, CU_STREAM_NON_BLOCKING, 0) != CUDA_SUCCESS) return cudaErrorNotSupported;
+    if (g_drv.greenStream(&b, p->bulk, CU_STREAM_NON_BLOCKING, 0) != CUDA_SUCCESS) {
+        g_drv.streamDestroy(a);
+        return cudaErrorNotSupported;
+    }
+    for (auto &e : sc.ev) {
+        cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        if (r != cudaSuccess) return r;
+    }
+    sc.chain = (cudaStream_t)a;
+    sc.bulk = (cudaStream_t)b;
+    return cudaSuccess;
+}
+
+fhd_cipher::Scratch *scratch_of(fhd_cipher *c, cudaStream_t s) {
+    for (auto &sc : c->scratch)
+        if (sc.stream == s) return &sc;
+    return nullptr;
+}
+
 bool check_dims(uint32_t h, uint32_t w, uint32_t C, std::string &why) {
     if (h == 0 || w == 0 || C == 0) { why = "frame dimensions must be non-zero"; return false; }
     if (C > 4) { why = "channels must be 1..4"; return false; }
@@ -167,6 +299,7 @@ int init_common(const double ic[5], uint32_t n, double h, const uint32_t u[4], f
     if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("prepare: ") + cudaGetErrorString(e));
     fhd_cipher *c = new fhd_cipher();
     c->device = dev;
+    c->partition = device_partition(dev) != nullptr;
     c->n = n;
     c->h = h;
     for (int m = 0; m < 4; ++m) c->u[m] = u[m];
@@ -230,10 +363,15 @@ int ensure_scratch(fhd_cipher *c, cudaStream_t s, size_t need, uint8_t **out) {
     if (capturing(s))
         return fail(c, FHD_ERR_STATE, "scratch too small during CUDA graph capture: run the batch once uncaptured first");
     if (!slot) {
-        c->scratch.push_back({s, nullptr, 0});
+        c->scratch.push_back({});
         slot = &c->scratch.back();
+        slot->stream = s;
     }
     cudaStreamSynchronize(s);
+    if (slot->chain) {   // work of the current call may still be on the internal streams
+        cudaStreamSynchronize(slot->chain);
+        cudaStreamSynchronize(slot->bulk);
+    }
     cudaFree(slot->ptr);
     slot->ptr = nullptr;
     slot->cap = 0;
@@ -276,6 +414,9 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
     cudaError_t e = prepare_device();
     if (e != cudaSuccess) return cuda_fail(c, e, "prepare");
     static thread_local Batch b;   // ~12 KB: kept off the stack
+    bool part = false;
+    cudaStream_t sc = s, sb = s;
+    cudaEvent_t *ev = nullptr;
     for (uint32_t base = 0; base < count; base += fhd::kMaxBatch) {
         uint32_t m = count - base < (uint32_t)fhd::kMaxBatch ? count - base : (uint32_t)fhd::kMaxBatch;
         std::memset(&b, 0, sizeof b);
@@ -293,6 +434,21 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
         uint8_t *p = nullptr;
         int rc = ensure_scratch(c, s, need, &p);
         if (rc != FHD_OK) return rc;
+        if (base == 0) {
+            // Streams of this call: with the SM partition (and outside graph capture), LHCS_m runs on
+            // `sc` (small partition) and everything else on `sb` (the rest), forked from and joined
+            // back to the caller's stream; otherwise everything runs on the caller's stream.
+            fhd_cipher::Scratch *slot = scratch_of(c, s);
+            part = c->partition && slot && !capturing(s) && partition_streams(c, *slot) == cudaSuccess;
+            if (part) {
+                sc = slot->chain;
+                sb = slot->bulk;
+                ev = slot->ev;
+                if ((e = cudaEventRecord(ev[0], s)) != cudaSuccess || (e = cudaStreamWaitEvent(sb, ev[0], 0)) != cudaSuccess ||
+                    (e = cudaStreamWaitEvent(sc, ev[0], 0)) != cudaSuccess)
+                    return cuda_fail(c, e, "fork");
+            }
+        }
         uint32_t ctas = 0, rctas = 0;
         for (uint32_t k = 0; k < m; ++k) {
             const fhd_frame &f = frames[base + k];
@@ -335,33 +491,41 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
         }
         b.group_begin[b.groups] = (uint16_t)pos;
         if (encrypt) {
-            if ((e = timed(c, FHD_K_SHA, s, [&] {
-                     cudaError_t r = fhd::launch_sha_subframes(b, s);
-                     return r == cudaSuccess ? fhd::launch_fold_batch(b, s) : r;
+            if ((e = timed(c, FHD_K_SHA, sb, [&] {
+                     cudaError_t r = fhd::launch_sha_subframes(b, sb);
+                     return r == cudaSuccess ? fhd::launch_fold_batch(b, sb) : r;
                  })) != cudaSuccess)
                 return cuda_fail(c, e, "sha launch");
-            if (digests_done && base + m >= count && (e = cudaEventRecord(digests_done, s)) != cudaSuccess)
+            if (digests_done && base + m >= count && (e = cudaEventRecord(digests_done, sb)) != cudaSuccess)
                 return cuda_fail(c, e, "record digest event");
         }
+        // LHCS_m of this group of frames after the bulk stream's work so far: this group's digests,
+        // and the previous group's workers, which read the iterates this LHCS_m overwrites.
+        if (part && ((e = cudaEventRecord(ev[1], sb)) != cudaSuccess || (e = cudaStreamWaitEvent(sc, ev[1], 0)) != cudaSuccess))
+            return cuda_fail(c, e, "bulk to chain stream");
         if (base == 0)
             for (uint32_t k = 0; k < n_wait; ++k)
-                if (wait_events[k] && (e = cudaStreamWaitEvent(s, (cudaEvent_t)wait_events[k], 0)) != cudaSuccess)
+                if (wait_events[k] && (e = cudaStreamWaitEvent(sc, (cudaEvent_t)wait_events[k], 0)) != cudaSuccess)
                     return cuda_fail(c, e, "wait event");
-        if ((e = timed(c, FHD_K_MASTER, s, [&] { return fhd::launch_master(b, c->d_states, c->d_status, s); })) != cudaSuccess)
+        if ((e = timed(c, FHD_K_MASTER, sc, [&] { return fhd::launch_master(b, c->d_states, c->d_status, sc); })) != cudaSuccess)
             return cuda_fail(c, e, "master launch");
-        if (master_done && base + m >= count && (e = cudaEventRecord(master_done, s)) != cudaSuccess)
+        if (master_done && base + m >= count && (e = cudaEventRecord(master_done, sc)) != cudaSuccess)
             return cuda_fail(c, e, "record master event");
-        if ((e = timed(c, FHD_K_KEYSTREAM, s, [&] { return fhd::launch_keystream(b, s); })) != cudaSuccess)
+        if (part && ((e = cudaEventRecord(ev[2], sc)) != cudaSuccess || (e = cudaStreamWaitEvent(sb, ev[2], 0)) != cudaSuccess))
+            return cuda_fail(c, e, "master to bulk stream");
+        if ((e = timed(c, FHD_K_KEYSTREAM, sb, [&] { return fhd::launch_keystream(b, sb, c->layout == FHD_LAYOUT_THROUGHPUT); })) != cudaSuccess)
             return cuda_fail(c, e, "keystream launch");
-        if (keystream_done && base + m >= count && (e = cudaEventRecord(keystream_done, s)) != cudaSuccess)
+        if (keystream_done && base + m >= count && (e = cudaEventRecord(keystream_done, sb)) != cudaSuccess)
             return cuda_fail(c, e, "record keystream event");
         if (base == 0)   // the first reader of frames[].src after the digest stage
             for (uint32_t k = 0; k < n_data; ++k)
-                if (data_events[k] && (e = cudaStreamWaitEvent(s, (cudaEvent_t)data_events[k], 0)) != cudaSuccess)
+                if (data_events[k] && (e = cudaStreamWaitEvent(sb, (cudaEvent_t)data_events[k], 0)) != cudaSuccess)
                     return cuda_fail(c, e, "wait data event");
-        if ((e = timed(c, encrypt ? FHD_K_ENCRYPT : FHD_K_DECRYPT, s, [&] { return fhd::launch_permute(b, encrypt, s); })) != cudaSuccess)
+        if ((e = timed(c, encrypt ? FHD_K_ENCRYPT : FHD_K_DECRYPT, sb, [&] { return fhd::launch_permute(b, encrypt, sb); })) != cudaSuccess)
             return cuda_fail(c, e, "permute launch");
     }
+    if (part && ((e = cudaEventRecord(ev[3], sb)) != cudaSuccess || (e = cudaStreamWaitEvent(s, ev[3], 0)) != cudaSuccess))
+        return cuda_fail(c, e, "join");
     c->last_stream = s;
     return FHD_OK;
 }
@@ -584,12 +748,50 @@ int cipher_profile_spans(fhd_cipher *c, void *origin, uint32_t cap, int32_t *kin
 
 uint64_t fhd_launch_count(void) { return g_launches.load(); }
 
+int cipher_set_partition(fhd_cipher *c, int enable) {
+    if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
+    if (!enable) { c->partition = false; return FHD_OK; }
+    if (!device_partition(c->device)) {
+        c->partition = false;
+        std::string why;
+        {
+            std::lock_guard<std::mutex> lk(g_part_mu);
+            why = c->device >= 0 && c->device < 64 ? g_part[c->device].why : "device index";
+        }
+        return fail(c, FHD_ERR_CUDA, "the device or driver cannot partition its SMs (green contexts): " + why);
+    }
+    c->partition = true;
+    return FHD_OK;
+}
+
+int cipher_set_layout(fhd_cipher *c, int layout) {
+    if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
+    if (layout != FHD_LAYOUT_LATENCY && layout != FHD_LAYOUT_THROUGHPUT)
+        return fail(c, FHD_ERR_INVALID_ARG, "unknown worker layout");
+    c->layout = layout;
+    return FHD_OK;
+}
+
+int cipher_get_partition(fhd_cipher *c, uint32_t *chain_sms, uint32_t *bulk_sms) {
+    if (!c || !chain_sms || !bulk_sms) return fail(c, FHD_ERR_INVALID_ARG, "null argument");
+    const DevicePartition *p = c->partition ? device_partition(c->device) : nullptr;
+    *chain_sms = p ? p->chain_sms : 0;
+    *bulk_sms = p ? p->bulk_sms : 0;
+    return FHD_OK;
+}
+
 void cipher_destroy(fhd_cipher *c) {
     if (!c) return;
     cudaDeviceSynchronize();
     for (auto &r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->pool) cudaEventDestroy(e);
-    for (auto &sc : c->scratch) cudaFree(sc.ptr);
+    for (auto &sc : c->scratch) {
+        cudaFree(sc.ptr);
+        for (auto e : sc.ev)
+            if (e) cudaEventDestroy(e);
+        if (sc.chain) g_drv.streamDestroy((CUstream)sc.chain);
+        if (sc.bulk) g_drv.streamDestroy((CUstream)sc.bulk);
+    }
     cudaFree(c->d_states);
     cudaFree(c->d_status);
     delete c;

@@ -108,6 +108,57 @@ __device__ __forceinline__ void rk4_step_lanes(double &s, const LaneRole &r, con
     }
 }
 
+// The same step with eight chains per warp (all 32 lanes carry variables, so
+// no lane holds a constant): three shuffles per stage, and the operands that
+// are a variable on some lanes and a constant on others are selected:
+//   v = x: p = fma(X, -1, Y), q = fma(W, 1, -0);  v = y: p = fma(X, rho, -0), p2 = fma(p, 1, -Y);
+//   v = z: p = fma(Z, beta, -0), p2 = -p;          v = w: p = fma(W, gamma, -0);
+// q = X Z, X Y, Y Z for y, z, w.  Fewer binary64 instructions per chain step
+// (27 per eight chains), a longer step (selects after the shuffles).
+struct LaneRole8 {
+    double Pb, B2, kS;
+    int s1, s2, s3;
+    bool vx, vy;
+};
+
+__device__ __forceinline__ LaneRole8 lane_role8(int lane, double gamma) {
+    LaneRole8 r;
+    const int v = lane & 3, base = lane & ~3;
+    r.Pb = v == 0 ? -1.0 : v == 1 ? kRho : v == 2 ? kBeta : gamma;
+    r.B2 = v == 0 ? kSigma : v == 2 ? -1.0 : 1.0;
+    r.kS = (v == 0 || v == 2) ? 1.0 : -1.0;
+    r.s1 = base + (v == 1 ? 0 : v);                        // X, X, Z, W
+    r.s2 = base + (v == 0 ? 3 : v == 3 ? 1 : 0);           // W, X, X, Y
+    r.s3 = base + ((v == 0 || v == 2) ? 1 : 2);            // Y, Z, Y, Z
+    r.vx = v == 0;
+    r.vy = v == 1;
+    return r;
+}
+
+__device__ __forceinline__ void rk4_step_lanes8(double &s, const LaneRole8 &r, const Rk4 &c) {
+    double tin = s, acc = 0.0;
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+        const double a = __shfl_sync(0xffffffffu, tin, r.s1);
+        const double b = __shfl_sync(0xffffffffu, tin, r.s2);
+        const double d = __shfl_sync(0xffffffffu, tin, r.s3);
+        const double Pc = r.vx ? d : -0.0;
+        const double Qb = r.vx ? 1.0 : d;
+        const double P2 = r.vy ? tin : 0.0;
+        const double p = __fma_rn(a, r.Pb, Pc);
+        const double q = __fma_rn(b, Qb, -0.0);
+        const double p2 = __fma_rn(p, r.B2, -P2);
+        const double k = __fma_rn(q, r.kS, p2);
+        if (st < 3) {
+            tin = __dadd_rn(s, __dmul_rn(st == 2 ? c.h : c.hh, k));
+            acc = st == 0 ? k : __fma_rn(k, 2.0, acc);
+        } else {
+            acc = __dadd_rn(acc, k);
+            s = __dadd_rn(s, __dmul_rn(c.h6, acc));
+        }
+    }
+}
+
 // Sec. II-A, Fig. 1a: reconstruct one initial condition from 8 digest bytes
 // (two for the integer part mod u, six for the 48-bit fraction), v by
 // magnitude; non-finite or |v| >= 2^52 contributes 0 and 0.
@@ -202,19 +253,38 @@ __device__ __forceinline__ WorkerSlice worker_slice(uint64_t LD, uint64_t LB, ui
     return w;
 }
 
-// K2b: one warp carries three worker pairs (six chains) of one frame for the
-// frame's uniform trip count; lane 4c + v holds variable v of chain c, chains
-// 2q and 2q + 1 are pair q, so the partner of a lane is lane ^ 4.
+// Bytes of one step: the pair's XOR of the 6 low mantissa bytes of each
+// variable; this lane writes its half (3 bytes) at stream position pos0 on.
+__device__ __forceinline__ void emit_bytes(double s, bool active, uint64_t pos0, uint64_t need, uint64_t ndb, int half,
+                                           uint8_t *Dbytes, uint8_t *Bp) {
+    const unsigned long long mine = (unsigned long long)__double_as_longlong(s) & 0xffffffffffffull;
+    const unsigned long long x = mine ^ __shfl_xor_sync(0xffffffffu, mine, 4);
+    if (active && pos0 < need) {
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) {
+            const uint64_t pos = pos0 + half + bb;
+            const uint8_t byte = (uint8_t)(x >> (8 * (half + bb)));
+            if (pos < ndb) Dbytes[pos] = byte;
+            else if (pos < need) Bp[pos - ndb] = byte;
+        }
+    }
+}
+
+// K2b: one warp carries kPairs worker pairs (three with the six-chain step,
+// four with the eight-chain step) of one frame for the frame's uniform trip
+// count; lane 4c + v holds variable v of chain c, chains 2q and 2q + 1 are
+// pair q, so the partner of a lane is lane ^ 4.
+template <int kPairs>
 __global__ void __launch_bounds__(32) keystream_kernel(const __grid_constant__ Batch b) {
-    const uint32_t wpf = (b.n + kPairsPerWarp - 1) / kPairsPerWarp;
+    const uint32_t wpf = (b.n + kPairs - 1) / kPairs;
     const uint32_t f = blockIdx.x / wpf, pg = blockIdx.x % wpf;
     if (f >= b.count) return;
     const FrameDesc &fd = b.f[f];
     const uint32_t n = b.n;
     const Rk4 c{b.hstep, b.hhalf, b.hsixth};
     const int lane = threadIdx.x, v = lane & 3, ch = lane >> 2;
-    const uint32_t p = pg * kPairsPerWarp + (ch >> 1);
-    const bool active = lane < 4 * kChainsPerWarp && p < n;
+    const uint32_t p = pg * kPairs + (ch >> 1);
+    const bool active = lane < 8 * kPairs && p < n;
     const uint64_t LD = (uint64_t)fd.C * (fd.h + fd.w);
     const uint64_t LB = fd.N;
     WorkerSlice ws{0, 0, 0, 0};
@@ -223,25 +293,24 @@ __global__ void __launch_bounds__(32) keystream_kernel(const __grid_constant__ B
     // Uniform trip count: the longest slice of the frame.
     const uint64_t need_max = 2 * ((LD + n - 1) / n) + (LB + n - 1) / n;
     const uint64_t T = (need_max + 23) / 24;
-    const LaneRole role = lane_role(lane, fd.gamma);
-    double s = lane_init(lane, active ? fd.IR[4 * (2 * p + (ch & 1)) + v] : 0.0);
+    const double chain_value = active ? fd.IR[4 * (2 * p + (ch & 1)) + v] : 0.0;
     uint8_t *Dbytes = reinterpret_cast<uint8_t *>(fd.D) + 2 * ws.d0;
     uint8_t *Bp = fd.B + ws.b0;
     const uint64_t ndb = 2 * ws.nd;
     const int half = (ch & 1) * 3;
-    for (uint64_t t = 0; t < T; ++t) {
-        rk4_step_lanes(s, role, c);
-        const unsigned long long mine = (unsigned long long)__double_as_longlong(s) & 0xffffffffffffull;
-        const unsigned long long x = mine ^ __shfl_xor_sync(0xffffffffu, mine, 4);
-        const uint64_t pos0 = 24 * t + 6 * v;
-        if (active && pos0 < need) {
-#pragma unroll
-            for (int bb = 0; bb < 3; ++bb) {
-                const uint64_t pos = pos0 + half + bb;
-                const uint8_t byte = (uint8_t)(x >> (8 * (half + bb)));
-                if (pos < ndb) Dbytes[pos] = byte;
-                else if (pos < need) Bp[pos - ndb] = byte;
-            }
+    if (kPairs == kPairsPerWarp) {
+        const LaneRole role = lane_role(lane, fd.gamma);
+        double s = lane_init(lane, chain_value);
+        for (uint64_t t = 0; t < T; ++t) {
+            rk4_step_lanes(s, role, c);
+            emit_bytes(s, active, 24 * t + 6 * v, need, ndb, half, Dbytes, Bp);
+        }
+    } else {
+        const LaneRole8 role = lane_role8(lane, fd.gamma);
+        double s = chain_value;
+        for (uint64_t t = 0; t < T; ++t) {
+            rk4_step_lanes8(s, role, c);
+            emit_bytes(s, active, 24 * t + 6 * v, need, ndb, half, Dbytes, Bp);
         }
     }
 }
@@ -263,10 +332,16 @@ cudaError_t launch_master_raw(double *state5, const uint8_t *H, uint32_t n, doub
     return cudaGetLastError();
 }
 
-cudaError_t launch_keystream(const Batch &b, cudaStream_t s) {
+cudaError_t launch_keystream(const Batch &b, cudaStream_t s, bool dense) {
     if (!b.count) return cudaSuccess;
+    if (dense) {
+        const uint32_t wpf = (b.n + 3) / 4;
+        keystream_kernel<4><<<b.count * wpf, 32, 0, s>>>(b);
+        note_launch();
+        return cudaGetLastError();
+    }
     const uint32_t wpf = (b.n + kPairsPerWarp - 1) / kPairsPerWarp;
-    keystream_kernel<<<b.count * wpf, 32, 0, s>>>(b);
+    keystream_kernel<kPairsPerWarp><<<b.count * wpf, 32, 0, s>>>(b);
     note_launch();
     return cudaGetLastError();
 }

@@ -179,3 +179,88 @@ def test_launch_count_per_call():
     torch.cuda.synchronize()
     assert (l1 - l0, l2 - l1) == (6, 4)
     assert torch.equal(R, F)
+
+
+def test_sm_partition_matches_single_stream():
+    """The SM partition (LHCS_m on its own SMs, the rest on the others) changes where kernels run,
+    not what they compute: a mixed batch encrypted with it on and off is byte-identical, and both
+    match the oracle."""
+    shapes = [(60, 100, 3), (32, 48, 1), (96, 128, 3)]
+    key = si.key(630)
+    frames = [to_dev(si.gradient_frame(*s, t=t, seed=631)) for t, s in enumerate(shapes)]
+    outs = []
+    for on in (True, False):
+        c = fhd.Cipher(key)
+        if not on:
+            c.set_partition(False)
+        sid = c.open_stream()
+        chain, bulk = c.partition()
+        if on and chain:
+            assert bulk > chain and (chain + bulk) == torch.cuda.get_device_properties(0).multi_processor_count
+        if not on:
+            assert (chain, bulk) == (0, 0)
+        E = [torch.empty_like(f) for f in frames]
+        H = torch.empty((len(frames), 32), dtype=torch.uint8, device=dev())
+        s = torch.cuda.Stream()
+        c.encrypt_frames([(sid, frames[k], E[k], H[k]) for k in range(len(frames))], stream=s)
+        torch.cuda.synchronize()
+        outs.append(([host(e) for e in E], host(H)))
+    for k in range(len(frames)):
+        assert np.array_equal(outs[0][0][k], outs[1][0][k]), k
+    assert np.array_equal(outs[0][1], outs[1][1])
+    ref = oracle.Stream.from_key(key)
+    for k in range(len(frames)):
+        E_ref, H_ref = ref.encrypt(host(frames[k]))
+        assert np.array_equal(outs[0][0][k], E_ref), k
+
+
+def test_more_than_one_descriptor_group():
+    """130 frames of one stream in one call (two groups of at most 128 descriptors): the groups
+    reuse the scratch, so each group's LHCS_m must wait for the previous group's workers; with the
+    SM partition they run on different internal streams."""
+    key = si.key(640)
+    F = 130
+    frames = torch.stack([to_dev(si.uniform_frame(8, 16, 3, seed=641 + t)) for t in range(F)])
+    snd, rcv = fhd.Cipher(key), fhd.Cipher(key)
+    sid, rid = snd.open_stream(), rcv.open_stream()
+    E, R = torch.empty_like(frames), torch.empty_like(frames)
+    H = torch.empty((F, 32), dtype=torch.uint8, device=dev())
+    snd.encrypt_frames([(sid, frames[t], E[t], H[t]) for t in range(F)])
+    rcv.decrypt_frames([(rid, E[t], R[t], H[t]) for t in range(F)])
+    torch.cuda.synchronize()
+    assert torch.equal(R, frames)
+    ref = oracle.Stream.from_key(key)
+    for t in range(F):
+        E_ref, H_ref = ref.encrypt(host(frames[t]))
+        if t in (0, 127, 128, 129):
+            assert np.array_equal(host(E[t]), E_ref), t
+            assert bytes(host(H[t])) == H_ref, t
+
+
+@pytest.mark.parametrize("layout", ["latency", "throughput"])
+def test_worker_layouts_match_oracle(layout):
+    """Both warp layouts of the worker kernel (six chains per warp with constant lanes, eight with
+    selects) produce the oracle's bytes, for worker counts that fill and do not fill the last warp."""
+    shapes = [(40, 56, 3), (24, 40, 1)]
+    for n in (5, 8, 32):
+        key = si.key(650 + n)
+        frames = [to_dev(si.uniform_frame(*s, seed=651 + n + k)) for k, s in enumerate(shapes)]
+        c = fhd.Cipher(key, n_workers=n)
+        c.set_layout(layout)
+        d = fhd.Cipher(key, n_workers=n)
+        d.set_layout(layout)
+        sid, rid = c.open_stream(), d.open_stream()
+        E = [torch.empty_like(f) for f in frames]
+        R = [torch.empty_like(f) for f in frames]
+        H = torch.empty((len(frames), 32), dtype=torch.uint8, device=dev())
+        c.encrypt_frames([(sid, frames[k], E[k], H[k]) for k in range(len(frames))])
+        d.decrypt_frames([(rid, E[k], R[k], H[k]) for k in range(len(frames))])
+        torch.cuda.synchronize()
+        ref = oracle.Stream.from_key(key, n=n)
+        for k in range(len(frames)):
+            E_ref, H_ref = ref.encrypt(host(frames[k]))
+            assert np.array_equal(host(E[k]), E_ref), (layout, n, k)
+            assert bytes(host(H[k])) == H_ref
+            assert torch.equal(R[k], frames[k])
+    with pytest.raises(KeyError):
+        c.set_layout("fast")
