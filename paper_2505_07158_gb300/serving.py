@@ -58,9 +58,14 @@ class Server:
 
     def __init__(self, keys, shapes, frame_pool, n_workers: int = 32, budget_bytes: int = 20 << 30,
                  lanes: int = 16, slots_per_lane: int = 1, max_batch: int = 64, fingerprint: bool = False,
-                 outputs_per_shape: int = 32):
+                 outputs_per_shape: int = 32, partition: bool = False):
         self.n = n_workers
         self.cipher = _lib.Cipher(keys[0], n_workers=n_workers)
+        # The lanes already overlap the frames of all streams; the SM partition would add two internal
+        # CUDA streams per lane, more than a context's hardware queues, and lanes would then wait on
+        # each other (measured: p50 12 -> 31 ms at 30 fps).  Off unless asked for.
+        if not partition:
+            self.cipher.set_partition(False)
         self.sids = [self.cipher.open_stream(k) for k in keys]
         self.shapes = list(shapes)
         self.pool = frame_pool               # shape -> list of device frames (inputs)
