@@ -49,8 +49,8 @@ RK4_FP64_OPS = 104      # per chain step: 4 x 13 (Eq. 1) + 3 x 8 (stages) + 4 x 
 # DRAM bytes (read + write) per 1080p frame of one launch, from the ncu capture summarised in
 # profiles/ncu_hot_kernels_clip1080p_4frames.md (4 frames per launch, scaled by frames; cold caches,
 # writes still in L2 at kernel end not counted); None where the kernel changed after that capture.
-TRAFFIC_PER_FRAME = {"keystream": 24832 / 4, "encrypt": (24923136 + 13824 + 49838848 + 910592) / 4,
-                     "decrypt": (49840896 + 952576 + 24923392 + 33024) / 4, "sha": 24936192 / 4,
+TRAFFIC_PER_FRAME = {"keystream": 41984 / 4, "encrypt": (24924000 + 2000 + 49840000 + 814000) / 4,
+                     "decrypt": (49841000 + 941000 + 24924000 + 6000) / 4, "sha": 24967000 / 4,
                      "master": 9216 / 4}
 
 
