@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="length of each serving run (60 s = full config)")
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed-batch, serving and stress measurements")
     ap.add_argument("--no-stress", action="store_true", help="skip the 256 x 8K stress round trip")
-    ap.add_argument("--gate", default="chain", choices=["permute", "keystream", "chain"],
+    ap.add_argument("--gate", default="chain", choices=["permute", "keystream", "chain", "window"],
                     help="what the next clip's LHCS_m waits for besides the chaining state (see round_trip)")
     ap.add_argument("--no-partition", action="store_true", help="run LHCS_m on the same SMs as everything else")
     ap.add_argument("--layout", default="throughput", choices=["latency", "throughput"], help="worker warp layout")
@@ -280,10 +280,10 @@ def run_ours(args):
             self.host_dig = torch.empty((FRAMES, 32), dtype=torch.uint8).pin_memory()
 
     slots = [Slot() for _ in range(max(1, args.inflight))]
-    last = [None]            # slot of the previous clip: the chaining state advances clip after clip
+    last = [None, None]      # slots of the previous two clips: the chaining state advances clip after clip
 
     def round_trip(sl, e2e=False):
-        prev = last[0]
+        prev, prev2 = last[-1], last[-2]
         if sl.used:
             sl.tx.wait_event(sl.rx_done)
         if e2e:
@@ -294,15 +294,25 @@ def run_ours(args):
         # (binary64 work).  This clip's LHCS_m waits for the chaining state and, by --gate, for:
         #   permute:   the previous clip's ciphertext and decrypted frames (all of its work);
         #   keystream: the previous clip's two keystreams (its permutations overlap this LHCS_m);
-        #   chain:     nothing more (this clip's chaotic stage overlaps the previous clip's).
-        # With one clip in flight only `permute` applies (the same slot's events would alias).
-        gate = args.gate if prev is not None and prev is not sl else "permute"
+        #   chain:     nothing more (this clip's chaotic stage overlaps the previous clip's);
+        #   window:    the keystreams of the clip before the previous one (at most two clips' keystreams
+        #              share the FP64 pipes, while a third clip's digest stage and LHCS_m run ahead).
+        # Events of this clip's own slot would alias (they are re-recorded by this very round trip), so with
+        # too few clips in flight a gate falls back to `permute`.
+        gate = args.gate
+        if gate == "window" and (prev2 is None or prev2 is sl):
+            gate = "chain"
+        if prev is sl:
+            gate = "permute"
         if prev is None:
             ew, dw = [], []
         elif gate == "permute":
             ew, dw = [prev.enc_master, prev.cipher_ready], [prev.dec_done]
         elif gate == "keystream":
             ew, dw = [prev.enc_master, prev.enc_ks, prev.dec_ks], [prev.dec_master, prev.enc_ks, prev.dec_ks]
+        elif gate == "window":
+            ew = [prev.enc_master, prev2.enc_ks, prev2.dec_ks]
+            dw = [prev.dec_master, prev2.enc_ks, prev2.dec_ks]
         else:
             ew, dw = [prev.enc_master], [prev.dec_master]
         enc.encrypt_frames(sl.enc_items, sl.tx, wait_events=ew, master_event=sl.enc_master,
@@ -319,7 +329,8 @@ def run_ours(args):
             sl.e2e_used = True
         sl.rx_done.record(sl.rx)
         sl.used = True
-        last[0] = sl
+        last.append(sl)
+        del last[:-2]
 
     def timed_steps(nsteps, inflight, e2e=False):
         """K round trips with up to `inflight` clips in flight; device time between two events on

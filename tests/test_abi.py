@@ -59,3 +59,19 @@ def test_strip_width_fits_shared_memory(lib):
     for h, w, c in [(480, 640, 3), (720, 1280, 3), (3, 5, 3), (12288, 7, 4), (12288, 16384, 3)]:
         P = fhd.fhd_strip_width(h, w, c)
         assert P >= 1 and ((h * P * c + 15) & ~15) <= 232448
+
+
+def test_host_side_checks_of_the_stream_ordering_and_placement_calls(lib):
+    """The split entry points, the SM-partition and layout switches and the profile spans reject a
+    null handle before touching a device, and report it through cipher_last_error."""
+    import paper_2505_07158_gb300 as fhd
+    ev = (ctypes.c_void_p * 1)()
+    n = ctypes.c_uint32()
+    assert lib.encrypt_frames_split(None, 1, None, None, None, 0, None, None, None) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.decrypt_frames_split(None, 1, None, None, None, 0, ev, 1, None, None) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.encrypt_frames_ex(None, 1, None, None, None, 0, None) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.cipher_set_partition(None, 1) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.cipher_get_partition(None, ctypes.byref(n), ctypes.byref(n)) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.cipher_set_layout(None, 0) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.cipher_profile_spans(None, None, 0, None, None, None, ctypes.byref(n)) == fhd.FHD_ERR_INVALID_ARG
+    assert b"null" in lib.cipher_last_error(None)
