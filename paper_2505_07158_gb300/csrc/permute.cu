@@ -33,8 +33,9 @@ namespace {
 constexpr int kStripThreads = 512;
 constexpr int kRowThreads = 256;
 constexpr int kRowsV = 4;                 // row segments per batch of independent vector loads
+constexpr int kRowsW = 8;                 // strip rows per batch of independent word loads (column pass)
 constexpr size_t kSmemLimit = 232448;     // opt-in dynamic shared memory per CTA on sm_100/sm_103
-constexpr size_t kRowSmemTarget = 49152;  // row pass: bands of ~2 rows at 1080p, four CTAs per SM
+constexpr size_t kRowSmemTarget = 32768;  // row pass: bands of 2 rows at 1080p
 
 // n mod d for n < 2^16, 1 <= d <= 2^18, by one 64-bit multiply: with
 // M = floor(2^40/d) + 1 and e = M d - 2^40 in (0, d], n M / 2^40 exceeds n/d
@@ -95,79 +96,71 @@ __global__ void __launch_bounds__(kStripThreads, 1) strip_kernel(const __grid_co
     const FastMod modH(h);
     uint8_t *S = smem;
 
-    // ---- phase 1: vector loads of the strip rows, bytes scattered to their rotated rows
+    // ---- phase 1: loads of the strip rows, bytes scattered to their rotated rows.  With 4-byte-aligned
+    // rows a lane owns one 32-bit word of the strip row (the lanes of a warp hold consecutive words), so
+    // in each byte store the lanes hit consecutive banks up to the row term 16 d (mod 32): at most two
+    // lanes share a bank.
     const uint32_t vec = strip_vec(rowB, P, C, Pe, src, out, fd.B);
-    const uint32_t nv = QC / vec;
-    const uint32_t RT = blockDim.x / nv;
-    if (threadIdx.x < nv * RT) {
-        const uint32_t tv = threadIdx.x % nv, tr = threadIdx.x / nv;
-        if (vec == 16) {
-            uint32_t ht[16];   // row offset of each byte: s_v (encrypt) or h - s_v (decrypt)
+    if (vec >= 4) {
+        const uint32_t nw = QC / 4;                    // words per strip row
+        const uint32_t RT = blockDim.x / nw;           // rows in parallel
+        if (threadIdx.x < nw * RT) {
+            const uint32_t j = threadIdx.x % nw, tr = threadIdx.x / nw;
+            uint32_t ht[4];   // row offset of each byte: s_v (encrypt) or h - s_v (decrypt)
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const uint32_t q = 16 * tv + k, jj = q / C, c = q - jj * C;
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t q = 4 * j + k, jj = q / C, c = q - jj * C;
                 const uint32_t t = modH.mod(Dv[(uint64_t)c * w + j0 + jj]);
                 ht[k] = kEnc ? t : h - t;
             }
-            for (uint32_t ib = tr; ib < h; ib += kRowsV * RT) {
-                uint4 e[kRowsV];
+            const uint8_t *sp = src + base + 4 * j;
+            const uint8_t *bp = fd.B + base + 4 * j;
+            for (uint32_t ib = tr; ib < h; ib += kRowsW * RT) {
+                uint32_t e[kRowsW];
 #pragma unroll
-                for (int k = 0; k < kRowsV; ++k) {
+                for (int k = 0; k < kRowsW; ++k) {
                     const uint32_t i = ib + k * RT;
                     if (i < h) {
-                        const uint64_t o = (uint64_t)i * rowB + base + 16 * tv;
-                        e[k] = __ldcs(reinterpret_cast<const uint4 *>(src + o));
-                        if (!kEnc) {
-                            const uint4 kb = __ldcs(reinterpret_cast<const uint4 *>(fd.B + o));
-                            e[k].x ^= kb.x; e[k].y ^= kb.y; e[k].z ^= kb.z; e[k].w ^= kb.w;
-                        }
+                        e[k] = __ldcs(reinterpret_cast<const unsigned int *>(sp + (uint64_t)i * rowB));
+                        if (!kEnc) e[k] ^= __ldcs(reinterpret_cast<const unsigned int *>(bp + (uint64_t)i * rowB));
                     }
                 }
 #pragma unroll
-                for (int k = 0; k < kRowsV; ++k) {
+                for (int k = 0; k < kRowsW; ++k) {
                     const uint32_t i = ib + k * RT;
                     if (i < h) {
-                        const uint32_t wd[4] = {e[k].x, e[k].y, e[k].z, e[k].w};
 #pragma unroll
-                        for (int bb = 0; bb < 16; ++bb) {
+                        for (int bb = 0; bb < 4; ++bb) {
                             uint32_t d = i + ht[bb];
                             d = d >= h ? d - h : d;
-                            S[(size_t)d * RP + 16 * tv + bb] = (uint8_t)(wd[bb >> 2] >> (8 * (bb & 3)));
+                            S[(size_t)d * RP + 4 * j + bb] = (uint8_t)(e[k] >> (8 * bb));
                         }
                     }
                 }
             }
-        } else {
-            const uint32_t q0 = vec * tv;
-            uint32_t ht[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint32_t q = q0 + k, jj = q / C, c = q - jj * C;
-                const uint32_t t = (uint32_t)k < vec ? modH.mod(Dv[(uint64_t)c * w + j0 + jj]) : 0;
-                ht[k] = kEnc ? t : h - t;
-            }
+        }
+    } else {
+        const uint32_t RT = blockDim.x / QC;
+        if (threadIdx.x < QC * RT) {
+            const uint32_t q = threadIdx.x % QC, tr = threadIdx.x / QC;
+            const uint32_t jj = q / C, c = q - jj * C;
+            const uint32_t t = modH.mod(Dv[(uint64_t)c * w + j0 + jj]);
+            const uint32_t ht = kEnc ? t : h - t;
             for (uint32_t i = tr; i < h; i += RT) {
-                const uint64_t o = (uint64_t)i * rowB + base + q0;
-                uint32_t e;
-                if (vec == 4) {
-                    e = *reinterpret_cast<const uint32_t *>(src + o);
-                    if (!kEnc) e ^= *reinterpret_cast<const uint32_t *>(fd.B + o);
-                } else {
-                    e = src[o];
-                    if (!kEnc) e ^= fd.B[o];
-                }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    uint32_t d = i + ht[k];
-                    d = d >= h ? d - h : d;
-                    if ((uint32_t)k < vec) S[(size_t)d * RP + q0 + k] = (uint8_t)(e >> (8 * k));
-                }
+                const uint64_t o = (uint64_t)i * rowB + base + q;
+                uint8_t e = src[o];
+                if (!kEnc) e ^= fd.B[o];
+                uint32_t d = i + ht;
+                d = d >= h ? d - h : d;
+                S[(size_t)d * RP + q] = e;
             }
         }
     }
     __syncthreads();
 
     // ---- phase 2: the strip leaves row by row (XORed with B when encrypting)
+    const uint32_t nv = QC / vec;
+    const uint32_t RT = blockDim.x / nv;
     if (threadIdx.x >= nv * RT) return;
     const uint32_t tv = threadIdx.x % nv, tr = threadIdx.x / nv;
     if (vec == 16) {
@@ -213,13 +206,13 @@ __global__ void __launch_bounds__(kStripThreads, 1) strip_kernel(const __grid_co
 // channel row of F by s_h bits.  Decrypt: output = right rotation of each
 // channel row of G by s_h bits.
 //
-// Interleaved RGB rows with w % 4 == 0 take a planar route: each group of 4
-// pixels (three 32-bit words) is split into one word per channel with
-// __byte_perm, a channel plane of w/4 words (plus one wrapped word) is
-// rotated four bytes at a time -- the five source bytes sit in two adjacent
-// words, so one 64-to-32-bit funnel shift by 8*(byte offset) + bit shift gives
-// the four rotated bytes -- and the words are interleaved back.  Other shapes
-// take the byte-wise route.
+// Interleaved RGB rows with w % 4 == 0 take a planar route: a thread
+// produces one 4-pixel group (12 bytes): for each channel the two words of
+// the channel plane that hold its source bytes are deinterleaved from the
+// staged row with __byte_perm (the five source bytes sit in two adjacent
+// plane words), one 64-to-32-bit funnel shift by 8*(byte offset) + bit shift
+// gives the four rotated bytes, and the three channels' words are
+// interleaved back.  Other shapes take the byte-wise route.
 template <bool kEnc>
 __global__ void __launch_bounds__(kRowThreads) row_kernel(const __grid_constant__ Batch b, uint32_t cta_base) {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -233,9 +226,8 @@ __global__ void __launch_bounds__(kRowThreads) row_kernel(const __grid_constant_
     const uint8_t *src = (kEnc ? fd.src : fd.G) + (uint64_t)i0 * rowB;
     uint8_t *dst = (kEnc ? fd.G : fd.dst) + (uint64_t)i0 * rowB;
     uint8_t *In = smem;                                          // RB rows
-    uint8_t *Out = smem + (size_t)RB * pitch;                    // RB rows (byte-wise route)
-    // shifts after the input rows and two plane buffers of RB * (pitch + 16) bytes each
-    uint32_t *sh = reinterpret_cast<uint32_t *>(smem + 3 * (size_t)RB * pitch + 32 * (size_t)RB);   // [r * C + c]
+    uint8_t *Out = smem + (size_t)RB * pitch;                    // RB rows
+    uint32_t *sh = reinterpret_cast<uint32_t *>(smem + 2 * (size_t)RB * pitch);   // row shifts [r * C + c]
     const FastMod modW8(8 * w);
 
     // ---- load the band (rows are contiguous in global memory)
@@ -260,54 +252,63 @@ __global__ void __launch_bounds__(kRowThreads) row_kernel(const __grid_constant_
     __syncthreads();
 
     if (C == 3 && (w & 3) == 0 && v16) {
-        // ---- planar route.  Planes: [r][c][W4 + 1] words (RB * (rowB + 12)
-        // bytes per set), input planes after the rows, output planes after them.
-        const uint32_t W4 = w >> 2, PW = W4 + 1;
-        uint32_t *Pin = reinterpret_cast<uint32_t *>(smem + (size_t)RB * pitch);
-        uint32_t *Pout = Pin + (size_t)RB * 3 * PW;
-        const uint32_t groups = nr * W4;
-        for (uint32_t k = threadIdx.x; k < groups; k += blockDim.x) {
-            const uint32_t r = k / W4, g = k - r * W4;
-            const uint32_t *wp = reinterpret_cast<const uint32_t *>(In + (size_t)r * pitch) + 3 * g;
-            const uint32_t w0 = wp[0], w1 = wp[1], w2 = wp[2];
-            uint32_t *pl = Pin + (size_t)r * 3 * PW;
-            const uint32_t R = __byte_perm(__byte_perm(w0, w1, 0x0630), w2, 0x5210);
-            const uint32_t G = __byte_perm(__byte_perm(w0, w1, 0x0741), w2, 0x6210);
-            const uint32_t B = __byte_perm(__byte_perm(w0, w1, 0x0052), w2, 0x7410);
-            pl[g] = R; pl[PW + g] = G; pl[2 * PW + g] = B;
-            if (g == 0) { pl[W4] = R; pl[PW + W4] = G; pl[2 * PW + W4] = B; }   // wrapped word
-        }
-        __syncthreads();
-        const uint32_t words = nr * 3 * W4;
-        for (uint32_t k = threadIdx.x; k < words; k += blockDim.x) {
-            const uint32_t rc = k / W4, m = k - rc * W4;
-            const uint32_t s = sh[rc];
-            const uint32_t a = s >> 3, rr = s & 7;
-            // first source byte of the plane: 4m - a - 1 (encrypt) or 4m + a (decrypt), mod w
-            int si = kEnc ? (int)(4 * m) - (int)a - 1 : (int)(4 * m + a);
-            if (si < 0) si += (int)w;
-            if (si >= (int)w) si -= (int)w;
-            const uint32_t u = (uint32_t)si >> 2, o = (uint32_t)si & 3;
-            const uint32_t *pl = Pin + (size_t)rc * PW;
-            Pout[(size_t)rc * PW + m] = __funnelshift_rc(pl[u], pl[u + 1], kEnc ? 8 * o + 8 - rr : 8 * o + rr);
-        }
-        __syncthreads();
-        for (uint32_t k = threadIdx.x; k < groups; k += blockDim.x) {
-            const uint32_t r = k / W4, g = k - r * W4;
-            const uint32_t *pl = Pout + (size_t)r * 3 * PW;
-            const uint32_t R = pl[g], G = pl[PW + g], B = pl[2 * PW + g];
-            uint32_t *wp = reinterpret_cast<uint32_t *>(In + (size_t)r * pitch) + 3 * g;
-            wp[0] = __byte_perm(__byte_perm(R, G, 0x1040), B, 0x3410);
-            wp[1] = __byte_perm(__byte_perm(G, R, 0x2601), B, 0x3250);
-            wp[2] = __byte_perm(__byte_perm(B, R, 0x3072), G, 0x3710);
+        // ---- planar route, one pass: a thread builds the 12 output bytes of one 4-pixel group.  For each
+        // channel the two source words of its plane are deinterleaved on the fly from the staged row (a
+        // plane word u is the channel's bytes of the interleaved words 3u .. 3u+2), rotated with one
+        // funnel shift, and the three rotated plane words are interleaved back into Out.  With w % 4 == 0
+        // the source offset within a plane word is the same for every group of a channel row, so a row
+        // needs only a word offset and a shift amount per channel.
+        const uint32_t W4 = w >> 2;
+        uint8_t *Outp = Out;
+        for (uint32_t r = 0; r < nr; ++r) {
+            const uint32_t *row = reinterpret_cast<const uint32_t *>(In + (size_t)r * pitch);
+            uint32_t *orow = reinterpret_cast<uint32_t *>(Outp + (size_t)r * pitch);
+            uint32_t du[3], fs[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const uint32_t sc = sh[r * 3 + c];
+                const uint32_t a = sc >> 3, rr = sc & 7;
+                // first source byte of the plane for output pixel 0: -a-1 (encrypt) or a (decrypt), mod w
+                int s0 = kEnc ? -(int)a - 1 : (int)a;
+                if (s0 < 0) s0 += (int)w;
+                du[c] = (uint32_t)s0 >> 2;
+                const uint32_t o = (uint32_t)s0 & 3;
+                fs[c] = kEnc ? 8 * o + 8 - rr : 8 * o + rr;
+            }
+            for (uint32_t g = threadIdx.x; g < W4; g += blockDim.x) {
+                uint32_t q[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    uint32_t u = g + du[c];
+                    u = u >= W4 ? u - W4 : u;
+                    const uint32_t u1 = u + 1 == W4 ? 0 : u + 1;
+                    const uint32_t a0 = row[3 * u], a1 = row[3 * u + 1], a2 = row[3 * u + 2];
+                    const uint32_t b0 = row[3 * u1], b1 = row[3 * u1 + 1], b2 = row[3 * u1 + 2];
+                    uint32_t lo, hi;
+                    if (c == 0) {
+                        lo = __byte_perm(__byte_perm(a0, a1, 0x0630), a2, 0x5210);
+                        hi = __byte_perm(__byte_perm(b0, b1, 0x0630), b2, 0x5210);
+                    } else if (c == 1) {
+                        lo = __byte_perm(__byte_perm(a0, a1, 0x0741), a2, 0x6210);
+                        hi = __byte_perm(__byte_perm(b0, b1, 0x0741), b2, 0x6210);
+                    } else {
+                        lo = __byte_perm(__byte_perm(a0, a1, 0x0052), a2, 0x7410);
+                        hi = __byte_perm(__byte_perm(b0, b1, 0x0052), b2, 0x7410);
+                    }
+                    q[c] = __funnelshift_rc(lo, hi, fs[c]);
+                }
+                uint32_t *wp = orow + 3 * g;
+                wp[0] = __byte_perm(__byte_perm(q[0], q[1], 0x1040), q[2], 0x3410);
+                wp[1] = __byte_perm(__byte_perm(q[1], q[0], 0x2601), q[2], 0x3250);
+                wp[2] = __byte_perm(__byte_perm(q[2], q[0], 0x3072), q[1], 0x3710);
+            }
         }
         __syncthreads();
         const uint32_t nvr = rowB / 16;
-        for (uint32_t k = threadIdx.x; k < nr * nvr; k += blockDim.x) {
-            const uint32_t r = k / nvr, v = k - r * nvr;
-            *reinterpret_cast<uint4 *>(dst + (uint64_t)r * rowB + 16 * v) =
-                *reinterpret_cast<const uint4 *>(In + (size_t)r * pitch + 16 * v);
-        }
+        for (uint32_t r = 0; r < nr; ++r)
+            for (uint32_t v = threadIdx.x; v < nvr; v += blockDim.x)
+                *reinterpret_cast<uint4 *>(dst + (uint64_t)r * rowB + 16 * v) =
+                    *reinterpret_cast<const uint4 *>(Outp + (size_t)r * pitch + 16 * v);
         return;
     }
 
@@ -370,17 +371,16 @@ size_t strip_smem_bytes(uint32_t h, uint32_t P, uint32_t C) { return ((size_t)h 
 
 uint32_t row_band(uint32_t w, uint32_t C) {
     const size_t pitch = ((size_t)w * C + 15) & ~(size_t)15;
-    size_t rb = kRowSmemTarget / (3 * pitch + 32 + 16);
+    size_t rb = kRowSmemTarget / (2 * pitch + 16);
     if (rb < 1) rb = 1;
     if (rb > 16) rb = 16;
     return (uint32_t)rb;
 }
 
-// Three row-sized buffers per row (input, then planes in and out, or the
-// byte-wise output) and the row shifts.
+// Two row-sized buffers per row (input and output) and the row shifts.
 size_t row_smem_bytes(uint32_t w, uint32_t C, uint32_t RB) {
     const size_t pitch = ((size_t)w * C + 15) & ~(size_t)15;
-    return 3 * (size_t)RB * pitch + 32 * (size_t)RB + 4 * (size_t)RB * C;
+    return 2 * (size_t)RB * pitch + 4 * (size_t)RB * C;
 }
 
 uint32_t permute_strips(uint32_t w, uint32_t P) { return (w + P - 1) / P; }

@@ -78,7 +78,9 @@ def test_keystream(h, w, C, n):
 # ---- K3 / K4: fused confusion + XOR and inverse ----
 
 SHAPES = [(1, 1, 1), (1, 1, 3), (1, 8, 3), (8, 1, 3), (3, 5, 3), (2, 2, 4), (7, 9, 3), (16, 13, 1), (37, 53, 3),
-          (64, 129, 3), (100, 1000, 3), (33, 300, 4), (480, 640, 3), (1080, 1920, 3)]
+          (64, 129, 3), (100, 1000, 3), (33, 300, 4), (480, 640, 3), (1080, 1920, 3),
+          # planar RGB route (w % 4 == 0): one group per row, a few groups, a wide row
+          (5, 4, 3), (3, 12, 3), (17, 36, 3), (2, 4096, 3)]
 
 
 def _rand(h, w, C, seed):
