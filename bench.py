@@ -616,9 +616,53 @@ def run_extras(args, rank, fhd, torch):
     del pool
     torch.cuda.empty_cache()
     out["worker_count_sweep"] = run_n_sweep(rank, fhd, torch)
+    out["frame_statistics"] = run_stats(rank, fhd, torch)
     if not args.no_stress:
         out["stress_8k"] = run_stress(rank, fhd, torch)
     return out
+
+
+def run_stats(rank, fhd, torch, frames=30, reps=10):
+    """Frame statistics (Sec. III, IV-B) over a 30-frame 1080p batch: the streaming passes against HBM
+    (histogram statistics read N bytes per frame, NPCR/UACI 2N), and the sampled ones (10,000 pairs per
+    direction, 30 blocks of 44 x 44 per frame) as latencies.  Inputs are device-generated uniform frames,
+    larger than L2 (187 MB per batch)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = torch.Generator(device=dev)
+    g.manual_seed(rank + 31)
+    a = torch.randint(0, 256, (frames, HGT, WID, CH), dtype=torch.uint8, device=dev, generator=g)
+    b = torch.randint(0, 256, (frames, HGT, WID, CH), dtype=torch.uint8, device=dev, generator=g)
+    pairs = torch.stack([torch.randint(0, HGT - 1, (frames, 3, 10000), device=dev, generator=g),
+                         torch.randint(0, WID - 1, (frames, 3, 10000), device=dev, generator=g)], dim=-1).int()
+    cells = [(44 * i, 44 * j) for i in range(HGT // 44) for j in range(WID // 44)]
+    pick = torch.stack([torch.randperm(len(cells), device=dev, generator=g)[:30] for _ in range(frames)])
+    blocks = torch.tensor(cells, dtype=torch.int32, device=dev)[pick]
+    calls = {"histogram_variance_chi2_entropy": (lambda: fhd.fhd_stats_histogram(a), a.numel()),
+             "npcr_uaci": (lambda: fhd.fhd_stats_npcr_uaci(a, b), 2 * a.numel()),
+             "correlation_10000_pairs_x3": (lambda: fhd.fhd_stats_correlation(a, pairs), None),
+             "local_entropy_30_blocks": (lambda: fhd.fhd_stats_local_entropy(a, blocks, 44), None)}
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", HBM_PEAK_FALLBACK)
+    res = {"workload": f"{frames} x 1920x1080x3 uint8 (device-generated uniform), statistics per frame and channel"}
+    for name, (fn, nbytes) in calls.items():
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        r = {"ms_per_batch": ms, "frames_per_s": frames / (ms / 1000.0)}
+        if nbytes:
+            ach = nbytes / (ms / 1000.0) / 1e9
+            r["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                             "bytes_per_batch": nbytes}
+        res[name] = r
+    _, st = fhd.fhd_stats_histogram(a[:1])
+    res["uniform_frame_0"] = {"chi2": st[0, :, 1].tolist(), "entropy": st[0, :, 2].tolist()}
+    return res
 
 
 def run_n_sweep(rank, fhd, torch, ns=(32, 128, 512), steps=3):

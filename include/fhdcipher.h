@@ -261,6 +261,52 @@ int cipher_get_partition(fhd_cipher *c, uint32_t *chain_sms, uint32_t *bulk_sms)
 enum { FHD_LAYOUT_LATENCY = 0, FHD_LAYOUT_THROUGHPUT = 1 };
 int cipher_set_layout(fhd_cipher *c, int layout);
 
+/* ---- Frame statistics of the paper's evaluation (Sec. III and IV-B) ----
+ * Batched over `count` frames stored contiguously in device memory as
+ * [count][height][width][channels] uint8, reported per frame and channel
+ * (index f * channels + c).  All output pointers are device pointers owned by
+ * the caller; calls are asynchronous on `stream`; argument errors return a
+ * negative FHD_ERR_* code and enqueue nothing.  Counts are exact integers and
+ * only each statistic's final formula rounds (binary64).  Random sample
+ * positions (pairs, blocks) are inputs: the caller draws them. */
+
+/* Histogram statistics, Sec. III-A and III-C: per frame and channel the 256-bin
+ * histogram z (optional `hist`, uint32 count*channels*256, may be NULL) and
+ * stats[3 * (f * channels + c) + {0, 1, 2}] = histogram variance (Eq. 4),
+ * chi^2 (Eq. 5), information entropy in bits (Eq. 10).  Uses a stream-ordered
+ * scratch of count*channels*256*8 bytes. */
+int fhd_stats_histogram(const uint8_t *frames, uint32_t count, uint32_t height, uint32_t width, uint32_t channels,
+                        uint32_t *hist, double *stats, void *stream);
+
+/* NPCR and UACI between frames a[f] and b[f] (Sec. IV-B, Eqs. 14-15), in
+ * percent: out[2 * (f * channels + c) + {0, 1}].  `counts` (optional, uint64
+ * count*channels*2, may be NULL) receives the exact number of changed pixels
+ * and the sum of |a - b| per frame and channel. */
+int fhd_stats_npcr_uaci(const uint8_t *a, const uint8_t *b, uint32_t count, uint32_t height, uint32_t width,
+                        uint32_t channels, uint64_t *counts, double *out, void *stream);
+
+/* Correlation coefficient of adjacent pixel pairs (Sec. III-B, Eqs. 6-9) in
+ * the horizontal (d = 0), vertical (1) and diagonal (2) directions:
+ * pairs[2 * ((f * 3 + d) * npairs + k) + {0, 1}] = (row, column) of pixel x
+ * of pair k; y is its right, lower or lower-right neighbour, which must lie
+ * inside the frame (1 <= npairs <= 2^22).  r[3 * (f * channels + c) + d];
+ * `sums` (optional, int64 count*channels*3*5, may be NULL) receives the exact
+ * sums of x, y, x^2, y^2, xy.  A pair outside the frame is skipped and sets
+ * bit 0 of *status (device uint32, optional). */
+int fhd_stats_correlation(const uint8_t *frames, uint32_t count, uint32_t height, uint32_t width, uint32_t channels,
+                          const uint32_t *pairs, uint32_t npairs, int64_t *sums, double *r, unsigned *status,
+                          void *stream);
+
+/* Local Shannon entropy (Sec. III-C, Eq. 11): the mean over k blocks of
+ * block x block pixels of their information entropy, per frame and channel:
+ * out[f * channels + c].  blocks[2 * (f * k + q) + {0, 1}] = (row, column) of
+ * block q's top-left pixel (the paper draws 30 non-overlapping 44 x 44
+ * blocks at random).  A block outside the frame sets bit 0 of *status.
+ * Uses a stream-ordered scratch of count*k*channels doubles. */
+int fhd_stats_local_entropy(const uint8_t *frames, uint32_t count, uint32_t height, uint32_t width,
+                            uint32_t channels, const uint32_t *blocks, uint32_t k, uint32_t block, double *out,
+                            unsigned *status, void *stream);
+
 /* Kernel kinds reported by cipher_profile_read, in this order. */
 enum { FHD_K_SHA = 0, FHD_K_MASTER = 1, FHD_K_KEYSTREAM = 2, FHD_K_ENCRYPT = 3, FHD_K_DECRYPT = 4, FHD_K_COUNT = 5 };
 

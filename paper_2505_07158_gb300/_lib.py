@@ -36,7 +36,8 @@ EXPORTS = (
     "cipher_profile", "cipher_profile_read", "fhd_launch_count", "encrypt_frames_ex", "decrypt_frames_ex",
     "cipher_reserve", "fhd_frame_scratch_bytes", "fhd_frame_digest_noalloc", "cipher_verify_frames",
     "decrypt_frames_split", "encrypt_frames_split", "cipher_profile_spans", "cipher_set_partition",
-    "cipher_get_partition", "cipher_set_layout",
+    "cipher_get_partition", "cipher_set_layout", "fhd_stats_histogram", "fhd_stats_npcr_uaci",
+    "fhd_stats_correlation", "fhd_stats_local_entropy",
 )
 KERNEL_KINDS = ("sha", "master", "keystream", "encrypt", "decrypt")
 
@@ -103,6 +104,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "cipher_set_partition": (i32, [P, i32]),
             "cipher_get_partition": (i32, [P, P, P]),
             "cipher_set_layout": (i32, [P, i32]),
+            "fhd_stats_histogram": (i32, [P, u32, u32, u32, u32, P, P, P]),
+            "fhd_stats_npcr_uaci": (i32, [P, P, u32, u32, u32, u32, P, P, P]),
+            "fhd_stats_correlation": (i32, [P, u32, u32, u32, u32, P, u32, P, P, P, P]),
+            "fhd_stats_local_entropy": (i32, [P, u32, u32, u32, u32, P, u32, u32, P, P, P]),
             "cipher_reserve": (i32, [P, P, u64]),
             "cipher_verify_frames": (i32, [P, u32, P, P, P]),
             "fhd_frame_scratch_bytes": (u64, [u32, u32, u32, u32]),
@@ -377,6 +382,74 @@ def fhd_frame_digest(data: torch.Tensor, n: int = 32, count: int = 1, out: torch
     _check(load().fhd_frame_digest(ctypes.c_void_p(ptr), nbytes, n, count, ctypes.c_void_p(out.data_ptr()),
                                    _stream_ptr(stream)))
     return out
+
+
+# ---- frame statistics (Sec. III and IV-B) ----
+
+def _frames4(frames: torch.Tensor) -> torch.Tensor:
+    if not frames.is_cuda or frames.dtype != torch.uint8 or not frames.is_contiguous():
+        raise ValueError("frames must be a contiguous CUDA uint8 tensor")
+    if frames.dim() == 3:
+        frames = frames.unsqueeze(0)
+    if frames.dim() != 4:
+        raise ValueError("frames must be (count, height, width, channels) or (height, width, channels)")
+    return frames
+
+
+def _vp(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p()
+
+
+def fhd_stats_histogram(frames: torch.Tensor, stream=None):
+    """(hist uint32 [count, C, 256], stats float64 [count, C, 3] = histogram variance, chi^2, entropy)."""
+    f = _frames4(frames)
+    n, h, w, c = f.shape
+    hist = torch.empty((n, c, 256), dtype=torch.int32, device=f.device)
+    st = torch.empty((n, c, 3), dtype=torch.float64, device=f.device)
+    _check(load().fhd_stats_histogram(_vp(f), n, h, w, c, _vp(hist), _vp(st), _stream_ptr(stream)))
+    return hist, st
+
+
+def fhd_stats_npcr_uaci(a: torch.Tensor, b: torch.Tensor, stream=None):
+    """(counts int64 [count, C, 2] = changed pixels and sum |a - b|, out float64 [count, C, 2] = NPCR, UACI %)."""
+    fa, fb = _frames4(a), _frames4(b)
+    if fa.shape != fb.shape:
+        raise ValueError("a and b shapes differ")
+    n, h, w, c = fa.shape
+    counts = torch.empty((n, c, 2), dtype=torch.int64, device=fa.device)
+    out = torch.empty((n, c, 2), dtype=torch.float64, device=fa.device)
+    _check(load().fhd_stats_npcr_uaci(_vp(fa), _vp(fb), n, h, w, c, _vp(counts), _vp(out), _stream_ptr(stream)))
+    return counts, out
+
+
+def fhd_stats_correlation(frames: torch.Tensor, pairs: torch.Tensor, stream=None):
+    """pairs int32 [count, 3, npairs, 2] (row, column of x; directions horizontal, vertical, diagonal) ->
+    (sums int64 [count, C, 3, 5], r float64 [count, C, 3], status int32 [1])."""
+    f = _frames4(frames)
+    n, h, w, c = f.shape
+    if not pairs.is_cuda or pairs.dtype != torch.int32 or not pairs.is_contiguous() or pairs.dim() != 4 \
+            or pairs.shape[0] != n or pairs.shape[1] != 3 or pairs.shape[3] != 2:
+        raise ValueError("pairs must be a contiguous CUDA int32 tensor [count, 3, npairs, 2]")
+    sums = torch.empty((n, c, 3, 5), dtype=torch.int64, device=f.device)
+    r = torch.empty((n, c, 3), dtype=torch.float64, device=f.device)
+    status = torch.zeros(1, dtype=torch.int32, device=f.device)
+    _check(load().fhd_stats_correlation(_vp(f), n, h, w, c, _vp(pairs), pairs.shape[2], _vp(sums), _vp(r),
+                                        _vp(status), _stream_ptr(stream)))
+    return sums, r, status
+
+
+def fhd_stats_local_entropy(frames: torch.Tensor, blocks: torch.Tensor, block: int, stream=None):
+    """blocks int32 [count, k, 2] (top-left row, column) -> (out float64 [count, C], status int32 [1])."""
+    f = _frames4(frames)
+    n, h, w, c = f.shape
+    if not blocks.is_cuda or blocks.dtype != torch.int32 or not blocks.is_contiguous() or blocks.dim() != 3 \
+            or blocks.shape[0] != n or blocks.shape[2] != 2:
+        raise ValueError("blocks must be a contiguous CUDA int32 tensor [count, k, 2]")
+    out = torch.empty((n, c), dtype=torch.float64, device=f.device)
+    status = torch.zeros(1, dtype=torch.int32, device=f.device)
+    _check(load().fhd_stats_local_entropy(_vp(f), n, h, w, c, _vp(blocks), blocks.shape[1], block, _vp(out),
+                                          _vp(status), _stream_ptr(stream)))
+    return out, status
 
 
 def fhd_frame_digest_noalloc(data: torch.Tensor, out: torch.Tensor, n: int = 32, count: int = 1, stream=None):

@@ -764,6 +764,91 @@ int cipher_set_partition(fhd_cipher *c, int enable) {
     return FHD_OK;
 }
 
+static int stats_args(const void *frames, uint32_t count, uint32_t h, uint32_t w, uint32_t C, const void *out) {
+    if (!frames || !out) return fail(nullptr, FHD_ERR_INVALID_ARG, "null argument");
+    if (count == 0) return fail(nullptr, FHD_ERR_INVALID_ARG, "count must be positive");
+    if (h == 0 || w == 0 || C == 0 || C > 4 || h > FHD_MAX_HEIGHT || w > FHD_MAX_DIM)
+        return fail(nullptr, FHD_ERR_INVALID_ARG, "frame dimensions out of range");
+    return FHD_OK;
+}
+
+int fhd_stats_histogram(const uint8_t *frames, uint32_t count, uint32_t height, uint32_t width, uint32_t channels,
+                        uint32_t *hist, double *stats, void *stream) {
+    int rc = stats_args(frames, count, height, width, channels, stats);
+    if (rc != FHD_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long *h64 = nullptr;
+    const uint64_t items = (uint64_t)count * channels;
+    cudaError_t e = cudaMallocAsync(&h64, items * 256 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+    e = fhd::launch_stats_histogram(frames, count, (uint64_t)height * width * channels, channels, h64, hist, stats, s);
+    cudaFreeAsync(h64, s);
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("histogram launch: ") + cudaGetErrorString(e));
+    return FHD_OK;
+}
+
+int fhd_stats_npcr_uaci(const uint8_t *a, const uint8_t *b, uint32_t count, uint32_t height, uint32_t width,
+                        uint32_t channels, uint64_t *counts, double *out, void *stream) {
+    int rc = stats_args(a, count, height, width, channels, out);
+    if (rc != FHD_OK) return rc;
+    if (!b) return fail(nullptr, FHD_ERR_INVALID_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(counts);
+    const uint64_t items = (uint64_t)count * channels;
+    cudaError_t e = cudaSuccess;
+    if (!acc) e = cudaMallocAsync(&acc, items * 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+    e = fhd::launch_stats_npcr(a, b, count, (uint64_t)height * width * channels, channels, (uint64_t)height * width,
+                               acc, out, s);
+    if (!counts) cudaFreeAsync(acc, s);
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("npcr launch: ") + cudaGetErrorString(e));
+    return FHD_OK;
+}
+
+int fhd_stats_correlation(const uint8_t *frames, uint32_t count, uint32_t height, uint32_t width, uint32_t channels,
+                          const uint32_t *pairs, uint32_t npairs, int64_t *sums, double *r, unsigned *status,
+                          void *stream) {
+    int rc = stats_args(frames, count, height, width, channels, r);
+    if (rc != FHD_OK) return rc;
+    if (!pairs || npairs == 0 || npairs > (1u << 22))
+        return fail(nullptr, FHD_ERR_INVALID_ARG, "pairs must be non-null and 1 <= npairs <= 2^22");
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t items = (uint64_t)count * channels;
+    long long *sm = reinterpret_cast<long long *>(sums);
+    unsigned *st = status;
+    cudaError_t e = cudaSuccess;
+    if (!sm) e = cudaMallocAsync(&sm, items * 3 * 5 * sizeof(long long), s);
+    if (e == cudaSuccess && !st) e = cudaMallocAsync(&st, sizeof(unsigned), s);
+    if (e == cudaSuccess && !status) e = cudaMemsetAsync(st, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_OOM, std::string("scratch: ") + cudaGetErrorString(e));
+    e = fhd::launch_stats_correlation(frames, count, height, width, channels, pairs, npairs, sm, r, st, s);
+    if (!sums) cudaFreeAsync(sm, s);
+    if (!status) cudaFreeAsync(st, s);
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("correlation launch: ") + cudaGetErrorString(e));
+    return FHD_OK;
+}
+
+int fhd_stats_local_entropy(const uint8_t *frames, uint32_t count, uint32_t height, uint32_t width,
+                            uint32_t channels, const uint32_t *blocks, uint32_t k, uint32_t block, double *out,
+                            unsigned *status, void *stream) {
+    int rc = stats_args(frames, count, height, width, channels, out);
+    if (rc != FHD_OK) return rc;
+    if (!blocks || k == 0 || block == 0 || block > height || block > width)
+        return fail(nullptr, FHD_ERR_INVALID_ARG, "blocks must be non-null, k >= 1 and 1 <= block <= min(height, width)");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned *st = status;
+    double *ent = nullptr;
+    cudaError_t e = cudaMallocAsync(&ent, (uint64_t)count * k * channels * sizeof(double), s);
+    if (e == cudaSuccess && !st) e = cudaMallocAsync(&st, sizeof(unsigned), s);
+    if (e == cudaSuccess && !status) e = cudaMemsetAsync(st, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_OOM, std::string("scratch: ") + cudaGetErrorString(e));
+    e = fhd::launch_stats_local_entropy(frames, count, height, width, channels, blocks, k, block, ent, out, st, s);
+    cudaFreeAsync(ent, s);
+    if (!status) cudaFreeAsync(st, s);
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("local entropy launch: ") + cudaGetErrorString(e));
+    return FHD_OK;
+}
+
 int cipher_set_layout(fhd_cipher *c, int layout) {
     if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
     if (layout != FHD_LAYOUT_LATENCY && layout != FHD_LAYOUT_THROUGHPUT)

@@ -68,6 +68,18 @@ cudaError_t launch_fold(const uint8_t *part, uint32_t n, uint32_t count, uint8_t
 cudaError_t launch_fold_batch(const Batch &b, cudaStream_t s);
 // Counts one kernel launch of this library (read by fhd_launch_count).
 void note_launch();
+
+// Frame statistics (stats.cu); frames are a contiguous batch [count][h][w][C].
+cudaError_t launch_stats_histogram(const uint8_t *frames, uint32_t count, uint64_t frame_bytes, uint32_t C,
+                                   unsigned long long *hist64, uint32_t *hist32, double *out, cudaStream_t s);
+cudaError_t launch_stats_npcr(const uint8_t *a, const uint8_t *b, uint32_t count, uint64_t frame_bytes, uint32_t C,
+                              uint64_t wh, unsigned long long *acc, double *out, cudaStream_t s);
+cudaError_t launch_stats_correlation(const uint8_t *frames, uint32_t count, uint32_t h, uint32_t w, uint32_t C,
+                                     const uint32_t *pairs, uint32_t npairs, long long *sums, double *out,
+                                     unsigned *status, cudaStream_t s);
+cudaError_t launch_stats_local_entropy(const uint8_t *frames, uint32_t count, uint32_t h, uint32_t w, uint32_t C,
+                                       const uint32_t *blocks, uint32_t k, uint32_t bs, double *ent, double *out,
+                                       unsigned *status, cudaStream_t s);
 cudaError_t noalloc_scratch(uint8_t **out);   // fixed sub-frame digest array of fhd_frame_digest_noalloc
 uint32_t noalloc_max_digests();
 cudaError_t launch_master(const Batch &b, StreamState *states, unsigned *status, cudaStream_t s);

@@ -72,3 +72,30 @@ def test_workers_are_independent():
         (d0, d1), (b0, b1) = dsl[i], bsl[i]
         same = np.array_equal(D[d0:d1], D2[d0:d1]) and np.array_equal(B[b0:b1], B2[b0:b1])
         assert same == (i != 4)
+
+
+def test_workers_fed_from_one_master_trajectory_are_shifted_copies():
+    """Documented consequence of the reading of Algorithm 2 (pair i starts at IR[2i] and IR[2i+1]):
+    IR holds consecutive iterates of one trajectory of Eq. (1), and the workers iterate the same map,
+    so chain 2i+1 is chain 2i one step ahead and worker i's byte stream is worker 0's stream shifted by
+    2i steps (48 i bytes).  The D/B slices then come from one sequence, and the XOR of adjacent
+    iterates leaves the sixth extracted byte (mantissa bits 40-47) far from uniform."""
+    key = si.key(21)
+    ic = oracle.key_to_ic(key)
+    F = si.gradient_frame(64, 96, 3, seed=21)
+    IR, _ = oracle.master(np.array(ic[:4]), oracle.frame_digest(F), ic[4])
+    IR = np.asarray(IR).reshape(-1, 4)
+    assert np.array_equal(oracle.rk4_step(IR[0], ic[4]), IR[1])
+
+    def stream(i, steps):
+        a = oracle.rk4_trajectory(IR[2 * i], ic[4], steps)
+        b = oracle.rk4_trajectory(IR[2 * i + 1], ic[4], steps)
+        x = (a.view(np.uint64) ^ b.view(np.uint64)) & np.uint64(0xFFFFFFFFFFFF)
+        return np.stack([(x >> np.uint64(8 * k)) & np.uint64(255) for k in range(6)], axis=-1).reshape(-1)
+
+    s0 = stream(0, 2000)
+    for i in (1, 5):
+        assert np.array_equal(stream(i, 1000)[:24 * 900], s0[48 * i:48 * i + 24 * 900])
+    sixth = np.bincount(s0[5::6].astype(np.int64), minlength=256)
+    e = sixth.sum() / 256.0
+    assert ((sixth - e) ** 2 / e).sum() > 1000.0          # uniform bytes would give ~255
