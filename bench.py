@@ -33,6 +33,11 @@ import time
 
 import numpy as np
 
+# One hardware queue per CUDA stream: with the default 8, the slots' streams (two callers' CUDA streams per
+# clip in flight plus the library's internal chain and bulk streams) share queues, and a stream held by an
+# event wait stalls unrelated streams queued behind it.  Read when the CUDA context is created.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -57,7 +62,7 @@ TRAFFIC_PER_FRAME = {"keystream": 41984 / 4, "encrypt": (24924000 + 2000 + 49840
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -68,11 +73,19 @@ def parse():
     ap.add_argument("--no-stress", action="store_true", help="skip the 256 x 8K stress round trip")
     ap.add_argument("--gate", default="chain", choices=["permute", "keystream", "chain", "window"],
                     help="what the next clip's LHCS_m waits for besides the chaining state (see round_trip)")
-    ap.add_argument("--no-partition", action="store_true", help="run LHCS_m on the same SMs as everything else")
+    ap.add_argument("--partition", action="store_true",
+                    help="run LHCS_m on its own 8-SM partition (green contexts) instead of beside the workers")
+    ap.add_argument("--no-partition", action="store_true", help="(the default) LHCS_m on the same SMs as the rest")
     ap.add_argument("--layout", default="throughput", choices=["latency", "throughput"], help="worker warp layout")
-    ap.add_argument("--inflight", type=int, default=2,
-                    help="clips in flight on separate buffers: the next clip's digest stage overlaps this clip's "
-                         "keystreams; its chaotic stage waits for this clip")
+    ap.add_argument("--inflight", type=int, default=5,
+                    help="clips in flight on separate buffers: later clips' digest stage and LHCS_m overlap earlier "
+                         "clips' keystreams")
+    ap.add_argument("--worker-window", type=int, default=3,
+                    help="clip k's workers (both sides) wait for the workers of clip k - W, so about W clips' "
+                         "workers share the FP64 pipes while later clips' digests and LHCS_m run ahead "
+                         "(0: no gate; needs more clips in flight than W)")
+    ap.add_argument("--spans", default=None,
+                    help="write the timed region's launch timeline (sender and receiver, ms from its start) as JSON")
     return ap.parse_args()
 
 
@@ -296,7 +309,7 @@ def run_ours(args):
     host = torch.from_numpy(clip).pin_memory()
     key = si.key(rank)
     enc, dec = fhd.Cipher(key, n_workers=N_WORKERS), fhd.Cipher(key, n_workers=N_WORKERS)
-    if args.no_partition:
+    if not args.partition or args.no_partition:
         enc.set_partition(False)
         dec.set_partition(False)
     enc.set_layout(args.layout)
@@ -326,7 +339,9 @@ def run_ours(args):
             self.host_dig = torch.empty((FRAMES, 32), dtype=torch.uint8).pin_memory()
 
     slots = [Slot() for _ in range(max(1, args.inflight))]
-    last = [None, None]      # slots of the previous two clips: the chaining state advances clip after clip
+    WW = args.worker_window if 0 < args.worker_window < len(slots) else 0
+    KEEP = max(2, WW)
+    last = [None] * KEEP     # slots of the previous clips, oldest first: the chaining state advances clip after clip
 
     def round_trip(sl, e2e=False):
         prev, prev2 = last[-1], last[-2]
@@ -361,11 +376,17 @@ def run_ours(args):
             dw = [prev.dec_master, prev2.enc_ks, prev2.dec_ks]
         else:
             ew, dw = [prev.enc_master], [prev.dec_master]
+        # Worker window: this clip's workers start once the workers of clip k - W are done; its digest stage
+        # and LHCS_m do not wait, so they run while W clips' workers fill the FP64 pipes.
+        wslot = last[-WW] if WW else None
+        if wslot is sl:
+            wslot = None
+        ewk, dwk = ([wslot.enc_ks], [wslot.dec_ks]) if wslot is not None else ([], [])
         enc.encrypt_frames(sl.enc_items, sl.tx, wait_events=ew, master_event=sl.enc_master,
-                           digest_event=sl.digests_ready, keystream_event=sl.enc_ks)
+                           digest_event=sl.digests_ready, keystream_event=sl.enc_ks, worker_wait_events=ewk)
         sl.cipher_ready.record(sl.tx)
         dec.decrypt_frames(sl.dec_items, sl.rx, wait_events=[sl.digests_ready] + dw, master_event=sl.dec_master,
-                           data_events=[sl.cipher_ready], keystream_event=sl.dec_ks)
+                           data_events=[sl.cipher_ready], keystream_event=sl.dec_ks, worker_wait_events=dwk)
         sl.dec_done.record(sl.rx)             # before the copy-out: gates the next clip's receiver
         if e2e:
             with torch.cuda.stream(sl.rx):
@@ -376,7 +397,7 @@ def run_ours(args):
         sl.rx_done.record(sl.rx)
         sl.used = True
         last.append(sl)
-        del last[:-2]
+        del last[:-KEEP]
 
     def timed_steps(nsteps, inflight, e2e=False):
         """K round trips with up to `inflight` clips in flight; device time between two events on
@@ -416,7 +437,12 @@ def run_ours(args):
         origin, ms_total, _ = timed_steps(args.steps, INF)
     launches = fhd.fhd_launch_count() - l0
     from paper_2505_07158_gb300 import replicas
-    spans = enc.profile_spans(origin) + dec.profile_spans(origin)
+    enc_spans, dec_spans = enc.profile_spans(origin), dec.profile_spans(origin)
+    spans = enc_spans + dec_spans
+    if args.spans and rank == 0:
+        with open(args.spans, "w") as fh:
+            json.dump({"ms_total": ms_total, "steps": args.steps, "inflight": INF,
+                       "sender": enc_spans, "receiver": dec_spans}, fh)
     prof = {}
     for c in (enc, dec):
         for k, (ms, n) in c.profile_read().items():
@@ -563,7 +589,9 @@ def run_ours(args):
                                    "per GPU, n=32 workers, RK4 h=0.001; per step encrypt_frames on the sender's CUDA stream and "
                                    "decrypt_frames on the receiver's (its chaotic stage waits for the digests, its "
                                    "inverse permutation for the ciphertext)",
-                       "clips_in_flight": INF, "next_clip_gate": args.gate, "worker_layout": args.layout,
+                       "clips_in_flight": INF, "next_clip_gate": args.gate, "worker_window": WW,
+                       "worker_layout": args.layout,
+                       "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),
                        "sm_partition": {"lhcs_m_sms": enc.partition()[0], "other_sms": enc.partition()[1]},
                        "frames_per_step": FRAMES * world, "l2": "inputs larger than L2 (~560 MB live per step)",
                        "parallelism": f"replicas x{world} (independent streams)",

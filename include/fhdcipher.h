@@ -148,6 +148,45 @@ int decrypt_frames_split(fhd_cipher *c, uint32_t count, const fhd_frame *frames,
                          void *const *key_waits, uint32_t n_key_waits, void *const *data_events,
                          uint32_t n_data, void *master_done, void *keystream_done);
 
+/* Every ordering hook of one call.  Events are cudaEvent_t passed as void*,
+ * owned by the caller; a list may be NULL when its count is 0 (a nonzero count
+ * with a NULL list is FHD_ERR_INVALID_ARG), NULL entries are skipped, and a
+ * NULL output event is not recorded.
+ *   key_waits      gate LHCS_m (Sec. II-A: the chaining step; it reads the
+ *                  digests and the chaining state);
+ *   worker_waits   gate the worker kernel (Sec. II-B, the 2n chaotic systems
+ *                  that produce D and B).  A caller streaming batch after batch
+ *                  can bound how many batches' workers share the FP64 pipes
+ *                  (e.g. the workers of batch k wait for those of batch k - 2)
+ *                  while the digest stage and LHCS_m of later batches still run
+ *                  ahead of them;
+ *   data_events    gate the first kernel that reads frames[i].src after the
+ *                  digest stage (the permutation);
+ *   digests_done   recorded once every digest H is in frames[i].digest, before
+ *                  LHCS_m (encryption only: decryption reads the digests);
+ *   master_done    recorded right after LHCS_m;
+ *   keystream_done recorded right after the last worker kernel, before the
+ *                  permutation.
+ * All hooks apply to the first group of 128 frames of the call, the output
+ * events to the last; groups of one call run in order. */
+typedef struct {
+    void *const *key_waits;
+    uint32_t n_key_waits;
+    void *const *worker_waits;
+    uint32_t n_worker_waits;
+    void *const *data_events;
+    uint32_t n_data;
+    void *digests_done;
+    void *master_done;
+    void *keystream_done;
+} fhd_schedule;
+
+/* encrypt_frames / decrypt_frames with the hooks of `sched` (NULL: none). */
+int encrypt_frames_sched(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream,
+                         const fhd_schedule *sched);
+int decrypt_frames_sched(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream,
+                         const fhd_schedule *sched);
+
 /* Pre-allocate at least `bytes` of scratch for calls on CUDA stream `stream`
  * (synchronises that stream), so that later calls on it never allocate.
  * frame_scratch_bytes() gives the scratch one frame needs. */
@@ -260,6 +299,7 @@ int cipher_get_partition(fhd_cipher *c, uint32_t *chain_sms, uint32_t *bulk_sms)
  * share the FP64 pipes (clips in flight, many concurrent streams). */
 enum { FHD_LAYOUT_LATENCY = 0, FHD_LAYOUT_THROUGHPUT = 1 };
 int cipher_set_layout(fhd_cipher *c, int layout);
+
 
 /* ---- Frame statistics of the paper's evaluation (Sec. III and IV-B) ----
  * Batched over `count` frames stored contiguously in device memory as

@@ -37,7 +37,7 @@ EXPORTS = (
     "cipher_reserve", "fhd_frame_scratch_bytes", "fhd_frame_digest_noalloc", "cipher_verify_frames",
     "decrypt_frames_split", "encrypt_frames_split", "cipher_profile_spans", "cipher_set_partition",
     "cipher_get_partition", "cipher_set_layout", "fhd_stats_histogram", "fhd_stats_npcr_uaci",
-    "fhd_stats_correlation", "fhd_stats_local_entropy",
+    "fhd_stats_correlation", "fhd_stats_local_entropy", "encrypt_frames_sched", "decrypt_frames_sched",
 )
 KERNEL_KINDS = ("sha", "master", "keystream", "encrypt", "decrypt")
 
@@ -56,6 +56,15 @@ class FhdFrame(ctypes.Structure):
     _fields_ = [("stream_id", ctypes.c_uint32), ("height", ctypes.c_uint32), ("width", ctypes.c_uint32),
                 ("channels", ctypes.c_uint32), ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p),
                 ("digest", ctypes.c_void_p)]
+
+
+class FhdSchedule(ctypes.Structure):
+    """``fhd_schedule``: the ordering hooks of one call (event lists and output events)."""
+    _fields_ = [("key_waits", ctypes.c_void_p), ("n_key_waits", ctypes.c_uint32),
+                ("worker_waits", ctypes.c_void_p), ("n_worker_waits", ctypes.c_uint32),
+                ("data_events", ctypes.c_void_p), ("n_data", ctypes.c_uint32),
+                ("digests_done", ctypes.c_void_p), ("master_done", ctypes.c_void_p),
+                ("keystream_done", ctypes.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -100,6 +109,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "decrypt_frames_ex": (i32, [P, u32, P, P, P, u32, P]),
             "decrypt_frames_split": (i32, [P, u32, P, P, P, u32, P, u32, P, P]),
             "encrypt_frames_split": (i32, [P, u32, P, P, P, u32, P, P, P]),
+            "encrypt_frames_sched": (i32, [P, u32, P, P, P]),
+            "decrypt_frames_sched": (i32, [P, u32, P, P, P]),
             "cipher_profile_spans": (i32, [P, P, u32, P, P, P, P]),
             "cipher_set_partition": (i32, [P, i32]),
             "cipher_get_partition": (i32, [P, P, P]),
@@ -227,53 +238,50 @@ class Cipher:
             ev.record(stream if stream is not None else torch.cuda.current_stream())
         return ctypes.c_void_p(ev.cuda_event)
 
-    def _run(self, plain, ex, items, stream, master_event, wait_events, encrypt, data_events=(), digest_event=None,
-             keystream_event=None):
+    def _run(self, plain, sched, items, stream, encrypt, key_waits=(), worker_waits=(), data_events=(),
+             digest_event=None, master_event=None, keystream_event=None):
         arr, n = self._frames(items)
-        if master_event is None and not wait_events and not data_events and digest_event is None \
+        if not (key_waits or worker_waits or data_events) and digest_event is None and master_event is None \
                 and keystream_event is None:
             _check(plain(self._handle(), n, arr, _stream_ptr(stream)), self._h)
             return
-        waits = self._events(wait_events)
-        md = self._out_event(master_event, stream)
-        kd = self._out_event(keystream_event, stream)
-        if encrypt and (digest_event is not None or keystream_event is not None):
-            dd = self._out_event(digest_event, stream)
-            _check(load().encrypt_frames_split(self._handle(), n, arr, _stream_ptr(stream), waits, len(wait_events),
-                                               dd, md, kd), self._h)
-            return
-        if not encrypt and (data_events or keystream_event is not None):
-            data = self._events(data_events)
-            _check(load().decrypt_frames_split(self._handle(), n, arr, _stream_ptr(stream), waits, len(wait_events),
-                                               data, len(data_events), md, kd), self._h)
-            return
-        _check(ex(self._handle(), n, arr, _stream_ptr(stream), waits, len(wait_events), md), self._h)
+        lists = [self._events(list(x)) for x in (key_waits, worker_waits, data_events)]
+        hk = FhdSchedule(ctypes.cast(lists[0], ctypes.c_void_p), len(key_waits),
+                         ctypes.cast(lists[1], ctypes.c_void_p), len(worker_waits),
+                         ctypes.cast(lists[2], ctypes.c_void_p), len(data_events),
+                         self._out_event(digest_event if encrypt else None, stream),
+                         self._out_event(master_event, stream), self._out_event(keystream_event, stream))
+        _check(sched(self._handle(), n, arr, _stream_ptr(stream), ctypes.byref(hk)), self._h)
 
     def encrypt_frames(self, items: Iterable, stream=None, master_event=None, wait_events=(), digest_event=None,
-                       keystream_event=None):
+                       keystream_event=None, worker_wait_events=()):
         """items: (stream_id, src, dst, digest) tuples; digest (32 B) is written.
 
         The chaining-state kernel first waits on ``wait_events`` and
         ``master_event`` is recorded right after it; ``digest_event`` is
         recorded once the digests are written, before the chaining-state
-        kernel, and ``keystream_event`` after the worker kernel, before the
-        permutation (all torch.cuda.Event's)."""
+        kernel; the worker kernel waits on ``worker_wait_events`` and
+        ``keystream_event`` is recorded after it, before the permutation (all
+        torch.cuda.Event's)."""
         lib = load()
-        self._run(lib.encrypt_frames, lib.encrypt_frames_ex, items, stream, master_event, list(wait_events), True,
-                  digest_event=digest_event, keystream_event=keystream_event)
+        self._run(lib.encrypt_frames, lib.encrypt_frames_sched, items, stream, True, key_waits=tuple(wait_events),
+                  worker_waits=tuple(worker_wait_events), digest_event=digest_event, master_event=master_event,
+                  keystream_event=keystream_event)
 
     def decrypt_frames(self, items: Iterable, stream=None, master_event=None, wait_events=(), data_events=(),
-                       keystream_event=None):
+                       keystream_event=None, worker_wait_events=()):
         """items: (stream_id, src, dst, digest) tuples; digest (32 B) is read.
 
         ``wait_events`` gate the chaining-state kernel (it reads the digests);
-        ``data_events`` gate the inverse permutation, the first kernel that
-        reads the ciphertext ``src``, so the chaotic stage can run while the
-        ciphertext is still being produced; ``keystream_event`` is recorded
-        after the worker kernel."""
+        ``worker_wait_events`` gate the worker kernel; ``data_events`` gate
+        the inverse permutation, the first kernel that reads the ciphertext
+        ``src``, so the chaotic stage can run while the ciphertext is still
+        being produced; ``keystream_event`` is recorded after the worker
+        kernel."""
         lib = load()
-        self._run(lib.decrypt_frames, lib.decrypt_frames_ex, items, stream, master_event, list(wait_events), False,
-                  list(data_events), keystream_event=keystream_event)
+        self._run(lib.decrypt_frames, lib.decrypt_frames_sched, items, stream, False, key_waits=tuple(wait_events),
+                  worker_waits=tuple(worker_wait_events), data_events=tuple(data_events), master_event=master_event,
+                  keystream_event=keystream_event)
 
     def verify_frames(self, items: Iterable, stream=None) -> torch.Tensor:
         """Receiver-side check: 1 per frame whose decrypted ``dst`` re-hashes to its ``digest``."""

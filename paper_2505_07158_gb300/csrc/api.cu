@@ -393,12 +393,16 @@ uint64_t frame_scratch(uint32_t n, uint32_t h, uint32_t w, uint32_t C) {
 }
 
 int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream, bool encrypt,
-               void *const *wait_events = nullptr, uint32_t n_wait = 0, cudaEvent_t master_done = nullptr,
-               void *const *data_events = nullptr, uint32_t n_data = 0, cudaEvent_t digests_done = nullptr,
-               cudaEvent_t keystream_done = nullptr) {
+               const fhd_schedule *sched = nullptr) {
     if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
+    static const fhd_schedule kNoHooks{};
+    const fhd_schedule &hk = sched ? *sched : kNoHooks;
+    if ((hk.n_key_waits && !hk.key_waits) || (hk.n_worker_waits && !hk.worker_waits) || (hk.n_data && !hk.data_events))
+        return fail(c, FHD_ERR_INVALID_ARG, "null event list with a nonzero count");
     if (count == 0) return FHD_OK;
     if (!frames) return fail(c, FHD_ERR_INVALID_ARG, "null frames");
+    const cudaEvent_t digests_done = (cudaEvent_t)hk.digests_done, master_done = (cudaEvent_t)hk.master_done,
+                      keystream_done = (cudaEvent_t)hk.keystream_done;
     cudaStream_t s = (cudaStream_t)stream;
     for (uint32_t k = 0; k < count; ++k) {
         const fhd_frame &f = frames[k];
@@ -504,8 +508,8 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
         if (part && ((e = cudaEventRecord(ev[1], sb)) != cudaSuccess || (e = cudaStreamWaitEvent(sc, ev[1], 0)) != cudaSuccess))
             return cuda_fail(c, e, "bulk to chain stream");
         if (base == 0)
-            for (uint32_t k = 0; k < n_wait; ++k)
-                if (wait_events[k] && (e = cudaStreamWaitEvent(sc, (cudaEvent_t)wait_events[k], 0)) != cudaSuccess)
+            for (uint32_t k = 0; k < hk.n_key_waits; ++k)
+                if (hk.key_waits[k] && (e = cudaStreamWaitEvent(sc, (cudaEvent_t)hk.key_waits[k], 0)) != cudaSuccess)
                     return cuda_fail(c, e, "wait event");
         if ((e = timed(c, FHD_K_MASTER, sc, [&] { return fhd::launch_master(b, c->d_states, c->d_status, sc); })) != cudaSuccess)
             return cuda_fail(c, e, "master launch");
@@ -513,13 +517,17 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
             return cuda_fail(c, e, "record master event");
         if (part && ((e = cudaEventRecord(ev[2], sc)) != cudaSuccess || (e = cudaStreamWaitEvent(sb, ev[2], 0)) != cudaSuccess))
             return cuda_fail(c, e, "master to bulk stream");
+        if (base == 0)   // caller's gate of the workers (e.g. how many batches' workers share the FP64 pipes)
+            for (uint32_t k = 0; k < hk.n_worker_waits; ++k)
+                if (hk.worker_waits[k] && (e = cudaStreamWaitEvent(sb, (cudaEvent_t)hk.worker_waits[k], 0)) != cudaSuccess)
+                    return cuda_fail(c, e, "wait worker event");
         if ((e = timed(c, FHD_K_KEYSTREAM, sb, [&] { return fhd::launch_keystream(b, sb, c->layout == FHD_LAYOUT_THROUGHPUT); })) != cudaSuccess)
             return cuda_fail(c, e, "keystream launch");
         if (keystream_done && base + m >= count && (e = cudaEventRecord(keystream_done, sb)) != cudaSuccess)
             return cuda_fail(c, e, "record keystream event");
         if (base == 0)   // the first reader of frames[].src after the digest stage
-            for (uint32_t k = 0; k < n_data; ++k)
-                if (data_events[k] && (e = cudaStreamWaitEvent(sb, (cudaEvent_t)data_events[k], 0)) != cudaSuccess)
+            for (uint32_t k = 0; k < hk.n_data; ++k)
+                if (hk.data_events[k] && (e = cudaStreamWaitEvent(sb, (cudaEvent_t)hk.data_events[k], 0)) != cudaSuccess)
                     return cuda_fail(c, e, "wait data event");
         if ((e = timed(c, encrypt ? FHD_K_ENCRYPT : FHD_K_DECRYPT, sb, [&] { return fhd::launch_permute(b, encrypt, sb); })) != cudaSuccess)
             return cuda_fail(c, e, "permute launch");
@@ -587,31 +595,55 @@ int decrypt_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void 
 
 int encrypt_frames_ex(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream,
                       void *const *wait_events, uint32_t n_wait, void *master_done) {
-    if (n_wait && !wait_events) return fail(c, FHD_ERR_INVALID_ARG, "null wait_events");
-    return run_frames(c, count, frames, stream, true, wait_events, n_wait, (cudaEvent_t)master_done);
+    fhd_schedule hk{};
+    hk.key_waits = wait_events;
+    hk.n_key_waits = n_wait;
+    hk.master_done = master_done;
+    return run_frames(c, count, frames, stream, true, &hk);
 }
 
 int decrypt_frames_ex(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream,
                       void *const *wait_events, uint32_t n_wait, void *master_done) {
-    if (n_wait && !wait_events) return fail(c, FHD_ERR_INVALID_ARG, "null wait_events");
-    return run_frames(c, count, frames, stream, false, wait_events, n_wait, (cudaEvent_t)master_done);
+    fhd_schedule hk{};
+    hk.key_waits = wait_events;
+    hk.n_key_waits = n_wait;
+    hk.master_done = master_done;
+    return run_frames(c, count, frames, stream, false, &hk);
 }
 
 int encrypt_frames_split(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream,
                          void *const *wait_events, uint32_t n_wait, void *digests_done, void *master_done,
                          void *keystream_done) {
-    if (n_wait && !wait_events) return fail(c, FHD_ERR_INVALID_ARG, "null wait_events");
-    return run_frames(c, count, frames, stream, true, wait_events, n_wait, (cudaEvent_t)master_done, nullptr, 0,
-                      (cudaEvent_t)digests_done, (cudaEvent_t)keystream_done);
+    fhd_schedule hk{};
+    hk.key_waits = wait_events;
+    hk.n_key_waits = n_wait;
+    hk.digests_done = digests_done;
+    hk.master_done = master_done;
+    hk.keystream_done = keystream_done;
+    return run_frames(c, count, frames, stream, true, &hk);
 }
 
 int decrypt_frames_split(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream,
                          void *const *key_waits, uint32_t n_key_waits, void *const *data_events,
                          uint32_t n_data, void *master_done, void *keystream_done) {
-    if (n_key_waits && !key_waits) return fail(c, FHD_ERR_INVALID_ARG, "null key_waits");
-    if (n_data && !data_events) return fail(c, FHD_ERR_INVALID_ARG, "null data_events");
-    return run_frames(c, count, frames, stream, false, key_waits, n_key_waits, (cudaEvent_t)master_done,
-                      data_events, n_data, nullptr, (cudaEvent_t)keystream_done);
+    fhd_schedule hk{};
+    hk.key_waits = key_waits;
+    hk.n_key_waits = n_key_waits;
+    hk.data_events = data_events;
+    hk.n_data = n_data;
+    hk.master_done = master_done;
+    hk.keystream_done = keystream_done;
+    return run_frames(c, count, frames, stream, false, &hk);
+}
+
+int encrypt_frames_sched(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream,
+                         const fhd_schedule *sched) {
+    return run_frames(c, count, frames, stream, true, sched);
+}
+
+int decrypt_frames_sched(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream,
+                         const fhd_schedule *sched) {
+    return run_frames(c, count, frames, stream, false, sched);
 }
 
 int cipher_verify_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, uint8_t *ok, void *stream) {

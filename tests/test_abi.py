@@ -70,6 +70,9 @@ def test_host_side_checks_of_the_stream_ordering_and_placement_calls(lib):
     assert lib.encrypt_frames_split(None, 1, None, None, None, 0, None, None, None) == fhd.FHD_ERR_INVALID_ARG
     assert lib.decrypt_frames_split(None, 1, None, None, None, 0, ev, 1, None, None) == fhd.FHD_ERR_INVALID_ARG
     assert lib.encrypt_frames_ex(None, 1, None, None, None, 0, None) == fhd.FHD_ERR_INVALID_ARG
+    hk = fhd._lib.FhdSchedule()
+    assert lib.encrypt_frames_sched(None, 1, None, None, ctypes.byref(hk)) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.decrypt_frames_sched(None, 1, None, None, None) == fhd.FHD_ERR_INVALID_ARG
     assert lib.cipher_set_partition(None, 1) == fhd.FHD_ERR_INVALID_ARG
     assert lib.cipher_get_partition(None, ctypes.byref(n), ctypes.byref(n)) == fhd.FHD_ERR_INVALID_ARG
     assert lib.cipher_set_layout(None, 0) == fhd.FHD_ERR_INVALID_ARG

@@ -4,6 +4,8 @@ Each frame's result must be the same alone and in the mix: graph replays of a
 mixed batch are compared with the CPU oracle stream by stream, and every
 frame the continuous-batching server produced is compared (by a digest of the
 ciphertext) with the same stream encrypted alone, one frame per call."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -160,6 +162,41 @@ def test_receiver_starts_before_ciphertext_arrives():
         assert torch.equal(R[k], frames[k]), k
     with pytest.raises(ValueError):
         rcv.decrypt_frames([(rid, wire[0], R[0], H[0])], stream=sb, data_events=[torch.cuda.Event()])
+
+
+def test_worker_gate_holds_only_the_workers():
+    """worker_wait_events gate the worker kernel alone: with the gate held by a ~10 ms sleep on
+    another CUDA stream, the digest stage and LHCS_m finish before it, the workers start after it,
+    and the ciphertext and digest are the oracle's."""
+    key = si.key(630)
+    F = to_dev(si.gradient_frame(120, 160, 3, t=0, seed=631))
+    c = fhd.Cipher(key)
+    sid = c.open_stream()
+    E, H = torch.empty_like(F), torch.empty(32, dtype=torch.uint8, device=dev())
+    other, s = torch.cuda.Stream(), torch.cuda.Stream()
+    origin, gate = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    c.profile(True)
+    origin.record(s)
+    other.wait_event(origin)
+    with torch.cuda.stream(other):
+        torch.cuda._sleep(20_000_000)
+        gate.record(other)
+    c.encrypt_frames([(sid, F, E, H)], stream=s, master_event=torch.cuda.Event(), worker_wait_events=[gate])
+    torch.cuda.synchronize()
+    spans = {k: (a, b) for k, a, b in c.profile_spans(origin)}
+    c.profile(False)
+    gate_ms = origin.elapsed_time(gate)
+    assert gate_ms > 1.0
+    assert spans["sha"][1] < gate_ms and spans["master"][1] < gate_ms
+    assert spans["keystream"][0] >= gate_ms - 1e-3
+    E_ref, H_ref = oracle.Stream.from_key(key).encrypt(host(F))
+    assert np.array_equal(host(E), E_ref) and bytes(host(H)) == H_ref
+    # a nonzero count with a null list is an argument error, caught before anything is enqueued
+    hk = fhd._lib.FhdSchedule()
+    hk.n_worker_waits = 1
+    arr, n = c._frames([(sid, F, E, H)])
+    assert fhd._lib.load().encrypt_frames_sched(c._handle(), n, arr, None, ctypes.byref(hk)) == fhd.FHD_ERR_INVALID_ARG
 
 
 def test_launch_count_per_call():
