@@ -54,7 +54,12 @@ def frame_footprint(h: int, w: int, C: int, n: int) -> int:
 
 
 class Server:
-    """Serve a set of video streams with continuous batching."""
+    """Serve a set of video streams with continuous batching.
+
+    The lanes are CUDA streams whose calls wait on each other's chaining events; run the process with
+    CUDA_DEVICE_MAX_CONNECTIONS=32 (set before CUDA starts) so that each lane has its own hardware queue.
+    With the default 8, a lane held by an event wait stalls the lanes that share its queue (measured on the
+    32-stream workload at 60 fps: p99 44.9 ms with 8 queues, 14.5 ms with 32)."""
 
     def __init__(self, keys, shapes, frame_pool, n_workers: int = 32, budget_bytes: int = 20 << 30,
                  lanes: int = 16, slots_per_lane: int = 1, max_batch: int = 64, fingerprint: bool = False,
