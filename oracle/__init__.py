@@ -59,6 +59,7 @@ def _load():
         u32, u64, dbl = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
         lib.oracle_sha256.argtypes = [P, u64, P]
         lib.oracle_frame_digest.argtypes = [P, u64, u32, P]
+        lib.oracle_frame_digest_tree.argtypes = [P, u64, u32, P]
         lib.oracle_key_to_ic.argtypes = [P, P, P]
         lib.oracle_reconstruct.argtypes = [dbl, P, u32]
         lib.oracle_reconstruct.restype = dbl
@@ -68,7 +69,7 @@ def _load():
         lib.oracle_permute_encrypt.argtypes = [P, u32, u32, u32, P, P, P]
         lib.oracle_permute_decrypt.argtypes = [P, u32, u32, u32, P, P, P]
         lib.oracle_frame_keystream.argtypes = [P, dbl, dbl, u32, P, P, u32, u32, u32, P, P]
-        lib.oracle_encrypt_frame.argtypes = [P, dbl, dbl, u32, P, P, u32, u32, u32, P, P]
+        lib.oracle_encrypt_frame.argtypes = [P, dbl, dbl, u32, P, P, u32, u32, u32, P, P, u32]
         lib.oracle_decrypt_frame.argtypes = [P, dbl, dbl, u32, P, P, u32, u32, u32, P, P]
         _lib = lib
         return lib
@@ -96,12 +97,17 @@ def sha256(msg) -> bytes:
     return out.tobytes()
 
 
-def frame_digest(frame, n: int = DEFAULT_N) -> bytes:
-    """Sec. II-A: XOR of the SHA-256 digests of the n sub-frames."""
+DIGEST_MODES = {"xor": 0, "tree": 1}
+
+
+def frame_digest(frame, n: int = DEFAULT_N, mode: str = "xor") -> bytes:
+    """Sec. II-A: XOR of the SHA-256 digests of the n sub-frames (mode "xor").  Mode "tree", an option of
+    this implementation rather than the paper's: SHA-256 of the n sub-frame digests concatenated in order."""
     f = _u8(frame).reshape(-1)
     out = np.zeros(32, np.uint8)
     buf = f if f.size else np.zeros(1, np.uint8)
-    _load().oracle_frame_digest(_ptr(buf), f.size, n, _ptr(out))
+    fn = _load().oracle_frame_digest_tree if DIGEST_MODES[mode] == 1 else _load().oracle_frame_digest
+    fn(_ptr(buf), f.size, n, _ptr(out))
     return out.tobytes()
 
 
@@ -188,15 +194,16 @@ class Stream:
     The first frame reconstructs from the key's x0..w0; every later frame from
     x_2n..w_2n of the previous frame's LHCS_m run (Algorithm 1)."""
 
-    def __init__(self, ic, n: int = DEFAULT_N, h: float = DEFAULT_H, u=DEFAULT_U):
+    def __init__(self, ic, n: int = DEFAULT_N, h: float = DEFAULT_H, u=DEFAULT_U, digest_mode: str = "xor"):
         ic = tuple(float(v) for v in ic)
         self.state = np.array(ic[:4], np.float64)
         self.gamma = ic[4]
         self.n, self.h, self.u = n, h, _u32x4(u)
+        self.digest_mode = DIGEST_MODES[digest_mode]
 
     @classmethod
-    def from_key(cls, key: bytes, n: int = DEFAULT_N, h: float = DEFAULT_H, u=DEFAULT_U):
-        return cls(key_to_ic(key, u), n, h, u)
+    def from_key(cls, key: bytes, n: int = DEFAULT_N, h: float = DEFAULT_H, u=DEFAULT_U, digest_mode: str = "xor"):
+        return cls(key_to_ic(key, u), n, h, u, digest_mode)
 
     def frame_keystream(self, H: bytes, hgt: int, wid: int, C: int):
         """Advance the chain by one frame; return that frame's (D, B)."""
@@ -214,7 +221,7 @@ class Stream:
         E = np.zeros_like(F)
         H = np.zeros(32, np.uint8)
         _load().oracle_encrypt_frame(_ptr(self.state), self.gamma, self.h, self.n, _ptr(self.u),
-                                     _ptr(F), h, w, C, _ptr(E), _ptr(H))
+                                     _ptr(F), h, w, C, _ptr(E), _ptr(H), self.digest_mode)
         return E, H.tobytes()
 
     def decrypt(self, E, H: bytes):

@@ -142,6 +142,23 @@ void oracle_frame_digest(const uint8_t *frame, uint64_t N, uint32_t n, uint8_t H
     }
 }
 
+/* Tree digest: an option of this implementation, not of the paper.  With the
+ * XOR fold above, identical sub-frames cancel (a flat frame split into an even
+ * number of equal sub-frames has H = 0) and the order of the sub-frames does
+ * not matter.  This mode keeps the same partition and sub-frame digests and
+ * hashes their concatenation instead: H = SHA-256(h_1 || h_2 || ... || h_n),
+ * 32 n bytes in sub-frame order.  Sender and receiver must use the same mode. */
+void oracle_frame_digest_tree(const uint8_t *frame, uint64_t N, uint32_t n, uint8_t H[32]) {
+    uint8_t *cat = (uint8_t *)malloc(32ull * n);
+    for (uint32_t i = 0; i < n; ++i) {
+        uint64_t lo = (uint64_t)(((unsigned __int128)N * i) / n);
+        uint64_t hi = (uint64_t)(((unsigned __int128)N * (i + 1)) / n);
+        oracle_sha256(frame + lo, hi - lo, cat + 32ull * i);
+    }
+    oracle_sha256(cat, 32ull * n, H);
+    free(cat);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Key and initial-condition reconstruction (Sec. II-A, Fig. 1a).           */
 /* ------------------------------------------------------------------------ */
@@ -433,12 +450,14 @@ void oracle_frame_keystream(double state[4], double gamma, double hstep, uint32_
     free(IR);
 }
 
+/* digest_mode 0: the paper's XOR fold; 1: the tree digest (not the paper's). */
 void oracle_encrypt_frame(double state[4], double gamma, double hstep, uint32_t n,
                           const uint32_t u[4], const uint8_t *F, uint32_t h, uint32_t w,
-                          uint32_t C, uint8_t *E, uint8_t H[32]) {
+                          uint32_t C, uint8_t *E, uint8_t H[32], uint32_t digest_mode) {
     uint64_t N = (uint64_t)h * w * C;
     uint64_t LD = (uint64_t)C * (h + w);
-    oracle_frame_digest(F, N, n, H);
+    if (digest_mode == 1) oracle_frame_digest_tree(F, N, n, H);
+    else oracle_frame_digest(F, N, n, H);
     uint16_t *D = (uint16_t *)malloc(sizeof(uint16_t) * (LD ? LD : 1));
     uint8_t *B = (uint8_t *)malloc(N ? N : 1);
     oracle_frame_keystream(state, gamma, hstep, n, u, H, h, w, C, D, B);
