@@ -690,6 +690,7 @@ def run_extras(args, rank, fhd, torch):
     del pool
     torch.cuda.empty_cache()
     out["worker_count_sweep"] = run_n_sweep(rank, fhd, torch)
+    out["digest_modes"] = run_digest_modes(rank, fhd, torch)
     out["frame_statistics"] = run_stats(rank, fhd, torch)
     if not args.no_stress:
         out["stress_8k"] = run_stress(rank, fhd, torch)
@@ -768,6 +769,53 @@ def run_n_sweep(rank, fhd, torch, ns=(32, 128, 512), steps=3):
                        "round_trip_ok": bool(torch.equal(R, clip))}
         enc.close(); dec.close()
     return {"workload": "30-frame 1080p clip round trip (as the headline) with n workers", **res}
+
+
+def run_digest_modes(rank, fhd, torch, reps=10, steps=3):
+    """The frame digest in the paper's XOR-fold mode and in the tree mode (SHA-256 of the concatenated
+    sub-frame digests, an option of this library): the digest stage alone on the 30-frame 1080p clip, and the
+    clip's round trip (one CUDA stream, as the n sweep) in each mode; frame 0's digests checked against the
+    oracle."""
+    import oracle
+    dev = torch.device("cuda", torch.cuda.current_device())
+    clip_np = si.clip(FRAMES, HGT, WID, CH, seed=rank + 5)
+    clip = torch.from_numpy(clip_np).to(dev)
+    flat = clip.reshape(-1)
+    res, ok = {}, True
+    for mode in ("xor", "tree"):
+        dig = fhd.fhd_frame_digest(flat, n=N_WORKERS, count=FRAMES, mode=mode)
+        torch.cuda.synchronize()
+        ok = ok and bytes(dig[0].cpu().numpy()) == oracle.frame_digest(clip_np[0], N_WORKERS, mode)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fhd.fhd_frame_digest(flat, n=N_WORKERS, count=FRAMES, out=dig, mode=mode)
+        b.record()
+        b.synchronize()
+        digest_ms = a.elapsed_time(b) / reps
+        key = si.key(900 + rank)
+        enc = fhd.Cipher(key, n_workers=N_WORKERS, digest_mode=mode)
+        dec = fhd.Cipher(key, n_workers=N_WORKERS, digest_mode=mode)
+        sid, rid = enc.open_stream(), dec.open_stream()
+        E, R = torch.empty_like(clip), torch.empty_like(clip)
+        H = torch.empty((FRAMES, 32), dtype=torch.uint8, device=dev)
+        ei = [(sid, clip[t], E[t], H[t]) for t in range(FRAMES)]
+        di = [(rid, E[t], R[t], H[t]) for t in range(FRAMES)]
+        enc.encrypt_frames(ei); dec.decrypt_frames(di)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(steps):
+            enc.encrypt_frames(ei)
+            dec.decrypt_frames(di)
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b) / steps
+        verified = dec.verify_frames(di)
+        res[mode] = {"digest_ms_per_clip": digest_ms, "round_trip_frames_per_s": FRAMES / (ms / 1000.0),
+                     "round_trip_ok": bool(torch.equal(R, clip)), "verify_ok": bool(int(verified.min()) == 1)}
+        enc.close(); dec.close()
+    return {"workload": "30 x 1080p clip: the digest stage alone (n = 32), and the round trip on one CUDA stream",
+            **res, "frame0_digests_match_oracle": bool(ok)}
 
 
 def run_stress(rank, fhd, torch, frames=256):

@@ -64,7 +64,15 @@ typedef struct {
     uint32_t n_workers;  /* n: sub-frames per frame and worker pairs; default 32 (Tab. speedEvaluation) */
     double rk4_h;        /* step of the RK4 integration of Eq. (1); default 0.001 */
     uint32_t u_bound[4]; /* reconstruction upper bounds u_x, u_y, u_z, u_w; default 20, 20, 40, 20 */
+    uint32_t digest_mode; /* how H is formed from the n sub-frame digests h_i: FHD_DIGEST_XOR (0, default) */
 } fhd_params;
+
+/* Digest modes.  FHD_DIGEST_XOR: H = h_1 xor ... xor h_n (Sec. II-A, Algorithm 1).  FHD_DIGEST_TREE, an
+ * option of this library and not of the paper: H = SHA-256(h_1 || ... || h_n), the 32 n bytes of the
+ * sub-frame digests concatenated in order, so that identical sub-frames do not cancel and their order
+ * counts.  Same partition and sub-frame digests either way; both ends of a channel must use the same
+ * mode (it decides the H the sender transmits and the receiver's integrity check). */
+enum { FHD_DIGEST_XOR = 0, FHD_DIGEST_TREE = 1 };
 
 /* One frame of a batch.  `digest` is written by encrypt_frames (the 32-byte
  * H the receiver needs, Sec. V) and read by decrypt_frames. */
@@ -226,6 +234,11 @@ void cipher_destroy(fhd_cipher *c);
  * (data + k*nbytes -> digest + 32k) are hashed in one launch. */
 int fhd_frame_digest(const uint8_t *data, uint64_t nbytes, uint32_t n, uint32_t count,
                      uint8_t *digest, void *stream);
+
+/* As fhd_frame_digest with the FHD_DIGEST_TREE mode: digest[32] = SHA-256 of the n sub-frame digests
+ * concatenated in order (not the paper's fold; see fhd_params.digest_mode). */
+int fhd_frame_digest_tree(const uint8_t *data, uint64_t nbytes, uint32_t n, uint32_t count,
+                          uint8_t *digest, void *stream);
 
 /* fhd_frame_digest for callers that cannot allocate device memory (no
  * counterpart in the paper).  Some callers may not call cudaMalloc or any

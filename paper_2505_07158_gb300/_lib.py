@@ -38,6 +38,7 @@ EXPORTS = (
     "decrypt_frames_split", "encrypt_frames_split", "cipher_profile_spans", "cipher_set_partition",
     "cipher_get_partition", "cipher_set_layout", "fhd_stats_histogram", "fhd_stats_npcr_uaci",
     "fhd_stats_correlation", "fhd_stats_local_entropy", "encrypt_frames_sched", "decrypt_frames_sched",
+    "fhd_frame_digest_tree",
 )
 KERNEL_KINDS = ("sha", "master", "keystream", "encrypt", "decrypt")
 
@@ -49,7 +50,13 @@ class FhdError(RuntimeError):
 
 
 class FhdParams(ctypes.Structure):
-    _fields_ = [("n_workers", ctypes.c_uint32), ("rk4_h", ctypes.c_double), ("u_bound", ctypes.c_uint32 * 4)]
+    _fields_ = [("n_workers", ctypes.c_uint32), ("rk4_h", ctypes.c_double), ("u_bound", ctypes.c_uint32 * 4),
+                ("digest_mode", ctypes.c_uint32)]
+
+
+# How the frame digest H is formed from the n sub-frame digests: "xor" is the paper's fold (Sec. II-A),
+# "tree" (an option of this library) is SHA-256 of the sub-frame digests concatenated in order.
+DIGEST_MODES = {"xor": 0, "tree": 1}
 
 
 class FhdFrame(ctypes.Structure):
@@ -95,6 +102,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "cipher_destroy": (None, [P]),
             "fhd_frame_digest": (i32, [P, u64, u32, u32, P, P]),
             "fhd_frame_digest_noalloc": (i32, [P, u64, u32, u32, P, P]),
+            "fhd_frame_digest_tree": (i32, [P, u64, u32, u32, P, P]),
             "fhd_master": (i32, [P, P, P, P, P]),
             "fhd_keystream": (i32, [P, dbl, P, u32, u32, u32, P, P, P]),
             "fhd_permute_encrypt": (i32, [P, P, u32, u32, u32, P, P, P]),
@@ -147,12 +155,13 @@ def _stream_ptr(stream) -> ctypes.c_void_p:
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _params(n_workers=32, rk4_h=0.001, u_bound=(20, 20, 40, 20)) -> FhdParams:
+def _params(n_workers=32, rk4_h=0.001, u_bound=(20, 20, 40, 20), digest_mode="xor") -> FhdParams:
     p = FhdParams()
     p.n_workers = n_workers
     p.rk4_h = rk4_h
     for m in range(4):
         p.u_bound[m] = u_bound[m]
+    p.digest_mode = DIGEST_MODES[digest_mode]
     return p
 
 
@@ -174,9 +183,10 @@ class Cipher:
     """A cipher handle: key, protocol parameters and device-resident streams."""
 
     def __init__(self, key: bytes | None = None, ic: Sequence[float] | None = None, n_workers: int = 32,
-                 rk4_h: float = 0.001, u_bound=(20, 20, 40, 20)):
+                 rk4_h: float = 0.001, u_bound=(20, 20, 40, 20), digest_mode: str = "xor"):
         lib = load()
-        self.params = _params(n_workers, rk4_h, u_bound)
+        self.params = _params(n_workers, rk4_h, u_bound, digest_mode)
+        self.digest_mode = digest_mode
         self.n_workers = n_workers
         h = ctypes.c_void_p()
         if ic is not None:
@@ -377,8 +387,11 @@ class Cipher:
 
 # ---- one call per step of the hot path ----
 
-def fhd_frame_digest(data: torch.Tensor, n: int = 32, count: int = 1, out: torch.Tensor | None = None, stream=None):
-    """XOR of sub-frame SHA-256 digests of ``count`` equal buffers laid end to end."""
+def fhd_frame_digest(data: torch.Tensor, n: int = 32, count: int = 1, out: torch.Tensor | None = None, stream=None,
+                     mode: str = "xor"):
+    """Frame digest of ``count`` equal buffers laid end to end: the XOR of the n sub-frame SHA-256 digests
+    (mode "xor", the paper's), or SHA-256 of those digests concatenated in order (mode "tree")."""
+    fn = {"xor": load().fhd_frame_digest, "tree": load().fhd_frame_digest_tree}[mode]
     if not data.is_cuda or data.dtype != torch.uint8 or not data.is_contiguous():
         raise ValueError("data must be a contiguous CUDA uint8 tensor")
     if data.numel() % max(count, 1):
@@ -387,8 +400,7 @@ def fhd_frame_digest(data: torch.Tensor, n: int = 32, count: int = 1, out: torch
     if out is None:
         out = torch.empty((count, 32), dtype=torch.uint8, device=data.device)
     ptr = data.data_ptr() if data.numel() else 0
-    _check(load().fhd_frame_digest(ctypes.c_void_p(ptr), nbytes, n, count, ctypes.c_void_p(out.data_ptr()),
-                                   _stream_ptr(stream)))
+    _check(fn(ctypes.c_void_p(ptr), nbytes, n, count, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
     return out
 
 

@@ -45,6 +45,7 @@ struct fhd_cipher {
     std::vector<Scratch> scratch;
     bool partition = false;
     int layout = FHD_LAYOUT_LATENCY;
+    uint32_t digest_mode = FHD_DIGEST_XOR;
     cudaStream_t last_stream = nullptr;
     std::string err;
     bool prof = false;
@@ -426,6 +427,7 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
         std::memset(&b, 0, sizeof b);
         b.count = m;
         b.n = c->n;
+        b.digest_mode = c->digest_mode;
         b.hstep = c->h;
         b.hhalf = c->h / 2.0;
         b.hsixth = c->h / 6.0;
@@ -497,7 +499,9 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
         if (encrypt) {
             if ((e = timed(c, FHD_K_SHA, sb, [&] {
                      cudaError_t r = fhd::launch_sha_subframes(b, sb);
-                     return r == cudaSuccess ? fhd::launch_fold_batch(b, sb) : r;
+                     if (r != cudaSuccess) return r;
+                     return b.digest_mode == FHD_DIGEST_TREE ? fhd::launch_tree_batch(b, sb)
+                                                             : fhd::launch_fold_batch(b, sb);
                  })) != cudaSuccess)
                 return cuda_fail(c, e, "sha launch");
             if (digests_done && base + m >= count && (e = cudaEventRecord(digests_done, sb)) != cudaSuccess)
@@ -544,26 +548,39 @@ extern "C" {
 
 const char *fhd_version(void) { return "fhdcipher 0.1 (sm_103a)"; }
 
+// The digest mode of `params` (FHD_DIGEST_XOR when params is NULL).
+bool resolve_digest_mode(const fhd_params *p, uint32_t &mode, std::string &why) {
+    mode = p ? p->digest_mode : (uint32_t)FHD_DIGEST_XOR;
+    if (mode != FHD_DIGEST_XOR && mode != FHD_DIGEST_TREE) { why = "unknown digest_mode"; return false; }
+    return true;
+}
+
 int cipher_init(const uint8_t key[32], const fhd_params *params, fhd_cipher **out) {
     if (!key || !out) return fail(nullptr, FHD_ERR_INVALID_ARG, "null argument");
-    uint32_t n, u[4];
+    uint32_t n, u[4], mode;
     double h;
     std::string why;
-    if (!resolve_params(params, n, h, u, why)) return fail(nullptr, FHD_ERR_INVALID_ARG, why);
+    if (!resolve_params(params, n, h, u, why) || !resolve_digest_mode(params, mode, why))
+        return fail(nullptr, FHD_ERR_INVALID_ARG, why);
     double ic[5];
     key_to_ic(key, u, ic);
-    return init_common(ic, n, h, u, out);
+    int rc = init_common(ic, n, h, u, out);
+    if (rc == FHD_OK) (*out)->digest_mode = mode;
+    return rc;
 }
 
 int cipher_init_raw(double x0, double y0, double z0, double w0, double gamma, const fhd_params *params,
                     fhd_cipher **out) {
     if (!out) return fail(nullptr, FHD_ERR_INVALID_ARG, "null argument");
-    uint32_t n, u[4];
+    uint32_t n, u[4], mode;
     double h;
     std::string why;
-    if (!resolve_params(params, n, h, u, why)) return fail(nullptr, FHD_ERR_INVALID_ARG, why);
+    if (!resolve_params(params, n, h, u, why) || !resolve_digest_mode(params, mode, why))
+        return fail(nullptr, FHD_ERR_INVALID_ARG, why);
     const double ic[5] = {x0, y0, z0, w0, gamma};
-    return init_common(ic, n, h, u, out);
+    int rc = init_common(ic, n, h, u, out);
+    if (rc == FHD_OK) (*out)->digest_mode = mode;
+    return rc;
 }
 
 int cipher_open_stream(fhd_cipher *c, uint32_t *stream_id) {
@@ -663,6 +680,7 @@ int cipher_verify_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames,
         std::memset(&b, 0, sizeof b);
         b.count = m;
         b.n = c->n;
+        b.digest_mode = c->digest_mode;
         uint8_t *p = nullptr;
         int rc = ensure_scratch(c, s, (uint64_t)m * 32ull * c->n, &p);
         if (rc != FHD_OK) return rc;
@@ -925,6 +943,22 @@ int fhd_frame_digest(const uint8_t *data, uint64_t nbytes, uint32_t n, uint32_t 
     if (e != cudaSuccess) return fail(nullptr, FHD_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
     e = timed(nullptr, FHD_K_SHA, s, [&] { return fhd::launch_sha_plain(data, nbytes, n, count, part, s); });
     if (e == cudaSuccess) e = timed(nullptr, FHD_K_SHA, s, [&] { return fhd::launch_fold(part, n, count, digest, s); });
+    cudaFreeAsync(part, s);
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("digest launch: ") + cudaGetErrorString(e));
+    return FHD_OK;
+}
+
+int fhd_frame_digest_tree(const uint8_t *data, uint64_t nbytes, uint32_t n, uint32_t count, uint8_t *digest,
+                          void *stream) {
+    if ((!data && nbytes) || !digest) return fail(nullptr, FHD_ERR_INVALID_ARG, "null argument");
+    if (n == 0 || n > FHD_MAX_WORKERS) return fail(nullptr, FHD_ERR_INVALID_ARG, "n must be 1..FHD_MAX_WORKERS");
+    if (count == 0) return FHD_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint8_t *part = nullptr;
+    cudaError_t e = cudaMallocAsync(&part, 32ull * n * count, s);
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+    e = timed(nullptr, FHD_K_SHA, s, [&] { return fhd::launch_sha_plain(data, nbytes, n, count, part, s); });
+    if (e == cudaSuccess) e = timed(nullptr, FHD_K_SHA, s, [&] { return fhd::launch_tree(part, n, count, digest, s); });
     cudaFreeAsync(part, s);
     if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("digest launch: ") + cudaGetErrorString(e));
     return FHD_OK;

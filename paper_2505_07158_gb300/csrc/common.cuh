@@ -37,6 +37,7 @@ struct Batch {
     uint32_t groups;          // streams in this batch (master CTAs)
     uint32_t perm_ctas;       // total column-pass CTAs
     uint32_t row_ctas;        // total row-pass CTAs
+    uint32_t digest_mode;     // FHD_DIGEST_XOR (the paper's fold) or FHD_DIGEST_TREE
     double hstep, hhalf, hsixth;   // RK4 step h, h/2 and h/6 (rounded once, on the host)
     uint32_t u[4];            // reconstruction bounds
     uint16_t order[kMaxBatch];          // frame indices grouped by stream, in call order
@@ -65,6 +66,8 @@ cudaError_t launch_verify(const Batch &b, uint8_t *ok, cudaStream_t s);   // ok[
 cudaError_t launch_sha_plain(const uint8_t *data, uint64_t nbytes, uint32_t n, uint32_t count,
                              uint8_t *part, cudaStream_t s);
 cudaError_t launch_fold(const uint8_t *part, uint32_t n, uint32_t count, uint8_t *digest, cudaStream_t s);
+cudaError_t launch_tree_batch(const Batch &b, cudaStream_t s);
+cudaError_t launch_tree(const uint8_t *part, uint32_t n, uint32_t count, uint8_t *digest, cudaStream_t s);
 cudaError_t launch_fold_batch(const Batch &b, cudaStream_t s);
 // Counts one kernel launch of this library (read by fhd_launch_count).
 void note_launch();

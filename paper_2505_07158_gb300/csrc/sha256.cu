@@ -268,13 +268,65 @@ __global__ void __launch_bounds__(64) sha_dst_kernel(const __grid_constant__ Bat
         b.count * n);
 }
 
-// ok[k] = (XOR over i of frame k's sub-frame digests) == frame k's digest.
+// One SHA-256 compression (FIPS 180-4 Sec. 6.2.2) of the 16 message words w into h; one thread.
+__device__ __forceinline__ void compress_block(uint32_t h[8], uint32_t w[16]) {
+    uint32_t a = h[0], bb = h[1], c = h[2], d = h[3], e = h[4], f = h[5], g = h[6], hh = h[7];
+#pragma unroll
+    for (int t = 0; t < 64; ++t) {
+        if (t >= 16) {
+            const uint32_t x = w[(t - 15) & 15], y = w[(t - 2) & 15];
+            w[t & 15] += (rotr(x, 7) ^ rotr(x, 18) ^ (x >> 3)) + w[(t - 7) & 15] + (rotr(y, 17) ^ rotr(y, 19) ^ (y >> 10));
+        }
+        const uint32_t t1 = hh + (rotr(e, 6) ^ rotr(e, 11) ^ rotr(e, 25)) + ((e & f) ^ (~e & g)) + kK[t] + w[t & 15];
+        const uint32_t t2 = (rotr(a, 2) ^ rotr(a, 13) ^ rotr(a, 22)) + ((a & bb) ^ (a & c) ^ (bb & c));
+        hh = g; g = f; f = e; e = d + t1; d = c; c = bb; bb = a; a = t1 + t2;
+    }
+    h[0] += a; h[1] += bb; h[2] += c; h[3] += d; h[4] += e; h[5] += f; h[6] += g; h[7] += hh;
+}
+
+// Tree digest (an option of this library, not of the paper): SHA-256 of the n sub-frame digests at `part`
+// concatenated in order, 32 n bytes; one thread.  The stored digests are big-endian bytes, so each message
+// word is the byte swap of a stored 32-bit word.  32 n bytes end on a half or a whole 64-byte block: the
+// padding (0x80, zeros, the 64-bit bit length 256 n) always fits in the last block.
+__device__ void tree_digest(const uint8_t *part, uint32_t n, uint32_t h[8]) {
+    ShaState st;
+    st.init();
+    const uint32_t *p = reinterpret_cast<const uint32_t *>(part);
+    const uint32_t words = 8 * n;
+    uint32_t w[16];
+    uint32_t i = 0;
+    for (; i + 16 <= words; i += 16) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) w[k] = bswap(p[i + k]);
+        compress_block(st.h, w);
+    }
+    const uint32_t rem = words - i;   // 0 or 8
+#pragma unroll
+    for (int k = 0; k < 16; ++k) w[k] = (uint32_t)k < rem ? bswap(p[i + k]) : 0u;
+    w[rem] = 0x80000000u;
+    const uint64_t bits = 256ull * n;
+    w[14] = (uint32_t)(bits >> 32);
+    w[15] = (uint32_t)bits;
+    compress_block(st.h, w);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) h[k] = st.h[k];
+}
+
+// ok[k] = (frame k's digest recomputed from its sub-frame digests, by the batch's digest mode) == frame k's
+// transmitted digest.
 __global__ void verify_kernel(const __grid_constant__ Batch b, uint8_t *ok) {
     const uint32_t k = blockIdx.x, lane = threadIdx.x;
     if (k >= b.count) return;
     const FrameDesc &fd = b.f[k];
     uint32_t diff = 0;
-    if (lane < 8) {
+    if (b.digest_mode == FHD_DIGEST_TREE) {
+        if (lane == 0) {
+            uint32_t h[8];
+            tree_digest(fd.part, b.n, h);
+            const uint32_t *t = reinterpret_cast<const uint32_t *>(fd.digest);
+            for (int q = 0; q < 8; ++q) diff |= bswap(h[q]) ^ t[q];
+        }
+    } else if (lane < 8) {
         const uint32_t *p = reinterpret_cast<const uint32_t *>(fd.part);
         uint32_t acc = 0;
         for (uint32_t i = 0; i < b.n; ++i) acc ^= p[8 * i + lane];
@@ -282,6 +334,25 @@ __global__ void verify_kernel(const __grid_constant__ Batch b, uint8_t *ok) {
     }
     diff = __reduce_or_sync(0xffffffffu, diff);
     if (lane == 0) ok[fd.slot] = diff == 0 ? 1 : 0;
+}
+
+// Tree digests of a batch: one thread per frame, written to the frame's digest.
+__global__ void tree_batch_kernel(const __grid_constant__ Batch b) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= b.count) return;
+    const FrameDesc &fd = b.f[k];
+    uint32_t h[8];
+    tree_digest(fd.part, b.n, h);
+    store_digest(fd.digest, h);
+}
+
+// Tree digests of `count` buffers' sub-frame digests (part[k*n .. k*n + n)); one thread per buffer.
+__global__ void tree_kernel(const uint8_t *part, uint32_t n, uint32_t count, uint8_t *digest) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    uint32_t h[8];
+    tree_digest(part + 32ull * n * k, n, h);
+    store_digest(digest + 32ull * k, h);
 }
 
 // digest[k] = XOR over i of part[k*n + i]; one warp per buffer, lane = byte-word.
@@ -371,6 +442,20 @@ cudaError_t launch_sha_plain(const uint8_t *data, uint64_t nbytes, uint32_t n, u
 cudaError_t launch_fold_batch(const Batch &b, cudaStream_t s) {
     if (!b.count) return cudaSuccess;
     fold_batch_kernel<<<b.count, 32, 0, s>>>(b);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tree_batch(const Batch &b, cudaStream_t s) {
+    if (!b.count) return cudaSuccess;
+    tree_batch_kernel<<<(b.count + 31) / 32, 32, 0, s>>>(b);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tree(const uint8_t *part, uint32_t n, uint32_t count, uint8_t *digest, cudaStream_t s) {
+    if (!count) return cudaSuccess;
+    tree_kernel<<<(count + 31) / 32, 32, 0, s>>>(part, n, count, digest);
     note_launch();
     return cudaGetLastError();
 }
