@@ -69,8 +69,9 @@ def _load():
         lib.oracle_permute_encrypt.argtypes = [P, u32, u32, u32, P, P, P]
         lib.oracle_permute_decrypt.argtypes = [P, u32, u32, u32, P, P, P]
         lib.oracle_frame_keystream.argtypes = [P, dbl, dbl, u32, P, P, u32, u32, u32, P, P]
-        lib.oracle_encrypt_frame.argtypes = [P, dbl, dbl, u32, P, P, u32, u32, u32, P, P, u32]
-        lib.oracle_decrypt_frame.argtypes = [P, dbl, dbl, u32, P, P, u32, u32, u32, P, P]
+        lib.oracle_encrypt_frame.argtypes = [P, dbl, dbl, u32, P, P, u32, u32, u32, P, P, u32, u32]
+        lib.oracle_decrypt_frame.argtypes = [P, dbl, dbl, u32, P, P, u32, u32, u32, P, P, u32]
+        lib.oracle_digest_mask.argtypes = [P, dbl, P]
         _lib = lib
         return lib
 
@@ -98,6 +99,9 @@ def sha256(msg) -> bytes:
 
 
 DIGEST_MODES = {"xor": 0, "tree": 1}
+# How the digest travels (Sec. V sends it encrypted, mechanism not given): "plain" as computed, or "masked"
+# (an option of this implementation) XORed with a mask derived from the stream's chaining state.
+TRANSPORTS = {"plain": 0, "masked": 1}
 
 
 def frame_digest(frame, n: int = DEFAULT_N, mode: str = "xor") -> bytes:
@@ -194,16 +198,26 @@ class Stream:
     The first frame reconstructs from the key's x0..w0; every later frame from
     x_2n..w_2n of the previous frame's LHCS_m run (Algorithm 1)."""
 
-    def __init__(self, ic, n: int = DEFAULT_N, h: float = DEFAULT_H, u=DEFAULT_U, digest_mode: str = "xor"):
+    def __init__(self, ic, n: int = DEFAULT_N, h: float = DEFAULT_H, u=DEFAULT_U, digest_mode: str = "xor",
+                 transport: str = "plain"):
         ic = tuple(float(v) for v in ic)
         self.state = np.array(ic[:4], np.float64)
         self.gamma = ic[4]
         self.n, self.h, self.u = n, h, _u32x4(u)
         self.digest_mode = DIGEST_MODES[digest_mode]
+        self.masked = TRANSPORTS[transport]
 
     @classmethod
-    def from_key(cls, key: bytes, n: int = DEFAULT_N, h: float = DEFAULT_H, u=DEFAULT_U, digest_mode: str = "xor"):
-        return cls(key_to_ic(key, u), n, h, u, digest_mode)
+    def from_key(cls, key: bytes, n: int = DEFAULT_N, h: float = DEFAULT_H, u=DEFAULT_U, digest_mode: str = "xor",
+                 transport: str = "plain"):
+        return cls(key_to_ic(key, u), n, h, u, digest_mode, transport)
+
+    def digest_mask(self) -> bytes:
+        """The mask M of the next frame's transmitted digest (masked transport, an option of this
+        implementation): SHA-256 of "FHDMASK1" and the LE64 bit patterns of the chaining state and gamma."""
+        M = np.zeros(32, np.uint8)
+        _load().oracle_digest_mask(_ptr(self.state), self.gamma, _ptr(M))
+        return M.tobytes()
 
     def frame_keystream(self, H: bytes, hgt: int, wid: int, C: int):
         """Advance the chain by one frame; return that frame's (D, B)."""
@@ -221,7 +235,7 @@ class Stream:
         E = np.zeros_like(F)
         H = np.zeros(32, np.uint8)
         _load().oracle_encrypt_frame(_ptr(self.state), self.gamma, self.h, self.n, _ptr(self.u),
-                                     _ptr(F), h, w, C, _ptr(E), _ptr(H), self.digest_mode)
+                                     _ptr(F), h, w, C, _ptr(E), _ptr(H), self.digest_mode, self.masked)
         return E, H.tobytes()
 
     def decrypt(self, E, H: bytes):
@@ -231,5 +245,5 @@ class Stream:
         Hb = _u8(np.frombuffer(bytes(H), dtype=np.uint8))
         F = np.zeros_like(E)
         _load().oracle_decrypt_frame(_ptr(self.state), self.gamma, self.h, self.n, _ptr(self.u),
-                                     _ptr(E), h, w, C, _ptr(Hb), _ptr(F))
+                                     _ptr(E), h, w, C, _ptr(Hb), _ptr(F), self.masked)
         return F

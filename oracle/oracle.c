@@ -450,14 +450,40 @@ void oracle_frame_keystream(double state[4], double gamma, double hstep, uint32_
     free(IR);
 }
 
-/* digest_mode 0: the paper's XOR fold; 1: the tree digest (not the paper's). */
+/* Digest transport: an option of this implementation.  Sec. V sends the
+ * SHA-256 hashes encrypted over the public channel but gives no mechanism.
+ * Masked transport sends H xor M, with
+ *   M = SHA-256("FHDMASK1" || LE64(x) || LE64(y) || LE64(z) || LE64(w) || LE64(gamma)),
+ * the bit patterns of the stream's chaining state before the frame (the key's
+ * x0..w0 for the first frame) and its gamma: 48 bytes, one SHA-256 block.  The
+ * receiver holds the same state and recovers H = (H xor M) xor M.  A hash and
+ * not further RK4 steps of the state: those would coincide with the previous
+ * frame's last worker chain, which seeds from the same iterate. */
+void oracle_digest_mask(const double state[4], double gamma, uint8_t M[32]) {
+    uint8_t msg[48];
+    memcpy(msg, "FHDMASK1", 8);
+    const double v[5] = {state[0], state[1], state[2], state[3], gamma};
+    for (int m = 0; m < 5; ++m) {
+        uint64_t bits;
+        memcpy(&bits, &v[m], 8);
+        for (int i = 0; i < 8; ++i) msg[8 + 8 * m + i] = (uint8_t)(bits >> (8 * i));
+    }
+    oracle_sha256(msg, 48, M);
+}
+
+/* digest_mode 0: the paper's XOR fold; 1: the tree digest (not the paper's).
+ * masked != 0: H_out is the transmitted digest H xor M (see oracle_digest_mask);
+ * the keystream is still derived from H itself. */
 void oracle_encrypt_frame(double state[4], double gamma, double hstep, uint32_t n,
                           const uint32_t u[4], const uint8_t *F, uint32_t h, uint32_t w,
-                          uint32_t C, uint8_t *E, uint8_t H[32], uint32_t digest_mode) {
+                          uint32_t C, uint8_t *E, uint8_t H_out[32], uint32_t digest_mode, uint32_t masked) {
     uint64_t N = (uint64_t)h * w * C;
     uint64_t LD = (uint64_t)C * (h + w);
+    uint8_t H[32], M[32];
     if (digest_mode == 1) oracle_frame_digest_tree(F, N, n, H);
     else oracle_frame_digest(F, N, n, H);
+    if (masked) oracle_digest_mask(state, gamma, M);
+    for (int i = 0; i < 32; ++i) H_out[i] = masked ? (uint8_t)(H[i] ^ M[i]) : H[i];
     uint16_t *D = (uint16_t *)malloc(sizeof(uint16_t) * (LD ? LD : 1));
     uint8_t *B = (uint8_t *)malloc(N ? N : 1);
     oracle_frame_keystream(state, gamma, hstep, n, u, H, h, w, C, D, B);
@@ -466,11 +492,15 @@ void oracle_encrypt_frame(double state[4], double gamma, double hstep, uint32_t 
     free(B);
 }
 
+/* masked != 0: H_in is the transmitted digest H xor M. */
 void oracle_decrypt_frame(double state[4], double gamma, double hstep, uint32_t n,
                           const uint32_t u[4], const uint8_t *E, uint32_t h, uint32_t w,
-                          uint32_t C, const uint8_t H[32], uint8_t *F) {
+                          uint32_t C, const uint8_t H_in[32], uint8_t *F, uint32_t masked) {
     uint64_t N = (uint64_t)h * w * C;
     uint64_t LD = (uint64_t)C * (h + w);
+    uint8_t H[32], M[32];
+    if (masked) oracle_digest_mask(state, gamma, M);
+    for (int i = 0; i < 32; ++i) H[i] = masked ? (uint8_t)(H_in[i] ^ M[i]) : H_in[i];
     uint16_t *D = (uint16_t *)malloc(sizeof(uint16_t) * (LD ? LD : 1));
     uint8_t *B = (uint8_t *)malloc(N ? N : 1);
     oracle_frame_keystream(state, gamma, hstep, n, u, H, h, w, C, D, B);
