@@ -772,17 +772,18 @@ def run_n_sweep(rank, fhd, torch, ns=(32, 128, 512), steps=3):
 
 
 def run_digest_modes(rank, fhd, torch, reps=10, steps=3):
-    """The frame digest in the paper's XOR-fold mode and in the tree mode (SHA-256 of the concatenated
-    sub-frame digests, an option of this library): the digest stage alone on the 30-frame 1080p clip, and the
-    clip's round trip (one CUDA stream, as the n sweep) in each mode; frame 0's digests checked against the
-    oracle."""
+    """The frame digest and its transport.  Modes: the paper's XOR fold sent as computed; the tree digest
+    (SHA-256 of the concatenated sub-frame digests); the fold sent masked (H xor M, M from the chaining
+    state; both options of this library).  Per mode: the digest stage alone on the 30-frame 1080p clip, the
+    clip's round trip on one CUDA stream (as the n sweep) with its LHCS_m time, the receiver-side check, and
+    frame 0's digests against the oracle."""
     import oracle
     dev = torch.device("cuda", torch.cuda.current_device())
     clip_np = si.clip(FRAMES, HGT, WID, CH, seed=rank + 5)
     clip = torch.from_numpy(clip_np).to(dev)
     flat = clip.reshape(-1)
     res, ok = {}, True
-    for mode in ("xor", "tree"):
+    for name, mode, transport in (("xor", "xor", "plain"), ("tree", "tree", "plain"), ("xor_masked", "xor", "masked")):
         dig = fhd.fhd_frame_digest(flat, n=N_WORKERS, count=FRAMES, mode=mode)
         torch.cuda.synchronize()
         ok = ok and bytes(dig[0].cpu().numpy()) == oracle.frame_digest(clip_np[0], N_WORKERS, mode)
@@ -794,8 +795,8 @@ def run_digest_modes(rank, fhd, torch, reps=10, steps=3):
         b.synchronize()
         digest_ms = a.elapsed_time(b) / reps
         key = si.key(900 + rank)
-        enc = fhd.Cipher(key, n_workers=N_WORKERS, digest_mode=mode)
-        dec = fhd.Cipher(key, n_workers=N_WORKERS, digest_mode=mode)
+        enc = fhd.Cipher(key, n_workers=N_WORKERS, digest_mode=mode, digest_transport=transport)
+        dec = fhd.Cipher(key, n_workers=N_WORKERS, digest_mode=mode, digest_transport=transport)
         sid, rid = enc.open_stream(), dec.open_stream()
         E, R = torch.empty_like(clip), torch.empty_like(clip)
         H = torch.empty((FRAMES, 32), dtype=torch.uint8, device=dev)
@@ -803,6 +804,17 @@ def run_digest_modes(rank, fhd, torch, reps=10, steps=3):
         di = [(rid, E[t], R[t], H[t]) for t in range(FRAMES)]
         enc.encrypt_frames(ei); dec.decrypt_frames(di)
         torch.cuda.synchronize()
+        if transport == "masked":   # frame 0 of the first clip: the transmitted digest against the oracle
+            ref = oracle.Stream.from_key(key, digest_mode=mode, transport=transport)
+            enc2 = fhd.Cipher(key, n_workers=N_WORKERS, digest_mode=mode, digest_transport=transport)
+            H0 = torch.empty(32, dtype=torch.uint8, device=dev)
+            E0 = torch.empty_like(clip[0])
+            enc2.encrypt_frames([(enc2.open_stream(), clip[0], E0, H0)])
+            torch.cuda.synchronize()
+            ok = ok and bytes(H0.cpu().numpy()) == ref.encrypt(clip_np[0])[1]
+            enc2.close()
+        enc.profile(True)
+        dec.profile(True)
         a.record()
         for _ in range(steps):
             enc.encrypt_frames(ei)
@@ -810,12 +822,16 @@ def run_digest_modes(rank, fhd, torch, reps=10, steps=3):
         b.record()
         b.synchronize()
         ms = a.elapsed_time(b) / steps
+        prof = [c.profile_read() for c in (enc, dec)]
+        enc.profile(False)
+        dec.profile(False)
         verified = dec.verify_frames(di)
-        res[mode] = {"digest_ms_per_clip": digest_ms, "round_trip_frames_per_s": FRAMES / (ms / 1000.0),
+        res[name] = {"digest_ms_per_clip": digest_ms, "round_trip_frames_per_s": FRAMES / (ms / 1000.0),
+                     "lhcs_m_ms_per_clip_each_side": sum(p["master"][0] for p in prof) / (2 * steps),
                      "round_trip_ok": bool(torch.equal(R, clip)), "verify_ok": bool(int(verified.min()) == 1)}
         enc.close(); dec.close()
     return {"workload": "30 x 1080p clip: the digest stage alone (n = 32), and the round trip on one CUDA stream",
-            **res, "frame0_digests_match_oracle": bool(ok)}
+            **res, "digests_match_oracle": bool(ok)}
 
 
 def run_stress(rank, fhd, torch, frames=256):

@@ -65,6 +65,7 @@ typedef struct {
     double rk4_h;        /* step of the RK4 integration of Eq. (1); default 0.001 */
     uint32_t u_bound[4]; /* reconstruction upper bounds u_x, u_y, u_z, u_w; default 20, 20, 40, 20 */
     uint32_t digest_mode; /* how H is formed from the n sub-frame digests h_i: FHD_DIGEST_XOR (0, default) */
+    uint32_t digest_transport; /* how H travels: FHD_TRANSPORT_PLAIN (0, default) or FHD_TRANSPORT_MASKED */
 } fhd_params;
 
 /* Digest modes.  FHD_DIGEST_XOR: H = h_1 xor ... xor h_n (Sec. II-A, Algorithm 1).  FHD_DIGEST_TREE, an
@@ -73,6 +74,17 @@ typedef struct {
  * counts.  Same partition and sub-frame digests either way; both ends of a channel must use the same
  * mode (it decides the H the sender transmits and the receiver's integrity check). */
 enum { FHD_DIGEST_XOR = 0, FHD_DIGEST_TREE = 1 };
+
+/* Digest transport.  Sec. V sends the frames' hashes encrypted over the public channel but gives no
+ * mechanism.  FHD_TRANSPORT_PLAIN: frames[i].digest holds H as computed.  FHD_TRANSPORT_MASKED, an option of
+ * this library: encryption writes H xor M to frames[i].digest, with
+ *   M = SHA-256("FHDMASK1" || LE64(x) || LE64(y) || LE64(z) || LE64(w) || LE64(gamma)),
+ * the bit patterns of the stream's chaining state before the frame (the key's x0..w0 for the first
+ * frame), so each frame has its own mask; the keystream still derives from H.  Decryption reads H xor M,
+ * unmasks it with its own chaining state and leaves H in frames[i].digest (so cipher_verify_frames can
+ * follow).  The masked digest is written by LHCS_m: encrypt_frames_split then records digests_done after
+ * LHCS_m, not after the digest stage.  Both ends must use the same transport. */
+enum { FHD_TRANSPORT_PLAIN = 0, FHD_TRANSPORT_MASKED = 1 };
 
 /* One frame of a batch.  `digest` is written by encrypt_frames (the 32-byte
  * H the receiver needs, Sec. V) and read by decrypt_frames. */

@@ -51,12 +51,15 @@ class FhdError(RuntimeError):
 
 class FhdParams(ctypes.Structure):
     _fields_ = [("n_workers", ctypes.c_uint32), ("rk4_h", ctypes.c_double), ("u_bound", ctypes.c_uint32 * 4),
-                ("digest_mode", ctypes.c_uint32)]
+                ("digest_mode", ctypes.c_uint32), ("digest_transport", ctypes.c_uint32)]
 
 
 # How the frame digest H is formed from the n sub-frame digests: "xor" is the paper's fold (Sec. II-A),
 # "tree" (an option of this library) is SHA-256 of the sub-frame digests concatenated in order.
 DIGEST_MODES = {"xor": 0, "tree": 1}
+# How the digest travels: "plain" as computed, or "masked" (an option of this library) as H xor M with M
+# derived from the stream's chaining state; the receiver unmasks it in place.
+TRANSPORTS = {"plain": 0, "masked": 1}
 
 
 class FhdFrame(ctypes.Structure):
@@ -155,13 +158,14 @@ def _stream_ptr(stream) -> ctypes.c_void_p:
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _params(n_workers=32, rk4_h=0.001, u_bound=(20, 20, 40, 20), digest_mode="xor") -> FhdParams:
+def _params(n_workers=32, rk4_h=0.001, u_bound=(20, 20, 40, 20), digest_mode="xor", transport="plain") -> FhdParams:
     p = FhdParams()
     p.n_workers = n_workers
     p.rk4_h = rk4_h
     for m in range(4):
         p.u_bound[m] = u_bound[m]
     p.digest_mode = DIGEST_MODES[digest_mode]
+    p.digest_transport = TRANSPORTS[transport]
     return p
 
 
@@ -183,10 +187,12 @@ class Cipher:
     """A cipher handle: key, protocol parameters and device-resident streams."""
 
     def __init__(self, key: bytes | None = None, ic: Sequence[float] | None = None, n_workers: int = 32,
-                 rk4_h: float = 0.001, u_bound=(20, 20, 40, 20), digest_mode: str = "xor"):
+                 rk4_h: float = 0.001, u_bound=(20, 20, 40, 20), digest_mode: str = "xor",
+                 digest_transport: str = "plain"):
         lib = load()
-        self.params = _params(n_workers, rk4_h, u_bound, digest_mode)
+        self.params = _params(n_workers, rk4_h, u_bound, digest_mode, digest_transport)
         self.digest_mode = digest_mode
+        self.digest_transport = digest_transport
         self.n_workers = n_workers
         h = ctypes.c_void_p()
         if ic is not None:

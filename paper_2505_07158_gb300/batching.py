@@ -56,7 +56,8 @@ def mixed_batch(shapes: Sequence[tuple], keys: Sequence[bytes], cipher: "_lib.Ci
                 device=None):
     """Open one stream per frame (own key) and allocate outputs: -> (enc_items, dec_items, decrypt cipher)."""
     device = device or torch.device("cuda", torch.cuda.current_device())
-    dec = _lib.Cipher(keys[0], n_workers=cipher.n_workers, digest_mode=cipher.digest_mode)
+    dec = _lib.Cipher(keys[0], n_workers=cipher.n_workers, digest_mode=cipher.digest_mode,
+                      digest_transport=cipher.digest_transport)
     enc_items, dec_items = [], []
     for shape, key, F in zip(shapes, keys, frames):
         sid = cipher.open_stream(key)

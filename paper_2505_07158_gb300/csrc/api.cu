@@ -46,6 +46,7 @@ struct fhd_cipher {
     bool partition = false;
     int layout = FHD_LAYOUT_LATENCY;
     uint32_t digest_mode = FHD_DIGEST_XOR;
+    uint32_t transport = FHD_TRANSPORT_PLAIN;
     cudaStream_t last_stream = nullptr;
     std::string err;
     bool prof = false;
@@ -428,6 +429,8 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
         b.count = m;
         b.n = c->n;
         b.digest_mode = c->digest_mode;
+        b.digest_masked = c->transport == FHD_TRANSPORT_MASKED;
+        b.encrypt = encrypt;
         b.hstep = c->h;
         b.hhalf = c->h / 2.0;
         b.hsixth = c->h / 6.0;
@@ -504,7 +507,8 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
                                                              : fhd::launch_fold_batch(b, sb);
                  })) != cudaSuccess)
                 return cuda_fail(c, e, "sha launch");
-            if (digests_done && base + m >= count && (e = cudaEventRecord(digests_done, sb)) != cudaSuccess)
+            if (digests_done && !b.digest_masked && base + m >= count &&
+                (e = cudaEventRecord(digests_done, sb)) != cudaSuccess)
                 return cuda_fail(c, e, "record digest event");
         }
         // LHCS_m of this group of frames after the bulk stream's work so far: this group's digests,
@@ -519,6 +523,10 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
             return cuda_fail(c, e, "master launch");
         if (master_done && base + m >= count && (e = cudaEventRecord(master_done, sc)) != cudaSuccess)
             return cuda_fail(c, e, "record master event");
+        // With the masked transport the transmitted digests (H xor M) are written by LHCS_m.
+        if (encrypt && digests_done && b.digest_masked && base + m >= count &&
+            (e = cudaEventRecord(digests_done, sc)) != cudaSuccess)
+            return cuda_fail(c, e, "record digest event");
         if (part && ((e = cudaEventRecord(ev[2], sc)) != cudaSuccess || (e = cudaStreamWaitEvent(sb, ev[2], 0)) != cudaSuccess))
             return cuda_fail(c, e, "master to bulk stream");
         if (base == 0)   // caller's gate of the workers (e.g. how many batches' workers share the FP64 pipes)
@@ -548,38 +556,49 @@ extern "C" {
 
 const char *fhd_version(void) { return "fhdcipher 0.1 (sm_103a)"; }
 
-// The digest mode of `params` (FHD_DIGEST_XOR when params is NULL).
-bool resolve_digest_mode(const fhd_params *p, uint32_t &mode, std::string &why) {
+// The digest mode and transport of `params` (the paper's fold, sent as computed, when params is NULL).
+bool resolve_digest_mode(const fhd_params *p, uint32_t &mode, uint32_t &transport, std::string &why) {
     mode = p ? p->digest_mode : (uint32_t)FHD_DIGEST_XOR;
+    transport = p ? p->digest_transport : (uint32_t)FHD_TRANSPORT_PLAIN;
     if (mode != FHD_DIGEST_XOR && mode != FHD_DIGEST_TREE) { why = "unknown digest_mode"; return false; }
+    if (transport != FHD_TRANSPORT_PLAIN && transport != FHD_TRANSPORT_MASKED) {
+        why = "unknown digest_transport";
+        return false;
+    }
     return true;
 }
 
 int cipher_init(const uint8_t key[32], const fhd_params *params, fhd_cipher **out) {
     if (!key || !out) return fail(nullptr, FHD_ERR_INVALID_ARG, "null argument");
-    uint32_t n, u[4], mode;
+    uint32_t n, u[4], mode, transport;
     double h;
     std::string why;
-    if (!resolve_params(params, n, h, u, why) || !resolve_digest_mode(params, mode, why))
+    if (!resolve_params(params, n, h, u, why) || !resolve_digest_mode(params, mode, transport, why))
         return fail(nullptr, FHD_ERR_INVALID_ARG, why);
     double ic[5];
     key_to_ic(key, u, ic);
     int rc = init_common(ic, n, h, u, out);
-    if (rc == FHD_OK) (*out)->digest_mode = mode;
+    if (rc == FHD_OK) {
+        (*out)->digest_mode = mode;
+        (*out)->transport = transport;
+    }
     return rc;
 }
 
 int cipher_init_raw(double x0, double y0, double z0, double w0, double gamma, const fhd_params *params,
                     fhd_cipher **out) {
     if (!out) return fail(nullptr, FHD_ERR_INVALID_ARG, "null argument");
-    uint32_t n, u[4], mode;
+    uint32_t n, u[4], mode, transport;
     double h;
     std::string why;
-    if (!resolve_params(params, n, h, u, why) || !resolve_digest_mode(params, mode, why))
+    if (!resolve_params(params, n, h, u, why) || !resolve_digest_mode(params, mode, transport, why))
         return fail(nullptr, FHD_ERR_INVALID_ARG, why);
     const double ic[5] = {x0, y0, z0, w0, gamma};
     int rc = init_common(ic, n, h, u, out);
-    if (rc == FHD_OK) (*out)->digest_mode = mode;
+    if (rc == FHD_OK) {
+        (*out)->digest_mode = mode;
+        (*out)->transport = transport;
+    }
     return rc;
 }
 

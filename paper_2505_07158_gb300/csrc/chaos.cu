@@ -36,6 +36,7 @@
 // 2 k is exact, so it equals the separate doubling and add whenever 2 k is
 // finite (an overflowing 2 k makes the definition's state non-finite anyway).
 #include "common.cuh"
+#include "sha256_core.cuh"
 
 namespace fhd {
 namespace {
@@ -193,6 +194,32 @@ __device__ void master_frame(double &s, int lane, const LaneRole &role, const ui
     }
 }
 
+// Mask of the transmitted digest (masked transport, an option of this library; Sec. V sends the hashes
+// encrypted without giving the mechanism): M = SHA-256("FHDMASK1" || LE64(x) || LE64(y) || LE64(z) ||
+// LE64(w) || LE64(gamma)) of the chaining state before the frame, 48 bytes in one block.  M is returned as
+// the 8 little-endian words of its big-endian byte string, ready to XOR with the stored digest words.
+__device__ void digest_mask(double x, double y, double z, double w, double gamma, uint32_t M[8]) {
+    uint32_t wd[16];
+    wd[0] = 0x4648444Du;   // "FHDM"
+    wd[1] = 0x41534B31u;   // "ASK1"
+    const double v[5] = {x, y, z, w, gamma};
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(v[m]);
+        wd[2 + 2 * m] = __byte_perm((uint32_t)bits, 0, 0x0123);           // bytes 0..3, big-endian word
+        wd[3 + 2 * m] = __byte_perm((uint32_t)(bits >> 32), 0, 0x0123);   // bytes 4..7
+    }
+    wd[12] = 0x80000000u;
+    wd[13] = 0u;
+    wd[14] = 0u;
+    wd[15] = 48u * 8u;
+    uint32_t h[8];
+    sha256_init(h);
+    sha256_compress(h, wd);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) M[q] = __byte_perm(h[q], 0, 0x0123);
+}
+
 // K2a: one warp per stream of the batch; the stream's frames in call order.
 __global__ void __launch_bounds__(32) master_kernel(const __grid_constant__ Batch b, StreamState *states,
                                                     unsigned *status) {
@@ -212,6 +239,30 @@ __global__ void __launch_bounds__(32) master_kernel(const __grid_constant__ Batc
         if (lane < 8)   // the frame's digest: folded by the digest stage, or the transmitted one
             reinterpret_cast<uint32_t *>(H)[lane] = reinterpret_cast<const uint32_t *>(fd.digest)[lane];
         __syncwarp();
+        if (b.digest_masked) {
+            // Lanes 0..3 hold the chaining state before this frame.  Encryption transmits H xor M (the
+            // keystream still derives from H); decryption unmasks the transmitted digest and leaves H in
+            // the frame's digest for the receiver-side check.
+            const double x = __shfl_sync(0xffffffffu, s, 0), y = __shfl_sync(0xffffffffu, s, 1);
+            const double z = __shfl_sync(0xffffffffu, s, 2), w = __shfl_sync(0xffffffffu, s, 3);
+            if (lane == 0) {
+                uint32_t M[8];
+                digest_mask(x, y, z, w, gamma, M);
+                uint32_t *hw = reinterpret_cast<uint32_t *>(H);
+                uint32_t *dg = reinterpret_cast<uint32_t *>(fd.digest);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const uint32_t t = hw[q] ^ M[q];
+                    if (b.encrypt) {
+                        dg[q] = t;
+                    } else {
+                        hw[q] = t;
+                        dg[q] = t;
+                    }
+                }
+            }
+            __syncwarp();
+        }
         master_frame(s, lane, role, H, b.u, b.n, c, fd.IR);
         __syncwarp();
     }

@@ -38,6 +38,8 @@ struct Batch {
     uint32_t perm_ctas;       // total column-pass CTAs
     uint32_t row_ctas;        // total row-pass CTAs
     uint32_t digest_mode;     // FHD_DIGEST_XOR (the paper's fold) or FHD_DIGEST_TREE
+    uint32_t digest_masked;   // transmitted digest is H xor M (FHD_TRANSPORT_MASKED)
+    uint32_t encrypt;         // 1: this batch encrypts (LHCS_m masks the digest), 0: decrypts (unmasks)
     double hstep, hhalf, hsixth;   // RK4 step h, h/2 and h/6 (rounded once, on the host)
     uint32_t u[4];            // reconstruction bounds
     uint16_t order[kMaxBatch];          // frame indices grouped by stream, in call order

@@ -18,19 +18,12 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "sha256_core.cuh"
 
 namespace fhd {
 namespace {
 
-__constant__ uint32_t kK[64] = {
-    0x428a2f98u, 0x71374491u, 0xb5c0fbcfu, 0xe9b5dba5u, 0x3956c25bu, 0x59f111f1u, 0x923f82a4u, 0xab1c5ed5u,
-    0xd807aa98u, 0x12835b01u, 0x243185beu, 0x550c7dc3u, 0x72be5d74u, 0x80deb1feu, 0x9bdc06a7u, 0xc19bf174u,
-    0xe49b69c1u, 0xefbe4786u, 0x0fc19dc6u, 0x240ca1ccu, 0x2de92c6fu, 0x4a7484aau, 0x5cb0a9dcu, 0x76f988dau,
-    0x983e5152u, 0xa831c66du, 0xb00327c8u, 0xbf597fc7u, 0xc6e00bf3u, 0xd5a79147u, 0x06ca6351u, 0x14292967u,
-    0x27b70a85u, 0x2e1b2138u, 0x4d2c6dfcu, 0x53380d13u, 0x650a7354u, 0x766a0abbu, 0x81c2c92eu, 0x92722c85u,
-    0xa2bfe8a1u, 0xa81a664bu, 0xc24b8b70u, 0xc76c51a3u, 0xd192e819u, 0xd6990624u, 0xf40e3585u, 0x106aa070u,
-    0x19a4c116u, 0x1e376c08u, 0x2748774cu, 0x34b0bcb5u, 0x391c0cb3u, 0x4ed8aa4au, 0x5b9cca4fu, 0x682e6ff3u,
-    0x748f82eeu, 0x78a5636fu, 0x84c87814u, 0x8cc70208u, 0x90befffau, 0xa4506cebu, 0xbef9a3f7u, 0xc67178f2u};
+
 
 __device__ __forceinline__ uint32_t rotr(uint32_t x, int n) { return __funnelshift_r(x, x, n); }
 __device__ __forceinline__ uint32_t bswap(uint32_t x) { return __byte_perm(x, 0, 0x0123); }
@@ -176,7 +169,7 @@ __device__ void sha_pipeline(Locate locate, uint32_t nmsg) {
                         wt = w[t & 15] + s0 + w[(t - 7) & 15] + s1;
                         w[t & 15] = wt;
                     }
-                    dst[t][lane] = wt + kK[t];
+                    dst[t][lane] = wt + kSha256K[t];
                 }
             }
             named_barrier_64();                 // block b is ready; block b-1 has been consumed
@@ -268,22 +261,6 @@ __global__ void __launch_bounds__(64) sha_dst_kernel(const __grid_constant__ Bat
         b.count * n);
 }
 
-// One SHA-256 compression (FIPS 180-4 Sec. 6.2.2) of the 16 message words w into h; one thread.
-__device__ __forceinline__ void compress_block(uint32_t h[8], uint32_t w[16]) {
-    uint32_t a = h[0], bb = h[1], c = h[2], d = h[3], e = h[4], f = h[5], g = h[6], hh = h[7];
-#pragma unroll
-    for (int t = 0; t < 64; ++t) {
-        if (t >= 16) {
-            const uint32_t x = w[(t - 15) & 15], y = w[(t - 2) & 15];
-            w[t & 15] += (rotr(x, 7) ^ rotr(x, 18) ^ (x >> 3)) + w[(t - 7) & 15] + (rotr(y, 17) ^ rotr(y, 19) ^ (y >> 10));
-        }
-        const uint32_t t1 = hh + (rotr(e, 6) ^ rotr(e, 11) ^ rotr(e, 25)) + ((e & f) ^ (~e & g)) + kK[t] + w[t & 15];
-        const uint32_t t2 = (rotr(a, 2) ^ rotr(a, 13) ^ rotr(a, 22)) + ((a & bb) ^ (a & c) ^ (bb & c));
-        hh = g; g = f; f = e; e = d + t1; d = c; c = bb; bb = a; a = t1 + t2;
-    }
-    h[0] += a; h[1] += bb; h[2] += c; h[3] += d; h[4] += e; h[5] += f; h[6] += g; h[7] += hh;
-}
-
 // Tree digest (an option of this library, not of the paper): SHA-256 of the n sub-frame digests at `part`
 // concatenated in order, 32 n bytes; one thread.  The stored digests are big-endian bytes, so each message
 // word is the byte swap of a stored 32-bit word.  32 n bytes end on a half or a whole 64-byte block: the
@@ -298,7 +275,7 @@ __device__ void tree_digest(const uint8_t *part, uint32_t n, uint32_t h[8]) {
     for (; i + 16 <= words; i += 16) {
 #pragma unroll
         for (int k = 0; k < 16; ++k) w[k] = bswap(p[i + k]);
-        compress_block(st.h, w);
+        sha256_compress(st.h, w);
     }
     const uint32_t rem = words - i;   // 0 or 8
 #pragma unroll
@@ -307,7 +284,7 @@ __device__ void tree_digest(const uint8_t *part, uint32_t n, uint32_t h[8]) {
     const uint64_t bits = 256ull * n;
     w[14] = (uint32_t)(bits >> 32);
     w[15] = (uint32_t)bits;
-    compress_block(st.h, w);
+    sha256_compress(st.h, w);
 #pragma unroll
     for (int k = 0; k < 8; ++k) h[k] = st.h[k];
 }
