@@ -5,8 +5,8 @@ P pixel columns held in shared memory.  Wide strips amortise the per-row gather
 overhead; narrow strips let two or more CTAs share an SM and hide memory
 latency.  The best P depends on the frame shape, so it is measured: for each
 (height, width, channels) every power-of-two P whose strip fits shared memory
-is timed (encrypt + decrypt of one frame, CUDA events, median of several
-runs), the fastest is installed in the library with ``fhd_set_strip_width``
+is timed (encrypt + decrypt per frame of a batch of up to 30 frames, CUDA
+events, median of several runs), the fastest is installed in the library with ``fhd_set_strip_width``
 and remembered in a JSON cache keyed by the GPU name.
 
 The chosen P only changes the schedule: outputs are bit-identical for every P
@@ -101,8 +101,16 @@ def time_shape(h: int, w: int, C: int, P: int, reps: int = 3, frames: int = 8) -
         dec.close()
 
 
+def batch_frames(h: int, w: int, C: int) -> int:
+    """Frames per timed batch: a 30-frame clip where it fits in about 1.5 GB, so that the wave count per
+    launch, which decides the best strip width, is the one of a clip's launch (timing 8 frames picked 64 at
+    1080p, where 16 is the fastest for 30 frames)."""
+    return max(4, min(30, int(1.5e9 // (h * w * C))))
+
+
 def tune_shape(h: int, w: int, C: int, reps: int = 7) -> tuple[int, dict]:
-    times = {P: time_shape(h, w, C, P, reps) for P in candidates(h, w, C)}
+    n = batch_frames(h, w, C)
+    times = {P: time_shape(h, w, C, P, reps, frames=n) for P in candidates(h, w, C)}
     best = min(times, key=times.get)
     return best, times
 
