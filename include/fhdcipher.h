@@ -144,7 +144,8 @@ int decrypt_frames_ex(fhd_cipher *c, uint32_t count, const fhd_frame *frames, vo
 /* Sender side with an early digest event: as encrypt_frames_ex, and
  * `digests_done` (may be NULL) is recorded on `stream` once every frame's
  * digest H (Algorithm 1: the XOR fold of the sub-frame digests) is in
- * frames[i].digest, before LHCS_m runs.  A receiver on the same device can
+ * frames[i].digest, before LHCS_m runs (after it with FHD_TRANSPORT_MASKED,
+ * whose transmitted digest LHCS_m writes).  A receiver on the same device can
  * wait on it to start its own chaotic stage while the sender's keystream and
  * permutation are still running.  For more than 128 frames it is recorded
  * after the digests of the last group of 128.  `keystream_done` (may be
@@ -183,7 +184,9 @@ int decrypt_frames_split(fhd_cipher *c, uint32_t count, const fhd_frame *frames,
  *   data_events    gate the first kernel that reads frames[i].src after the
  *                  digest stage (the permutation);
  *   digests_done   recorded once every digest H is in frames[i].digest, before
- *                  LHCS_m (encryption only: decryption reads the digests);
+ *                  LHCS_m (after it with FHD_TRANSPORT_MASKED, whose transmitted
+ *                  digest LHCS_m writes; encryption only: decryption reads the
+ *                  digests);
  *   master_done    recorded right after LHCS_m;
  *   keystream_done recorded right after the last worker kernel, before the
  *                  permutation.
