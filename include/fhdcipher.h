@@ -191,7 +191,12 @@ int decrypt_frames_split(fhd_cipher *c, uint32_t count, const fhd_frame *frames,
  *   keystream_done recorded right after the last worker kernel, before the
  *                  permutation.
  * All hooks apply to the first group of 128 frames of the call, the output
- * events to the last; groups of one call run in order. */
+ * events to the last; groups of one call run in order.  A pipeline that keeps
+ * many CUDA streams busy (clips in flight, serving lanes, and with the SM
+ * partition two internal streams per caller stream) should run with
+ * CUDA_DEVICE_MAX_CONNECTIONS=32, set before CUDA starts: with the default 8
+ * hardware queues, a stream held by an event wait stalls the streams that share
+ * its queue. */
 typedef struct {
     void *const *key_waits;
     uint32_t n_key_waits;
