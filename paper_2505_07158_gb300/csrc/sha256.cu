@@ -23,17 +23,12 @@
 namespace fhd {
 namespace {
 
-
-
 __device__ __forceinline__ uint32_t rotr(uint32_t x, int n) { return __funnelshift_r(x, x, n); }
 __device__ __forceinline__ uint32_t bswap(uint32_t x) { return __byte_perm(x, 0, 0x0123); }
 
 struct ShaState {
     uint32_t h[8];
-    __device__ __forceinline__ void init() {
-        h[0] = 0x6a09e667u; h[1] = 0xbb67ae85u; h[2] = 0x3c6ef372u; h[3] = 0xa54ff53au;
-        h[4] = 0x510e527fu; h[5] = 0x9b05688cu; h[6] = 0x1f83d9abu; h[7] = 0x5be0cd19u;
-    }
+    __device__ __forceinline__ void init() { sha256_init(h); }
 };
 
 __device__ __forceinline__ void block_words(const uint4 q[4], uint32_t w[16]) {
