@@ -199,6 +199,49 @@ def test_worker_gate_holds_only_the_workers():
     assert fhd._lib.load().encrypt_frames_sched(c._handle(), n, arr, None, ctypes.byref(hk)) == fhd.FHD_ERR_INVALID_ARG
 
 
+def test_worker_gate_on_the_receiver_and_a_null_schedule():
+    """The worker gate on decrypt_frames holds the receiver's workers behind an event (its LHCS_m runs
+    first); encrypt_frames_sched / decrypt_frames_sched with a NULL schedule behave as the plain calls."""
+    key = si.key(660)
+    F = to_dev(si.gradient_frame(72, 96, 3, t=0, seed=661))
+    snd, rcv = fhd.Cipher(key), fhd.Cipher(key)
+    sid, rid = snd.open_stream(), rcv.open_stream()
+    E, R = torch.empty_like(F), torch.empty_like(F)
+    H = torch.empty(32, dtype=torch.uint8, device=dev())
+    snd.encrypt_frames([(sid, F, E, H)])
+    torch.cuda.synchronize()
+    other, s = torch.cuda.Stream(), torch.cuda.Stream()
+    origin, gate = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rcv.profile(True)
+    origin.record(s)
+    other.wait_event(origin)
+    with torch.cuda.stream(other):
+        torch.cuda._sleep(20_000_000)
+        gate.record(other)
+    rcv.decrypt_frames([(rid, E, R, H)], stream=s, master_event=torch.cuda.Event(), worker_wait_events=[gate])
+    torch.cuda.synchronize()
+    spans = {k: (a, b) for k, a, b in rcv.profile_spans(origin)}
+    rcv.profile(False)
+    gate_ms = origin.elapsed_time(gate)
+    assert spans["master"][1] < gate_ms <= spans["keystream"][0] + 1e-3
+    assert torch.equal(R, F)
+    # NULL schedule through the C ABI: the next frame of both streams, checked against the oracle
+    lib = fhd._lib.load()
+    F2 = to_dev(si.gradient_frame(72, 96, 3, t=1, seed=661))
+    E2, R2 = torch.empty_like(F2), torch.empty_like(F2)
+    H2 = torch.empty(32, dtype=torch.uint8, device=dev())
+    arr, n = snd._frames([(sid, F2, E2, H2)])
+    assert lib.encrypt_frames_sched(snd._handle(), n, arr, None, None) == fhd.FHD_OK
+    arr, n = rcv._frames([(rid, E2, R2, H2)])
+    assert lib.decrypt_frames_sched(rcv._handle(), n, arr, None, None) == fhd.FHD_OK
+    torch.cuda.synchronize()
+    ref = oracle.Stream.from_key(key)
+    ref.encrypt(host(F))
+    E_ref, H_ref = ref.encrypt(host(F2))
+    assert np.array_equal(host(E2), E_ref) and bytes(host(H2)) == H_ref
+    assert torch.equal(R2, F2)
+
+
 def test_launch_count_per_call():
     """fhd_launch_count counts every kernel: digest (SHA + fold), LHCS_m, workers, and the two
     permutation passes on encryption; LHCS_m, workers and the two passes on decryption."""
