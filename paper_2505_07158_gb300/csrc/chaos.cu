@@ -136,13 +136,18 @@ __device__ __forceinline__ LaneRole8 lane_role8(int lane, double gamma) {
     return r;
 }
 
-__device__ __forceinline__ void rk4_step_lanes8(double &s, const LaneRole8 &r, const Rk4 &c) {
+// `after_fetch(s)` runs once the first stage's operands are fetched, with the state at the start of the
+// step: the worker kernel emits the previous step's stream bytes there, so that their integer work follows
+// the shuffles that start this step instead of delaying them.
+template <class F>
+__device__ __forceinline__ void rk4_step_lanes8(double &s, const LaneRole8 &r, const Rk4 &c, F &&after_fetch) {
     double tin = s, acc = 0.0;
 #pragma unroll
     for (int st = 0; st < 4; ++st) {
         const double a = __shfl_sync(0xffffffffu, tin, r.s1);
         const double b = __shfl_sync(0xffffffffu, tin, r.s2);
         const double d = __shfl_sync(0xffffffffu, tin, r.s3);
+        if (st == 0) after_fetch(tin);
         const double Pc = r.vx ? d : -0.0;
         const double Qb = r.vx ? 1.0 : d;
         const double P2 = r.vy ? tin : 0.0;
@@ -357,12 +362,16 @@ __global__ void __launch_bounds__(32) keystream_kernel(const __grid_constant__ B
             emit_bytes(s, active, 24 * t + 6 * v, need, ndb, half, Dbytes, Bp);
         }
     } else {
+        // The bytes of step t (the state after it) are emitted during step t + 1, and the last step's after
+        // the loop: the same bytes at the same positions.
         const LaneRole8 role = lane_role8(lane, fd.gamma);
         double s = chain_value;
         for (uint64_t t = 0; t < T; ++t) {
-            rk4_step_lanes8(s, role, c);
-            emit_bytes(s, active, 24 * t + 6 * v, need, ndb, half, Dbytes, Bp);
+            rk4_step_lanes8(s, role, c, [&](double prev) {
+                if (t) emit_bytes(prev, active, 24 * (t - 1) + 6 * v, need, ndb, half, Dbytes, Bp);
+            });
         }
+        if (T) emit_bytes(s, active, 24 * (T - 1) + 6 * v, need, ndb, half, Dbytes, Bp);
     }
 }
 
