@@ -112,10 +112,12 @@ __device__ __forceinline__ void rk4_step_lanes(double &s, const LaneRole &r, con
 // The same step with eight chains per warp (all 32 lanes carry variables, so
 // no lane holds a constant): three shuffles per stage, and the operands that
 // are a variable on some lanes and a constant on others are selected:
-//   v = x: p = fma(X, -1, Y), q = fma(W, 1, -0);  v = y: p = fma(X, rho, -0), p2 = fma(p, 1, -Y);
+//   v = x: p = fma(Y, 1, -X), q = fma(W, 1, -0);  v = y: p = fma(X, rho, -0), p2 = fma(p, 1, -Y);
 //   v = z: p = fma(Z, beta, -0), p2 = -p;          v = w: p = fma(W, gamma, -0);
-// q = X Z, X Y, Y Z for y, z, w.  Fewer binary64 instructions per chain step
-// (27 per eight chains), a longer step (selects after the shuffles).
+// q = X Z, X Y, Y Z for y, z, w.  The first fma's shuffled operand is a factor
+// on every lane and its addend a select on the lane's own value (-X or -0),
+// so no select sits between the shuffles and the first fma.  Fewer binary64
+// instructions per chain step (27 per eight chains), a longer step (selects).
 struct LaneRole8 {
     double Pb, B2, kS;
     int s1, s2, s3;
@@ -125,10 +127,10 @@ struct LaneRole8 {
 __device__ __forceinline__ LaneRole8 lane_role8(int lane, double gamma) {
     LaneRole8 r;
     const int v = lane & 3, base = lane & ~3;
-    r.Pb = v == 0 ? -1.0 : v == 1 ? kRho : v == 2 ? kBeta : gamma;
+    r.Pb = v == 0 ? 1.0 : v == 1 ? kRho : v == 2 ? kBeta : gamma;
     r.B2 = v == 0 ? kSigma : v == 2 ? -1.0 : 1.0;
     r.kS = (v == 0 || v == 2) ? 1.0 : -1.0;
-    r.s1 = base + (v == 1 ? 0 : v);                        // X, X, Z, W
+    r.s1 = base + (v == 0 ? 1 : v == 1 ? 0 : v);           // Y, X, Z, W
     r.s2 = base + (v == 0 ? 3 : v == 3 ? 1 : 0);           // W, X, X, Y
     r.s3 = base + ((v == 0 || v == 2) ? 1 : 2);            // Y, Z, Y, Z
     r.vx = v == 0;
@@ -148,10 +150,10 @@ __device__ __forceinline__ void rk4_step_lanes8(double &s, const LaneRole8 &r, c
         const double b = __shfl_sync(0xffffffffu, tin, r.s2);
         const double d = __shfl_sync(0xffffffffu, tin, r.s3);
         if (st == 0) after_fetch(tin);
-        const double Pc = r.vx ? d : -0.0;
+        const double Pc = r.vx ? tin : 0.0;
         const double Qb = r.vx ? 1.0 : d;
         const double P2 = r.vy ? tin : 0.0;
-        const double p = __fma_rn(a, r.Pb, Pc);
+        const double p = __fma_rn(a, r.Pb, -Pc);
         const double q = __fma_rn(b, Qb, -0.0);
         const double p2 = __fma_rn(p, r.B2, -P2);
         const double k = __fma_rn(q, r.kS, p2);
