@@ -78,3 +78,23 @@ def test_host_side_checks_of_the_stream_ordering_and_placement_calls(lib):
     assert lib.cipher_set_layout(None, 0) == fhd.FHD_ERR_INVALID_ARG
     assert lib.cipher_profile_spans(None, None, 0, None, None, None, ctypes.byref(n)) == fhd.FHD_ERR_INVALID_ARG
     assert b"null" in lib.cipher_last_error(None)
+
+
+def test_protocol_parameters_are_checked_before_any_device_work(lib):
+    """cipher_init / cipher_init_raw validate fhd_params (worker count, step, bounds, digest mode and
+    transport) before they select a device, so the errors are the same with and without a GPU."""
+    import paper_2505_07158_gb300 as fhd
+    from paper_2505_07158_gb300 import _lib
+    h = ctypes.c_void_p()
+    bad = []
+    p = _lib._params(); p.digest_mode = 7; bad.append((p, b"digest_mode"))
+    p = _lib._params(); p.digest_transport = 3; bad.append((p, b"digest_transport"))
+    p = _lib._params(n_workers=4096); bad.append((p, b"n_workers"))
+    p = _lib._params(rk4_h=2.0); bad.append((p, b"rk4_h"))
+    p = _lib._params(u_bound=(20, 20, 70000, 20)); bad.append((p, b"u_bound"))
+    for params, word in bad:
+        assert lib.cipher_init(bytes(32), ctypes.byref(params), ctypes.byref(h)) == fhd.FHD_ERR_INVALID_ARG
+        assert word in lib.cipher_last_error(None)
+        assert lib.cipher_init_raw(1.0, 2.0, 3.0, 4.0, -1.0, ctypes.byref(params), ctypes.byref(h)) == \
+            fhd.FHD_ERR_INVALID_ARG
+    assert set(_lib.DIGEST_MODES.values()) == {0, 1} and set(_lib.TRANSPORTS.values()) == {0, 1}
