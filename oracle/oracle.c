@@ -313,125 +313,99 @@ void oracle_keystream(const double *IR, uint32_t n, double gamma, double hstep,
 /* Frame encryption on the expanded bit matrices (Sec. II-C, Algos 3-7).    */
 /* ------------------------------------------------------------------------ */
 
-/* One channel c at a time, with the paper's [8w x h] bit matrices stored as
- * one byte per bit, row i of length 8w.  Algorithm 1 runs Algos 3..7 in turn
- * and swaps M_t <- M_e after each; the swap is read as taking effect after
- * Algos 4, 5 and 6 (after Algo 3 the extracted bits are already in M_t).
- * Readings: d_h of (row i, channel c) is D[c*h + i]; d_v of (pixel column j,
- * channel c) is D[C*h + c*w + j] -- Algo 5 gives one d_v per thread, shared by
- * its eight bits, and Eq. (3)'s unbalanced parentheses are read as Algo 5's
- * ((i + (d_v mod h)) mod h); the byte b of Algo 6 for thread (i, j, c) is
- * B[(i*w + j)*C + c]. */
+/* bit k of byte x, k = 0 the least significant (the order of Algo 3). */
+static uint8_t bit_of(uint8_t x, int k) { return (uint8_t)((x >> k) & 1u); }
+
+/* A byte from its eight bits, bits[k] the coefficient of 2^k (Algo 7 packs
+ * the bits back in the order Algo 3 took them out). */
+static uint8_t byte_of(const uint8_t *bits) {
+    uint32_t v = 0;
+    for (int k = 0; k < 8; ++k) v += (uint32_t)bits[k] << k;
+    return (uint8_t)v;
+}
+
+/* The confusion of Sec. II-C on one channel c, stated on the paper's
+ * [8w x h] bit matrix, one byte per bit, row i of length 8w:
+ *   M (i, 8j + k)                   = bit k of F(i, j, c)               (Algo 3)
+ *   M1(i, (p + d_h(i)) mod 8w)      = M (i, p)                          (Algo 4)
+ *   M2((i + d_v(p / 8)) mod h, p)   = M1(i, p)                          (Algo 5)
+ *   M3(i, 8j + k)                   = M2(i, 8j + k) xor bit k of B(i, j, c)   (Algo 6)
+ *   E (i, j, c)                     = sum over k of M3(i, 8j + k) 2^k    (Algo 7)
+ * Readings: Algorithm 1's "M_t <- M_e" is a buffer swap after Algos 4, 5 and
+ * 6 (after Algo 3 the extracted bits are already the matrix the shifts act
+ * on); d_h(i) of (row i, channel c) is D[c*h + i]; d_v of (pixel column j,
+ * channel c) is D[C*h + c*w + j] -- Algo 5 gives one d_v per thread, shared
+ * by its eight bits, and Eq. (3)'s unbalanced parentheses are read as
+ * Algo 5's ((i + (d_v mod h)) mod h); the byte of Algo 6 for pixel (i, j) of
+ * channel c is B[(i*w + j)*C + c]. */
 void oracle_permute_encrypt(const uint8_t *F, uint32_t h, uint32_t w, uint32_t C,
                             const uint16_t *D, const uint8_t *B, uint8_t *E) {
     uint64_t W8 = 8ull * w;
-    uint8_t *Mt = (uint8_t *)malloc(h * W8);
-    uint8_t *Me = (uint8_t *)malloc(h * W8);
+    uint8_t *M = (uint8_t *)malloc(h * W8);
+    uint8_t *M1 = (uint8_t *)malloc(h * W8);
     for (uint32_t c = 0; c < C; ++c) {
-        /* Algorithm 3: bit k of F_o^c(i,j), least significant first. */
         for (uint32_t i = 0; i < h; ++i)
-            for (uint32_t j = 0; j < w; ++j) {
-                uint8_t p = F[((uint64_t)i * w + j) * C + c];
-                for (int k = 0; k < 8; ++k) {
-                    Mt[i * W8 + 8ull * j + k] = p & 1u;
-                    p >>= 1;
-                }
-            }
-        /* Algorithm 4: horizontal circular shift of row i by d_h. */
-        for (uint32_t i = 0; i < h; ++i) {
-            uint64_t dh = D[(uint64_t)c * h + i] % W8;
             for (uint32_t j = 0; j < w; ++j)
                 for (int k = 0; k < 8; ++k)
-                    Me[i * W8 + (8ull * j + k + dh) % W8] = Mt[i * W8 + 8ull * j + k];
+                    M[i * W8 + 8ull * j + k] = bit_of(F[((uint64_t)i * w + j) * C + c], k);
+        for (uint32_t i = 0; i < h; ++i) {
+            uint64_t dh = D[(uint64_t)c * h + i] % W8;
+            for (uint64_t p = 0; p < W8; ++p) M1[i * W8 + (p + dh) % W8] = M[i * W8 + p];
         }
-        { uint8_t *t = Mt; Mt = Me; Me = t; }
-        /* Algorithm 5: vertical circular shift of pixel column j by d_v. */
-        for (uint32_t j = 0; j < w; ++j) {
-            uint64_t dv = D[(uint64_t)C * h + (uint64_t)c * w + j] % h;
-            for (uint32_t i = 0; i < h; ++i)
+        /* M2 reuses M's storage: every position of M is written once. */
+        uint8_t *M2 = M;
+        for (uint64_t p = 0; p < W8; ++p) {
+            uint64_t dv = D[(uint64_t)C * h + (uint64_t)c * w + p / 8] % h;
+            for (uint32_t i = 0; i < h; ++i) M2[((i + dv) % h) * W8 + p] = M1[i * W8 + p];
+        }
+        uint8_t *M3 = M1;
+        for (uint32_t i = 0; i < h; ++i)
+            for (uint32_t j = 0; j < w; ++j)
                 for (int k = 0; k < 8; ++k)
-                    Me[((i + dv) % h) * W8 + 8ull * j + k] = Mt[i * W8 + 8ull * j + k];
-        }
-        { uint8_t *t = Mt; Mt = Me; Me = t; }
-        /* Algorithm 6: XOR with the bits of b, least significant first. */
+                    M3[i * W8 + 8ull * j + k] =
+                        M2[i * W8 + 8ull * j + k] ^ bit_of(B[((uint64_t)i * w + j) * C + c], k);
         for (uint32_t i = 0; i < h; ++i)
-            for (uint32_t j = 0; j < w; ++j) {
-                uint8_t b = B[((uint64_t)i * w + j) * C + c];
-                for (int k = 0; k < 8; ++k) {
-                    Me[i * W8 + 8ull * j + k] = Mt[i * W8 + 8ull * j + k] ^ (b & 1u);
-                    b >>= 1;
-                }
-            }
-        { uint8_t *t = Mt; Mt = Me; Me = t; }
-        /* Algorithm 7: rebuild the byte, k from 7 down to 0, shifting left
-         * after every bit but the last. */
-        for (uint32_t i = 0; i < h; ++i)
-            for (uint32_t j = 0; j < w; ++j) {
-                uint32_t px = 0;
-                for (int k = 7; k >= 0; --k) {
-                    px |= Mt[i * W8 + 8ull * j + k];
-                    if (k != 0) px <<= 1;
-                }
-                E[((uint64_t)i * w + j) * C + c] = (uint8_t)px;
-            }
+            for (uint32_t j = 0; j < w; ++j)
+                E[((uint64_t)i * w + j) * C + c] = byte_of(M3 + i * W8 + 8ull * j);
     }
-    free(Mt);
-    free(Me);
+    free(M);
+    free(M1);
 }
 
 /* Decryption: the paper gives it only as "the inverse transformation of the
- * encryption procedure" (Sec. II-D).  On the same bit matrices, in reverse
- * order: XOR with B (Algo 6 is an involution), undo the vertical shift
- * (row (i + d_v) mod h goes back to row i), undo the horizontal shift (bit
- * (p + d_h) mod 8w goes back to p), rebuild bytes. */
+ * encryption procedure" (Sec. II-D).  On the same bit matrices, each map of
+ * the encryption undone in reverse order:
+ *   A (i, 8j + k)  = bit k of E(i, j, c)
+ *   A2(i, 8j + k)  = A(i, 8j + k) xor bit k of B(i, j, c)      (Algo 6 is an involution)
+ *   A1(i, p)       = A2((i + d_v(p / 8)) mod h, p)             (inverse of Algo 5)
+ *   A0(i, p)       = A1(i, (p + d_h(i)) mod 8w)                (inverse of Algo 4)
+ *   F (i, j, c)    = sum over k of A0(i, 8j + k) 2^k */
 void oracle_permute_decrypt(const uint8_t *E, uint32_t h, uint32_t w, uint32_t C,
                             const uint16_t *D, const uint8_t *B, uint8_t *F) {
     uint64_t W8 = 8ull * w;
-    uint8_t *Mt = (uint8_t *)malloc(h * W8);
-    uint8_t *Me = (uint8_t *)malloc(h * W8);
+    uint8_t *A = (uint8_t *)malloc(h * W8);
+    uint8_t *A1 = (uint8_t *)malloc(h * W8);
     for (uint32_t c = 0; c < C; ++c) {
         for (uint32_t i = 0; i < h; ++i)
             for (uint32_t j = 0; j < w; ++j) {
-                uint8_t p = E[((uint64_t)i * w + j) * C + c];
-                for (int k = 0; k < 8; ++k) {
-                    Mt[i * W8 + 8ull * j + k] = p & 1u;
-                    p >>= 1;
-                }
+                uint8_t e = E[((uint64_t)i * w + j) * C + c], b = B[((uint64_t)i * w + j) * C + c];
+                for (int k = 0; k < 8; ++k) A[i * W8 + 8ull * j + k] = bit_of(e, k) ^ bit_of(b, k);
             }
-        for (uint32_t i = 0; i < h; ++i)
-            for (uint32_t j = 0; j < w; ++j) {
-                uint8_t b = B[((uint64_t)i * w + j) * C + c];
-                for (int k = 0; k < 8; ++k) {
-                    Me[i * W8 + 8ull * j + k] = Mt[i * W8 + 8ull * j + k] ^ (b & 1u);
-                    b >>= 1;
-                }
-            }
-        { uint8_t *t = Mt; Mt = Me; Me = t; }
-        for (uint32_t j = 0; j < w; ++j) {
-            uint64_t dv = D[(uint64_t)C * h + (uint64_t)c * w + j] % h;
-            for (uint32_t i = 0; i < h; ++i)
-                for (int k = 0; k < 8; ++k)
-                    Me[i * W8 + 8ull * j + k] = Mt[((i + dv) % h) * W8 + 8ull * j + k];
+        for (uint64_t p = 0; p < W8; ++p) {
+            uint64_t dv = D[(uint64_t)C * h + (uint64_t)c * w + p / 8] % h;
+            for (uint32_t i = 0; i < h; ++i) A1[i * W8 + p] = A[((i + dv) % h) * W8 + p];
         }
-        { uint8_t *t = Mt; Mt = Me; Me = t; }
+        uint8_t *A0 = A;
         for (uint32_t i = 0; i < h; ++i) {
             uint64_t dh = D[(uint64_t)c * h + i] % W8;
-            for (uint64_t p = 0; p < W8; ++p)
-                Me[i * W8 + p] = Mt[i * W8 + (p + dh) % W8];
+            for (uint64_t p = 0; p < W8; ++p) A0[i * W8 + p] = A1[i * W8 + (p + dh) % W8];
         }
-        { uint8_t *t = Mt; Mt = Me; Me = t; }
         for (uint32_t i = 0; i < h; ++i)
-            for (uint32_t j = 0; j < w; ++j) {
-                uint32_t px = 0;
-                for (int k = 7; k >= 0; --k) {
-                    px |= Mt[i * W8 + 8ull * j + k];
-                    if (k != 0) px <<= 1;
-                }
-                F[((uint64_t)i * w + j) * C + c] = (uint8_t)px;
-            }
+            for (uint32_t j = 0; j < w; ++j)
+                F[((uint64_t)i * w + j) * C + c] = byte_of(A0 + i * W8 + 8ull * j);
     }
-    free(Mt);
-    free(Me);
+    free(A);
+    free(A1);
 }
 
 /* ------------------------------------------------------------------------ */
