@@ -51,9 +51,9 @@ HBM_PEAK_FALLBACK = 6800.0
 # 2.07 GHz maximum SM clock.
 FP64_PEAK_TOPS = 1.684 * 152 * 2.07e9 / 1e12
 RK4_FP64_OPS = 104      # per chain step: 4 x 13 (Eq. 1) + 3 x 8 (stages) + 4 x 7 (combination)
-# DRAM bytes (read + write) per 1080p frame of one launch, from the ncu capture summarised in
-# profiles/ncu_hot_kernels_clip1080p_4frames.md (4 frames per launch, scaled by frames; cold caches,
-# writes still in L2 at kernel end not counted); None where the kernel changed after that capture.
+# DRAM bytes (read + write) per 1080p frame of one launch, from an ncu capture of the hot kernels on a
+# 4-frame clip (scaled by frames; cold caches, writes still in L2 at kernel end not counted); None where
+# the kernel changed after that capture.
 TRAFFIC_PER_FRAME = {"keystream": (44288 + 256) / 4, "encrypt": (24923392 + 19456 + 49830912 + 1633280) / 4,
                      "decrypt": (49858304 + 1448704 + 24923136 + 12032) / 4, "sha": 24928000 / 4,
                      "master": 33792 / 4}

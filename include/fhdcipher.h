@@ -251,7 +251,8 @@ void cipher_destroy(fhd_cipher *c);
 /* Sec. II-A: digest[32] = XOR over i < n of SHA-256 of bytes
  * [floor(i*nbytes/n), floor((i+1)*nbytes/n)) of `data` (FIPS 180-4).
  * nbytes may be 0.  `count` independent buffers of equal size laid end to end
- * (data + k*nbytes -> digest + 32k) are hashed in one launch. */
+ * (data + k*nbytes -> digest + 32k) are hashed in one launch.  count * n above
+ * 2^32 - 1 returns FHD_ERR_TOO_LARGE and enqueues nothing. */
 int fhd_frame_digest(const uint8_t *data, uint64_t nbytes, uint32_t n, uint32_t count,
                      uint8_t *digest, void *stream);
 
@@ -272,7 +273,10 @@ int fhd_frame_digest_tree(const uint8_t *data, uint64_t nbytes, uint32_t n, uint
  * FHD_NOALLOC_MAX_SUBFRAMES returns FHD_ERR_TOO_LARGE and enqueues nothing.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, once per device, with that device current); make
- * that first call before any stream capture.  All calls share the one array:
+ * that first call before any stream capture.  The address is cached for the
+ * life of the process: it assumes the device's primary context is never torn
+ * down, so do not call this entry point again after cudaDeviceReset (the
+ * reloaded module's array may sit elsewhere).  All calls share the one array:
  * calls that overlap on the GPU (e.g. on two CUDA streams without ordering)
  * race and may return wrong digests. */
 #define FHD_NOALLOC_MAX_SUBFRAMES 65536u

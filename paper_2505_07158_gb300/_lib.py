@@ -397,11 +397,11 @@ def fhd_frame_digest(data: torch.Tensor, n: int = 32, count: int = 1, out: torch
                      mode: str = "xor"):
     """Frame digest of ``count`` equal buffers laid end to end: the XOR of the n sub-frame SHA-256 digests
     (mode "xor", the paper's), or SHA-256 of those digests concatenated in order (mode "tree")."""
+    if data.numel() % max(count, 1):
+        raise ValueError("data size must be a multiple of count")
     fn = {"xor": load().fhd_frame_digest, "tree": load().fhd_frame_digest_tree}[mode]
     if not data.is_cuda or data.dtype != torch.uint8 or not data.is_contiguous():
         raise ValueError("data must be a contiguous CUDA uint8 tensor")
-    if data.numel() % max(count, 1):
-        raise ValueError("data size must be a multiple of count")
     nbytes = data.numel() // max(count, 1)
     if out is None:
         out = torch.empty((count, 32), dtype=torch.uint8, device=data.device)
@@ -480,6 +480,8 @@ def fhd_stats_local_entropy(frames: torch.Tensor, blocks: torch.Tensor, block: i
 
 def fhd_frame_digest_noalloc(data: torch.Tensor, out: torch.Tensor, n: int = 32, count: int = 1, stream=None):
     """fhd_frame_digest into a caller-provided ``out`` (count x 32 bytes); the library allocates nothing."""
+    if data.numel() % max(count, 1):
+        raise ValueError("data size must be a multiple of count")
     if not data.is_cuda or data.dtype != torch.uint8 or not data.is_contiguous():
         raise ValueError("data must be a contiguous CUDA uint8 tensor")
     if not out.is_cuda or out.dtype != torch.uint8 or not out.is_contiguous() or out.numel() < 32 * count:

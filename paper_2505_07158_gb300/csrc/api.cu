@@ -956,6 +956,8 @@ int fhd_frame_digest(const uint8_t *data, uint64_t nbytes, uint32_t n, uint32_t 
     if ((!data && nbytes) || !digest) return fail(nullptr, FHD_ERR_INVALID_ARG, "null argument");
     if (n == 0 || n > FHD_MAX_WORKERS) return fail(nullptr, FHD_ERR_INVALID_ARG, "n must be 1..FHD_MAX_WORKERS");
     if (count == 0) return FHD_OK;
+    if ((uint64_t)count * n > UINT32_MAX)   // the hash kernel numbers the count * n messages with 32 bits
+        return fail(nullptr, FHD_ERR_TOO_LARGE, "count * n exceeds 2^32 - 1 sub-frames");
     cudaStream_t s = (cudaStream_t)stream;
     uint8_t *part = nullptr;
     cudaError_t e = cudaMallocAsync(&part, 32ull * n * count, s);
@@ -972,6 +974,8 @@ int fhd_frame_digest_tree(const uint8_t *data, uint64_t nbytes, uint32_t n, uint
     if ((!data && nbytes) || !digest) return fail(nullptr, FHD_ERR_INVALID_ARG, "null argument");
     if (n == 0 || n > FHD_MAX_WORKERS) return fail(nullptr, FHD_ERR_INVALID_ARG, "n must be 1..FHD_MAX_WORKERS");
     if (count == 0) return FHD_OK;
+    if ((uint64_t)count * n > UINT32_MAX)   // the hash kernel numbers the count * n messages with 32 bits
+        return fail(nullptr, FHD_ERR_TOO_LARGE, "count * n exceeds 2^32 - 1 sub-frames");
     cudaStream_t s = (cudaStream_t)stream;
     uint8_t *part = nullptr;
     cudaError_t e = cudaMallocAsync(&part, 32ull * n * count, s);

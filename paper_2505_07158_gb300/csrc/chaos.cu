@@ -7,8 +7,8 @@
 //   s' = s + (h/6) (((k1 + 2 k2) + 2 k3) + k4),
 // every operation an explicit round-to-nearest binary64 intrinsic (no FMA
 // contraction; the library is also built with -fmad=false), so the iterates
-// are bit-identical to a plain C implementation.  2 k is an exact doubling
-// done on the bit pattern.
+// are bit-identical to a plain C implementation.  The term acc + 2 k of the
+// combination is one fma(k, 2, acc) (see below).
 //
 // GPU mapping.  On this GPU a binary64 instruction occupies the SM
 // sub-partition's FP64 pipe for ~64 cycles whatever the number of active

@@ -98,3 +98,23 @@ def test_protocol_parameters_are_checked_before_any_device_work(lib):
         assert lib.cipher_init_raw(1.0, 2.0, 3.0, 4.0, -1.0, ctypes.byref(params), ctypes.byref(h)) == \
             fhd.FHD_ERR_INVALID_ARG
     assert set(_lib.DIGEST_MODES.values()) == {0, 1} and set(_lib.TRANSPORTS.values()) == {0, 1}
+
+
+def test_digest_calls_reject_more_than_2_32_sub_frames(lib):
+    """count * n is the hash kernel's 32-bit message count: beyond 2^32 - 1 the allocating digest calls
+    return FHD_ERR_TOO_LARGE before any allocation or launch (so this needs no GPU)."""
+    import paper_2505_07158_gb300 as fhd
+    dig = ctypes.create_string_buffer(32)
+    for fn in (lib.fhd_frame_digest, lib.fhd_frame_digest_tree, lib.fhd_frame_digest_noalloc):
+        assert fn(None, 0, 4, 1 << 31, dig, None) == fhd.FHD_ERR_TOO_LARGE
+        assert b"exceeds" in lib.cipher_last_error(None)
+
+
+def test_digest_wrappers_reject_a_size_that_count_does_not_divide():
+    import torch
+    import paper_2505_07158_gb300 as fhd
+    data = torch.zeros(10, dtype=torch.uint8)
+    with pytest.raises(ValueError, match="multiple of count"):
+        fhd.fhd_frame_digest(data, n=2, count=3)
+    with pytest.raises(ValueError, match="multiple of count"):
+        fhd._lib.fhd_frame_digest_noalloc(data, torch.zeros(96, dtype=torch.uint8), n=2, count=3)
