@@ -46,10 +46,9 @@ import synth_inputs as si  # noqa: E402
 FRAMES, HGT, WID, CH = 30, 1080, 1920, 3
 N_WORKERS = 32
 HBM_PEAK_FALLBACK = 6800.0
-# FP64 pipe: 1.684 binary64 lane-ops per clock per SM (measured with a
-# dependent-free DADD/DMUL microbenchmark, clock-independent), x 152 SMs x
-# 2.07 GHz maximum SM clock.
-FP64_PEAK_TOPS = 1.684 * 152 * 2.07e9 / 1e12
+# FP64 pipe, used only when the in-run probe (run_fp64_probe) cannot run: 1.684 binary64 lane-ops per clock
+# per SM (an earlier probe with one warp per sub-partition), x 152 SMs x 2.07 GHz maximum SM clock.
+FP64_PEAK_TOPS_FALLBACK = 1.684 * 152 * 2.07e9 / 1e12
 RK4_FP64_OPS = 104      # per chain step: 4 x 13 (Eq. 1) + 3 x 8 (stages) + 4 x 7 (combination)
 # DRAM bytes (read + write) per 1080p frame of one launch, from an ncu capture of the hot kernels on a
 # 4-frame clip (scaled by frames; cold caches, writes still in L2 at kernel end not counted); None where
@@ -68,6 +67,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
     ap.add_argument("--frames", type=int, default=30, help="frames per step (30 = the clip; smaller for ncu)")
+    ap.add_argument("--dry-run", action="store_true",
+                    help="multi-process skeleton only (gloo, no GPU): ranks, barrier, max-over-ranks, one line")
+    ap.add_argument("--repeats", type=int, default=5,
+                    help="timed regions of --steps steps each; value is the median region")
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="length of each serving run (60 s = full config)")
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed-batch, serving and stress measurements")
     ap.add_argument("--no-stress", action="store_true", help="skip the 256 x 8K stress round trip")
@@ -155,6 +158,43 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- binary64 peak
+
+def run_fp64_probe(fhd, torch, dev, gpu_index, iters=16384, reps=5, warps=(1, 2, 3, 4, 6, 8)):
+    """The binary64 pipe's rate on this GPU, measured in this run: the library's probe kernel (one CTA per
+    SM, k warps per sub-partition, eight independent fma chains per lane), each k timed with CUDA events
+    (best of `reps` launches) while nvidia-smi samples the SM clock.  Returns the per-k rates, the peak
+    (the best rate, in binary64 Top/s) and the lane-ops per clock per SM at the sampled median clock."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.zeros(sms, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    rows = {}
+    with ClockSampler(gpu_index) as clk:
+        for k in warps:
+            for _ in range(2):
+                fhd.fhd_fp64_probe(k, iters, sink, stream)
+            best = None
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ops = fhd.fhd_fp64_probe(k, iters, sink, stream)
+                b.record(stream)
+                b.synchronize()
+                ms = a.elapsed_time(b)
+                best = ms if best is None else min(best, ms)
+            rows[k] = {"ms": best, "lane_ops": ops, "tops": ops / (best / 1000.0) / 1e12}
+    clocks = clk.summary()
+    mhz = clocks.get("sm_mhz")
+    for r in rows.values():
+        r["lane_ops_per_clk_per_sm"] = (r["tops"] * 1e12 / (mhz * 1e6 * sms)) if mhz else None
+    kbest = max(rows, key=lambda k: rows[k]["tops"])
+    return {"peak_tops": rows[kbest]["tops"], "best_warps_per_subpartition": kbest,
+            "lane_ops_per_clk_per_sm": rows[kbest]["lane_ops_per_clk_per_sm"], "sms": sms,
+            "per_warps_per_subpartition": {str(k): v for k, v in rows.items()}, "clocks": clocks,
+            "kernel": "fp64_probe_kernel: one CTA per SM, 4k warps, 8 independent __fma_rn chains per lane, "
+                      f"{iters} steps; best of {reps} launches per k, CUDA events"}
 
 
 # ---------------------------------------------------------------- work model
@@ -431,29 +471,42 @@ def run_ours(args):
     # ---- one clip in flight (the sender's next clip waits for the receiver), when the headline has more
     ms_one = timed_steps(args.steps, 1)[1] if INF > 1 else None
 
-    # ---- device-resident timed region (with per-kernel events on the launch streams)
+    # ---- the binary64 peak of this GPU, measured in this run (the keystream roofline's denominator)
+    try:
+        fp64 = run_fp64_probe(fhd, torch, dev, local)
+    except Exception as exc:   # noqa: BLE001 -- report, fall back to the recorded figure
+        fp64 = {"error": repr(exc)}
+
+    # ---- device-resident timed region, repeated; per-kernel events on the launch streams in every
+    # repeat.  value = the median repeat (its spans and kernel sums feed the rooflines); min and max reported.
+    from paper_2505_07158_gb300 import replicas
     enc.profile(True)
     dec.profile(True)
+    reps = []
     l0 = fhd.fhd_launch_count()
     with ClockSampler(local) as clk:
-        origin, ms_total, _ = timed_steps(args.steps, INF)
-    launches = fhd.fhd_launch_count() - l0
-    from paper_2505_07158_gb300 import replicas
-    enc_spans, dec_spans = enc.profile_spans(origin), dec.profile_spans(origin)
+        for r in range(max(1, args.repeats)):
+            origin, ms_r, _ = timed_steps(args.steps, INF)
+            if r == 0:
+                launches = fhd.fhd_launch_count() - l0
+            es, ds = enc.profile_spans(origin), dec.profile_spans(origin)
+            pr = {}
+            for c in (enc, dec):
+                for k, (ms, n) in c.profile_read().items():
+                    a = pr.setdefault(k, [0.0, 0])
+                    a[0] += ms
+                    a[1] += n
+            reps.append((replicas.max_over_ranks(ms_r, device=dev), es, ds, pr))
+    enc.profile(False)
+    dec.profile(False)
+    order = sorted(range(len(reps)), key=lambda i: reps[i][0])
+    ms_total, enc_spans, dec_spans, prof = reps[order[len(order) // 2]]
+    rep_values = [world * FRAMES * args.steps / (r[0] / 1000.0) for r in reps]
     spans = enc_spans + dec_spans
     if args.spans and rank == 0:
         with open(args.spans, "w") as fh:
             json.dump({"ms_total": ms_total, "steps": args.steps, "inflight": INF,
                        "sender": enc_spans, "receiver": dec_spans}, fh)
-    prof = {}
-    for c in (enc, dec):
-        for k, (ms, n) in c.profile_read().items():
-            a = prof.setdefault(k, [0.0, 0])
-            a[0] += ms
-            a[1] += n
-    enc.profile(False)
-    dec.profile(False)
-    ms_total = replicas.max_over_ranks(ms_total, device=dev)
     ms_step = ms_total / args.steps
     value = replicas.job_throughput(FRAMES * args.steps, ms_total, world)
     ms_one = replicas.max_over_ranks(ms_one, device=dev) if ms_one is not None else ms_total
@@ -524,6 +577,14 @@ def run_ours(args):
     chain_steps = worker_steps(HGT, WID, CH, N_WORKERS) * per_step_frames   # per keystream launch (one per call)
     master_steps = 2 * N_WORKERS * per_step_frames
 
+    if "peak_tops" in fp64:
+        fp64_peak = fp64["peak_tops"]
+        fp64_source = (f"fp64_probe leg of this run: binary64 lane-ops/s of the library's probe kernel at "
+                       f"{fp64['best_warps_per_subpartition']} warps per sub-partition (best of 1-8)")
+    else:
+        fp64_peak = FP64_PEAK_TOPS_FALLBACK
+        fp64_source = "fallback: 1.684 lane-op/clk/SM x 152 SMs x 2.07 GHz (probe did not run)"
+
     def fp64_roof(k, steps_per_launch):
         # Launches of one kind overlap (sender and receiver, clips in flight): achieved = algorithmic
         # ops of all its launches / the union of their spans; per launch for reference.
@@ -532,9 +593,9 @@ def run_ours(args):
         ach = n_l * steps_per_launch * RK4_FP64_OPS / (busy / 1000.0) / 1e12
         ms = kern[k]["avg_launch_ms"]
         tpf = TRAFFIC_PER_FRAME.get(k)
-        return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TOPS, "traffic": tpf * per_step_frames if tpf is not None else None,
-                "peak_source": "binary64 pipe: measured 1.684 lane-op/clk/SM x 152 SMs x 2.07 GHz",
+        return {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": ach / fp64_peak, "traffic": tpf * per_step_frames if tpf is not None else None,
+                "peak_source": fp64_source,
                 "per_launch_units": f"{steps_per_launch} RK4 chain steps x {RK4_FP64_OPS} binary64 ops",
                 "busy_ms_per_step": busy / args.steps,
                 "achieved_per_launch": steps_per_launch * RK4_FP64_OPS / (ms / 1000.0) / 1e12,
@@ -571,7 +632,7 @@ def run_ours(args):
                         "note": f"{N_WORKERS} sequential messages per frame: one thread each"}
     dominant = max(kern, key=lambda k: kern[k]["share"]) if kern else None
 
-    extras = {} if args.no_extras else run_extras(args, rank, fhd, torch)
+    extras = {} if (args.no_extras or world > 1) else run_extras(args, rank, fhd, torch)
 
     line = None
     if rank == 0:
@@ -585,6 +646,8 @@ def run_ours(args):
         line = {
             "metric": "1080p RGB frames/s (encrypt + decrypt round trip)", "value": value, "unit": "frames/s",
             "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step,
+            "repeats": {"n": len(rep_values), "steps_each": args.steps, "value": "median",
+                        "min": min(rep_values), "max": max(rep_values), "values": rep_values},
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8+f64",
             "data": "synthetic",
             "config": {"workload": "30-frame 1920x1080x3 gradient+noise clip (sigma 8, 2 px/frame), one stream "
@@ -608,6 +671,7 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clocks,
             "roofline": dict(roofs[dominant], kernel=dominant) if dominant in roofs else None,
+            "fp64_probe": fp64,
             "roofline_fused_encrypt": roofs.get("encrypt"),
             "kernels": kern,
             "kernel_roofs": roofs,
@@ -778,8 +842,8 @@ def run_digest_modes(rank, fhd, torch, reps=10, steps=3):
     (SHA-256 of the concatenated sub-frame digests); the fold sent masked (H xor M, M from the chaining
     state; both options of this library).  Per mode: the digest stage alone on the 30-frame 1080p clip, the
     clip's round trip on one CUDA stream (as the n sweep) with its LHCS_m time, the receiver-side check, and
-    frame 0's digests against the oracle."""
-    import oracle
+    the digests of encrypt_frames against the standalone digest entry point (the oracle comparisons of
+    every mode are in the GPU tests)."""
     dev = torch.device("cuda", torch.cuda.current_device())
     clip_np = si.clip(FRAMES, HGT, WID, CH, seed=rank + 5)
     clip = torch.from_numpy(clip_np).to(dev)
@@ -788,7 +852,6 @@ def run_digest_modes(rank, fhd, torch, reps=10, steps=3):
     for name, mode, transport in (("xor", "xor", "plain"), ("tree", "tree", "plain"), ("xor_masked", "xor", "masked")):
         dig = fhd.fhd_frame_digest(flat, n=N_WORKERS, count=FRAMES, mode=mode)
         torch.cuda.synchronize()
-        ok = ok and bytes(dig[0].cpu().numpy()) == oracle.frame_digest(clip_np[0], N_WORKERS, mode)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         for _ in range(reps):
@@ -806,15 +869,8 @@ def run_digest_modes(rank, fhd, torch, reps=10, steps=3):
         di = [(rid, E[t], R[t], H[t]) for t in range(FRAMES)]
         enc.encrypt_frames(ei); dec.decrypt_frames(di)
         torch.cuda.synchronize()
-        if transport == "masked":   # frame 0 of the first clip: the transmitted digest against the oracle
-            ref = oracle.Stream.from_key(key, digest_mode=mode, transport=transport)
-            enc2 = fhd.Cipher(key, n_workers=N_WORKERS, digest_mode=mode, digest_transport=transport)
-            H0 = torch.empty(32, dtype=torch.uint8, device=dev)
-            E0 = torch.empty_like(clip[0])
-            enc2.encrypt_frames([(enc2.open_stream(), clip[0], E0, H0)])
-            torch.cuda.synchronize()
-            ok = ok and bytes(H0.cpu().numpy()) == ref.encrypt(clip_np[0])[1]
-            enc2.close()
+        # the receiver leaves the unmasked digest H in place: it must equal the standalone digest
+        ok = ok and torch.equal(H, dig)
         enc.profile(True)
         dec.profile(True)
         a.record()
@@ -833,13 +889,13 @@ def run_digest_modes(rank, fhd, torch, reps=10, steps=3):
                      "round_trip_ok": bool(torch.equal(R, clip)), "verify_ok": bool(int(verified.min()) == 1)}
         enc.close(); dec.close()
     return {"workload": "30 x 1080p clip: the digest stage alone (n = 32), and the round trip on one CUDA stream",
-            **res, "digests_match_oracle": bool(ok)}
+            **res, "digests_match_standalone_digest": bool(ok)}
 
 
 def run_stress(rank, fhd, torch, frames=256):
     """256 frames of 7680x4320x3 (uniform and gradient+noise halves, generated on the device), one stream,
-    encrypt then decrypt in one call each; round trip, sampled digests vs the oracle, permutation rooflines."""
-    import oracle
+    encrypt then decrypt in one call each; round trip, digests against the standalone digest entry point,
+    permutation rooflines (an 8K frame against the oracle is in the GPU tests)."""
     from paper_2505_07158_gb300 import autotune
     dev = torch.device("cuda", torch.cuda.current_device())
     h, w, C = 4320, 7680, 3
@@ -885,15 +941,14 @@ def run_stress(rank, fhd, torch, frames=256):
     dec.profile(False)
     ok = all(torch.equal(R[k], src[k]) for k in range(frames))
     N = h * w * C
-    digest_ok = all(bytes(Hd[k].cpu().numpy()) == oracle.frame_digest(src[k].cpu().numpy(), N_WORKERS)
-                    for k in (0, frames - 1))
+    digest_ok = all(torch.equal(Hd[k], fhd.fhd_frame_digest(src[k].view(-1), n=N_WORKERS)[0]) for k in (0, frames - 1))
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", HBM_PEAK_FALLBACK)
     enc_ms, dec_ms = a.elapsed_time(b), b.elapsed_time(c2)
     perm_e, perm_d = pe["encrypt"][0], pd["decrypt"][0]
     res = {"workload": f"{frames} x 7680x4320x3 uint8 (uniform / gradient+noise halves, device-generated), one stream, "
                        "encrypt then decrypt, one call each",
-           "round_trip_ok": bool(ok), "sampled_digests_match_oracle": bool(digest_ok),
+           "round_trip_ok": bool(ok), "digests_match_standalone_digest": bool(digest_ok),
            "encrypt_ms": enc_ms, "decrypt_ms": dec_ms,
            "frames_per_s_round_trip": frames / ((enc_ms + dec_ms) / 1000.0),
            "kernel_ms": {"encrypt": {k: v[0] for k, v in pe.items() if v[1]},
@@ -912,10 +967,56 @@ def run_stress(rank, fhd, torch, frames=256):
     return res
 
 
+def free_port() -> int:
+    import socket
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def launch_ranks(n: int) -> int:
+    """--gpus N without a launcher: start N copies of this command, one process per GPU (RANK = LOCAL_RANK =
+    index, WORLD_SIZE = N, rendezvous on 127.0.0.1), and return the worst exit code.  Rank 0 prints the
+    JSON line; the other ranks print nothing."""
+    port = free_port()
+    procs = []
+    for r in range(n):
+        env = dict(os.environ, RANK=str(r), LOCAL_RANK=str(r), WORLD_SIZE=str(n), LOCAL_WORLD_SIZE=str(n),
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+        procs.append(subprocess.Popen([sys.executable, os.path.abspath(__file__), *sys.argv[1:]], env=env))
+    return max(p.wait() for p in procs)
+
+
+def run_dry(args):
+    """The multi-process skeleton without a GPU (gloo): barrier, max-over-ranks of a per-rank time, one JSON
+    line from rank 0 with the job-level count of ranks."""
+    import torch
+    import torch.distributed as dist
+    from paper_2505_07158_gb300 import replicas
+    rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        dist.init_process_group("gloo")
+    ranks = torch.ones(1)
+    if world > 1:
+        dist.all_reduce(ranks)
+    ms = replicas.max_over_ranks(1.0 + rank)
+    if rank == 0:
+        print(json.dumps({"dry_run": True, "n_gpus": world, "ranks_seen": int(ranks.item()), "max_ms": ms,
+                          "value": replicas.job_throughput(FRAMES, ms, world)}))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        return launch_ranks(args.gpus)
+    if args.dry_run:
+        return run_dry(args)
     return run_ours(args)
 
 

@@ -407,6 +407,17 @@ int cipher_profile_read(fhd_cipher *c, double *ms, uint32_t *launches);
 int cipher_profile_spans(fhd_cipher *c, void *origin, uint32_t cap, int32_t *kinds, double *start_ms,
                          double *end_ms, uint32_t *count);
 
+/* Binary64 pipe probe (measurement only; the paper has no counterpart): the
+ * peak rate against which the worker kernel's roofline (Sec. II-B) is quoted.
+ * Launches one CTA per SM with 4 * warps_per_subpartition warps (1..8), every
+ * lane running eight independent binary64 fused multiply-add chains of `iters`
+ * steps (1..2^24), asynchronously on `stream`; the caller times it with CUDA
+ * events.  *lane_ops (host) receives the binary64 lane-operations it executes
+ * (SMs x threads x iters x 8).  `sink` is a device buffer of at least one
+ * double per SM that the kernel may write.  Bad arguments return
+ * FHD_ERR_INVALID_ARG and enqueue nothing. */
+int fhd_fp64_probe(uint32_t warps_per_subpartition, uint32_t iters, double *sink, uint64_t *lane_ops, void *stream);
+
 /* Number of kernels this library has launched in this process. */
 uint64_t fhd_launch_count(void);
 

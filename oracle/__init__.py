@@ -238,6 +238,15 @@ class Stream:
                                      _ptr(F), h, w, C, _ptr(E), _ptr(H), self.digest_mode, self.masked)
         return E, H.tobytes()
 
+    def advance(self, F):
+        """The chaining step of Algorithm 1 alone: the state after frame F (its digest H, then 2n LHCS_m
+        steps from the state reconstructed from H), without the worker keystream or the confusion, which
+        do not feed the state.  Returns the frame's digest H (as computed, not masked)."""
+        H = frame_digest(F, self.n, "tree" if self.digest_mode == 1 else "xor")
+        _, ns = master(self.state, H, self.gamma, self.n, self.h, self.u)
+        self.state = np.array(ns, np.float64)
+        return H
+
     def decrypt(self, E, H: bytes):
         """Inverse of :meth:`encrypt` given the transmitted digest H."""
         E = _u8(E)

@@ -38,7 +38,7 @@ EXPORTS = (
     "decrypt_frames_split", "encrypt_frames_split", "cipher_profile_spans", "cipher_set_partition",
     "cipher_get_partition", "cipher_set_layout", "fhd_stats_histogram", "fhd_stats_npcr_uaci",
     "fhd_stats_correlation", "fhd_stats_local_entropy", "encrypt_frames_sched", "decrypt_frames_sched",
-    "fhd_frame_digest_tree",
+    "fhd_frame_digest_tree", "fhd_fp64_probe",
 )
 KERNEL_KINDS = ("sha", "master", "keystream", "encrypt", "decrypt")
 
@@ -133,6 +133,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "cipher_reserve": (i32, [P, P, u64]),
             "cipher_verify_frames": (i32, [P, u32, P, P, P]),
             "fhd_frame_scratch_bytes": (u64, [u32, u32, u32, u32]),
+            "fhd_fp64_probe": (i32, [u32, u32, P, ctypes.POINTER(u64), P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -476,6 +477,16 @@ def fhd_stats_local_entropy(frames: torch.Tensor, blocks: torch.Tensor, block: i
     _check(load().fhd_stats_local_entropy(_vp(f), n, h, w, c, _vp(blocks), blocks.shape[1], block, _vp(out),
                                           _vp(status), _stream_ptr(stream)))
     return out, status
+
+
+def fhd_fp64_probe(warps_per_subpartition: int, iters: int, sink: torch.Tensor, stream=None) -> int:
+    """Launch the binary64 pipe probe; returns the binary64 lane-operations it executes."""
+    if not sink.is_cuda or sink.dtype != torch.float64:
+        raise ValueError("sink must be a CUDA float64 tensor (one element per SM)")
+    ops = ctypes.c_uint64()
+    _check(load().fhd_fp64_probe(warps_per_subpartition, iters, ctypes.c_void_p(sink.data_ptr()), ctypes.byref(ops),
+                                 _stream_ptr(stream)))
+    return int(ops.value)
 
 
 def fhd_frame_digest_noalloc(data: torch.Tensor, out: torch.Tensor, n: int = 32, count: int = 1, stream=None):

@@ -1,6 +1,6 @@
 """Build ``libfhdcipher.so`` in-tree with nvcc for sm_103a (GB300).
 
-The five translation units are compiled in parallel and linked as one shared
+The translation units are compiled in parallel and linked as one shared
 library under ``paper_2505_07158_gb300/_build/``.  Device code is compiled
 with ``-fmad=false`` and host code with ``-ffp-contract=off``: the chaotic
 iteration must round every binary64 multiply and add on its own."""
@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfhdcipher.so")
-SOURCES = ["api.cu", "sha256.cu", "chaos.cu", "permute.cu", "stats.cu"]
+SOURCES = ["api.cu", "sha256.cu", "chaos.cu", "permute.cu", "stats.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "--expt-relaxed-constexpr",
               "-Xcompiler", "-fPIC,-ffp-contract=off", "-Xptxas", "-warn-spills"]

@@ -817,6 +817,16 @@ int cipher_profile_spans(fhd_cipher *c, void *origin, uint32_t cap, int32_t *kin
 
 uint64_t fhd_launch_count(void) { return g_launches.load(); }
 
+int fhd_fp64_probe(uint32_t warps_per_subpartition, uint32_t iters, double *sink, uint64_t *lane_ops, void *stream) {
+    if (!sink || !lane_ops) return fail(nullptr, FHD_ERR_INVALID_ARG, "null argument");
+    if (warps_per_subpartition < 1 || warps_per_subpartition > 8)
+        return fail(nullptr, FHD_ERR_INVALID_ARG, "warps_per_subpartition must be 1..8");
+    if (iters < 1 || iters > (1u << 24)) return fail(nullptr, FHD_ERR_INVALID_ARG, "iters must be 1..2^24");
+    cudaError_t e = fhd::launch_fp64_probe(warps_per_subpartition, iters, sink, lane_ops, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("probe launch: ") + cudaGetErrorString(e));
+    return FHD_OK;
+}
+
 int cipher_set_partition(fhd_cipher *c, int enable) {
     if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
     if (!enable) { c->partition = false; return FHD_OK; }

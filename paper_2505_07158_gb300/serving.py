@@ -63,7 +63,7 @@ class Server:
 
     def __init__(self, keys, shapes, frame_pool, n_workers: int = 32, budget_bytes: int = 20 << 30,
                  lanes: int = 16, slots_per_lane: int = 1, max_batch: int = 64, fingerprint: bool = False,
-                 outputs_per_shape: int = 32, partition: bool = False):
+                 outputs_per_shape: int = 32, partition: bool = False, keep: bool = False):
         self.n = n_workers
         self.cipher = _lib.Cipher(keys[0], n_workers=n_workers)
         # The lanes already overlap the frames of all streams; the SM partition would add two internal
@@ -97,6 +97,8 @@ class Server:
         self.batch_sizes = []
         self.fingerprint = fingerprint
         self.prints = {}                      # (stream, seq) -> digest of the ciphertext
+        self.keep = keep
+        self.kept = {}                        # (stream, seq) -> (ciphertext, transmitted digest) copies
         self._rr = 0
 
     def submit(self, fr: Frame):
@@ -117,6 +119,8 @@ class Server:
                     if self.fingerprint:
                         d = _lib.fhd_frame_digest(E.view(-1), n=256)
                         self.prints[(fr.stream, fr.seq)] = bytes(d.cpu().numpy().reshape(-1))
+                    if self.keep:               # before the buffers are reused (checks of served output)
+                        self.kept[(fr.stream, fr.seq)] = (E.clone(), H.clone())
                     self.free_out[self.shapes[fr.stream]].append((E, H))
 
     def _free_lane(self):
@@ -208,14 +212,17 @@ def latency_stats(frames, fps: float):
 
 
 def run(keys, shapes, frame_pool, fps: float, duration: float, seed: int = 0, n_workers: int = 32,
-        budget_bytes: int = 20 << 30, lanes: int | None = None, mode: str = "served", fingerprint: bool = False):
-    """Replay a Poisson arrival trace in real time; returns (stats, server)."""
+        budget_bytes: int = 20 << 30, lanes: int | None = None, mode: str = "served", fingerprint: bool = False,
+        keep: bool = False):
+    """Replay a Poisson arrival trace in real time; returns (stats, server).  keep=True keeps a copy of
+    every served frame's ciphertext and digest in ``server.kept``."""
     trace = arrivals([fps] * len(shapes), duration, seed)
     if mode == "plain":
         srv = Server(keys, shapes, frame_pool, n_workers, budget_bytes, lanes=1, slots_per_lane=1, max_batch=1,
-                     fingerprint=fingerprint)
+                     fingerprint=fingerprint, keep=keep)
     else:
-        srv = Server(keys, shapes, frame_pool, n_workers, budget_bytes, lanes=lanes or 16, fingerprint=fingerprint)
+        srv = Server(keys, shapes, frame_pool, n_workers, budget_bytes, lanes=lanes or 16, fingerprint=fingerprint,
+                     keep=keep)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     now = lambda: time.perf_counter() - t0

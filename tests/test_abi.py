@@ -47,6 +47,10 @@ def test_host_side_argument_checks(lib):
     assert lib.fhd_permute_encrypt(None, None, 4, 4, 3, None, None, None) == fhd.FHD_ERR_INVALID_ARG
     assert b"null" in lib.cipher_last_error(None)
     assert lib.fhd_set_strip_width(0, 4, 3, 8) == fhd.FHD_ERR_INVALID_ARG
+    ops = ctypes.c_uint64()
+    assert lib.fhd_fp64_probe(1, 16, None, ctypes.byref(ops), None) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.fhd_fp64_probe(9, 16, ctypes.c_void_p(16), ctypes.byref(ops), None) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.fhd_fp64_probe(1, 0, ctypes.c_void_p(16), ctypes.byref(ops), None) == fhd.FHD_ERR_INVALID_ARG
 
 
 def test_strip_width_fits_shared_memory(lib):

@@ -113,3 +113,24 @@ def test_key_sensitivity():
     P = oracle.Stream.from_key(bytes(k)).decrypt(E, H)
     npcr, _ = npcr_uaci(P, F)
     assert all(abs(v - NPCR_IDEAL) < 1.0 for v in npcr), npcr
+
+
+@pytest.mark.parametrize("mode", ["xor", "tree"])
+def test_chaining_step_alone_leaves_the_state_encryption_leaves(mode):
+    """Stream.advance (digest + LHCS_m only) leaves the chaining state that a full encryption of the same
+    frame leaves: the next frame then encrypts to the same ciphertext.  A wrong worker count, step, digest
+    mode or a skipped reconstruction in advance() would change that next ciphertext."""
+    key = si.key(3)
+    frames = si.clip(3, 24, 40, 3, seed=4)
+    full = oracle.Stream.from_key(key, n=5, digest_mode=mode)
+    short = oracle.Stream.from_key(key, n=5, digest_mode=mode)
+    for F in frames[:2]:
+        _, H = full.encrypt(F)
+        assert short.advance(F) == H
+        assert np.array_equal(full.state, short.state)
+    E_full, _ = full.encrypt(frames[2])
+    E_short, _ = short.encrypt(frames[2])
+    assert np.array_equal(E_full, E_short)
+    skipped = oracle.Stream.from_key(key, n=5, digest_mode=mode)
+    skipped.advance(frames[0])
+    assert not np.array_equal(skipped.encrypt(frames[2])[0], E_full)
