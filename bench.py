@@ -53,7 +53,7 @@ RK4_FP64_OPS = 104      # per chain step: 4 x 13 (Eq. 1) + 3 x 8 (stages) + 4 x 
 # DRAM bytes (read + write) per 1080p frame of one launch, from an ncu capture of the hot kernels on a
 # 4-frame clip (scaled by frames; cold caches, writes still in L2 at kernel end not counted); None where
 # the kernel changed after that capture.
-TRAFFIC_PER_FRAME = {"keystream": (44288 + 256) / 4, "encrypt": (24923392 + 19456 + 49830912 + 1633280) / 4,
+TRAFFIC_PER_FRAME = {"keystream": (44288 + 256) / 4, "encrypt": None,
                      "decrypt": (49858304 + 1448704 + 24923136 + 12032) / 4, "sha": 24928000 / 4,
                      "master": 33792 / 4}
 
@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--frames", type=int, default=30, help="frames per step (30 = the clip; smaller for ncu)")
     ap.add_argument("--dry-run", action="store_true",
                     help="multi-process skeleton only (gloo, no GPU): ranks, barrier, max-over-ranks, one line")
+    ap.add_argument("--no-probe", action="store_true", help="skip the binary64 peak probe (profiling runs)")
     ap.add_argument("--repeats", type=int, default=5,
                     help="timed regions of --steps steps each; value is the median region")
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="length of each serving run (60 s = full config)")
@@ -472,10 +473,12 @@ def run_ours(args):
     ms_one = timed_steps(args.steps, 1)[1] if INF > 1 else None
 
     # ---- the binary64 peak of this GPU, measured in this run (the keystream roofline's denominator)
-    try:
-        fp64 = run_fp64_probe(fhd, torch, dev, local)
-    except Exception as exc:   # noqa: BLE001 -- report, fall back to the recorded figure
-        fp64 = {"error": repr(exc)}
+    fp64 = {"skipped": "--no-probe"}
+    if not args.no_probe:
+        try:
+            fp64 = run_fp64_probe(fhd, torch, dev, local)
+        except Exception as exc:   # noqa: BLE001 -- report, fall back to the recorded figure
+            fp64 = {"error": repr(exc)}
 
     # ---- device-resident timed region, repeated; per-kernel events on the launch streams in every
     # repeat.  value = the median repeat (its spans and kernel sums feed the rooflines); min and max reported.
@@ -562,6 +565,28 @@ def run_ours(args):
     enc.profile(False)
     dec.profile(False)
     alone_ok = all(torch.equal(sl0.decs[t], sl0.srcs[t]) for t in range(FRAMES))
+    # the clip's encryption alone on a fresh stream through each route of the confusion + XOR (the single
+    # gather pass and the row pass + column pass): launch time of each, and equal ciphertexts
+    routes = {}
+    for route in ("single_pass", "two_pass"):
+        fhd.fhd_set_encrypt_route(route)
+        try:
+            tmp = fhd.Cipher(key, n_workers=N_WORKERS)
+            tmp.set_partition(False)
+            tmp.set_layout(args.layout)
+            tsid = tmp.open_stream()
+            outs = [torch.empty_like(x) for x in sl0.srcs]
+            items = [(tsid, sl0.srcs[t], outs[t], torch.empty(32, dtype=torch.uint8, device=dev))
+                     for t in range(FRAMES)]
+            tmp.profile(True)
+            tmp.encrypt_frames(items, stream)
+            torch.cuda.synchronize()
+            ms_r, n_r = tmp.profile_read()["encrypt"]
+            tmp.close()
+        finally:
+            fhd.fhd_set_encrypt_route("two_pass")
+        routes[route] = {"ms": ms_r / max(n_r, 1), "launches": n_r, "outs": outs}
+    routes_equal = all(torch.equal(a, b) for a, b in zip(routes["single_pass"]["outs"], routes["two_pass"]["outs"]))
 
     # ---- roofline of the dominant kernel (largest share of device time)
     peaks = measured_peaks()
@@ -673,6 +698,10 @@ def run_ours(args):
             "roofline": dict(roofs[dominant], kernel=dominant) if dominant in roofs else None,
             "fp64_probe": fp64,
             "roofline_fused_encrypt": roofs.get("encrypt"),
+            "encrypt_routes_alone": {"single_pass_ms": routes["single_pass"]["ms"], "single_pass_launches": routes["single_pass"]["launches"],
+                                     "two_pass_ms": routes["two_pass"]["ms"], "two_pass_launches": routes["two_pass"]["launches"],
+                                     "ciphertexts_equal": bool(routes_equal),
+                                     "frames": FRAMES, "note": "one encrypt_frames call of the clip on a fresh stream each"},
             "kernels": kern,
             "kernel_roofs": roofs,
             "cpu_baseline": cpu,

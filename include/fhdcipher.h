@@ -310,6 +310,21 @@ int fhd_permute_decrypt(const uint8_t *src, uint8_t *dst, uint32_t height, uint3
 uint32_t fhd_strip_width(uint32_t height, uint32_t width, uint32_t channels);
 int fhd_set_strip_width(uint32_t height, uint32_t width, uint32_t channels, uint32_t P);
 
+/* Route of the encryption's confusion + XOR (Sec. II-C), bit-identical either
+ * way, process-wide.  FHD_ROUTE_TWO_PASS (default): a row pass (row
+ * rotations, whole rows staged in shared memory) writes the row-rotated frame
+ * to scratch, then a column pass (full-height strips in shared memory)
+ * rotates its columns and XORs with B.  FHD_ROUTE_SINGLE_PASS: one gather
+ * pass -- each CTA builds a full-height strip of the row-rotated frame from the
+ * source rows at their offsets, rotates its columns in shared memory and
+ * writes it XORed with B, so the row-rotated frame never reaches memory (one
+ * frame read, B read and one frame written) -- for batches of interleaved RGB
+ * frames with width % 16 == 0, strip widths 16, 32 or 64 and 16-byte aligned
+ * buffers, the two passes otherwise.  Decryption always runs its two passes.
+ * Returns FHD_ERR_INVALID_ARG for another value. */
+enum { FHD_ROUTE_TWO_PASS = 0, FHD_ROUTE_SINGLE_PASS = 1 };
+int fhd_set_encrypt_route(int route);
+
 /* ---- Instrumentation (not part of the cipher). ---- */
 
 /* SM partition (CUDA green contexts, on by default where the device and

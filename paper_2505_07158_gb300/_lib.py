@@ -38,7 +38,7 @@ EXPORTS = (
     "decrypt_frames_split", "encrypt_frames_split", "cipher_profile_spans", "cipher_set_partition",
     "cipher_get_partition", "cipher_set_layout", "fhd_stats_histogram", "fhd_stats_npcr_uaci",
     "fhd_stats_correlation", "fhd_stats_local_entropy", "encrypt_frames_sched", "decrypt_frames_sched",
-    "fhd_frame_digest_tree", "fhd_fp64_probe",
+    "fhd_frame_digest_tree", "fhd_fp64_probe", "fhd_set_encrypt_route",
 )
 KERNEL_KINDS = ("sha", "master", "keystream", "encrypt", "decrypt")
 
@@ -134,6 +134,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "cipher_verify_frames": (i32, [P, u32, P, P, P]),
             "fhd_frame_scratch_bytes": (u64, [u32, u32, u32, u32]),
             "fhd_fp64_probe": (i32, [u32, u32, P, ctypes.POINTER(u64), P]),
+            "fhd_set_encrypt_route": (i32, [i32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -477,6 +478,15 @@ def fhd_stats_local_entropy(frames: torch.Tensor, blocks: torch.Tensor, block: i
     _check(load().fhd_stats_local_entropy(_vp(f), n, h, w, c, _vp(blocks), blocks.shape[1], block, _vp(out),
                                           _vp(status), _stream_ptr(stream)))
     return out, status
+
+
+ROUTES = {"two_pass": 0, "single_pass": 1}
+
+
+def fhd_set_encrypt_route(route: str = "two_pass"):
+    """Encryption's confusion + XOR: "two_pass" (row pass + column pass, the default) or "single_pass" (one
+    gather pass where the batch allows it)."""
+    _check(load().fhd_set_encrypt_route(ROUTES[route]))
 
 
 def fhd_fp64_probe(warps_per_subpartition: int, iters: int, sink: torch.Tensor, stream=None) -> int:

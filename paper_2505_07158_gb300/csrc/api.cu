@@ -817,6 +817,11 @@ int cipher_profile_spans(fhd_cipher *c, void *origin, uint32_t cap, int32_t *kin
 
 uint64_t fhd_launch_count(void) { return g_launches.load(); }
 
+int fhd_set_encrypt_route(int route) {
+    if (fhd::set_encrypt_route(route) != 0) return fail(nullptr, FHD_ERR_INVALID_ARG, "route must be FHD_ROUTE_TWO_PASS or FHD_ROUTE_SINGLE_PASS");
+    return FHD_OK;
+}
+
 int fhd_fp64_probe(uint32_t warps_per_subpartition, uint32_t iters, double *sink, uint64_t *lane_ops, void *stream) {
     if (!sink || !lane_ops) return fail(nullptr, FHD_ERR_INVALID_ARG, "null argument");
     if (warps_per_subpartition < 1 || warps_per_subpartition > 8)

@@ -106,5 +106,6 @@ cudaError_t permute_prepare();   // opt in to large dynamic shared memory
 cudaError_t launch_fp64_probe(uint32_t warps_per_subpartition, uint32_t iters, double *sink, uint64_t *lane_ops,
                               cudaStream_t s);
 int set_strip_override(uint32_t h, uint32_t w, uint32_t C, uint32_t P);
+int set_encrypt_route(int route);   // FHD_ROUTE_TWO_PASS or FHD_ROUTE_SINGLE_PASS; -1 on a bad value
 
 }  // namespace fhd

@@ -79,7 +79,7 @@ __device__ __forceinline__ uint32_t strip_vec(uint64_t rowB, uint32_t P, uint32_
 // Column pass.  Encrypt: S[(i + s_v) mod h][q] = G[i][q]; E = S ^ B.
 // Decrypt: S[(i - s_v) mod h][q] = (E ^ B)[i][q]; G = S.
 template <bool kEnc>
-__global__ void __launch_bounds__(kStripThreads, 1) strip_kernel(const __grid_constant__ Batch b, uint32_t cta_base) {
+__global__ void __launch_bounds__(kStripThreads, 2) strip_kernel(const __grid_constant__ Batch b, uint32_t cta_base) {
     extern __shared__ __align__(16) uint8_t smem[];
     const uint32_t cta = cta_base + blockIdx.x;
     const FrameDesc &fd = b.f[find_frame<false>(b, cta)];
@@ -365,6 +365,227 @@ __global__ void __launch_bounds__(kRowThreads) row_kernel(const __grid_constant_
     }
 }
 
+// Single-pass encryption (row rotation, column rotation and XOR in one kernel) for interleaved RGB frames
+// with w % 16 == 0, strip widths P in {16, 32, 64} and 16-byte aligned buffers.  A CTA owns a full-height
+// strip of P pixel columns of the output.
+//
+// Phase 1 builds the strip of G (the row-rotated frame) directly from F.  For source row i' and channel c,
+// the P output plane bytes of the strip are the rotation of a window of P/4 + 1 plane words of F's
+// channel-c plane at the row's offset (mod w); in the interleaved row those are 12 (P/4 + 1) consecutive
+// bytes (mod the row length).  Each warp takes a few source rows at a time: its lanes copy the rows'
+// 3 windows into a per-warp staging buffer as 16-byte chunks (coalesced loads of whole sectors, the
+// window rounded out to 16-byte boundaries), issued one iteration ahead into registers; then each unit --
+// two plane words, eight pixels of channel c -- reads its three plane words' interleaved words from the
+// buffer, deinterleaves them with byte permutes, makes its eight rotated bytes with two funnel shifts, and
+// stores each byte into its vertically rotated row of the shared strip, S[(i' + s_v(j, c)) mod h][j, c]
+// (Algo 5).  Phase 2 streams the strip out row by row XORed with B (Algo 6) in 16-byte loads and
+// stores.  DRAM traffic is one read of F and B and one write of E: G never exists in memory.
+constexpr int kGatherWarps = 12;
+constexpr int kGatherThreads = 32 * kGatherWarps;
+
+template <int P>
+struct GatherShape {
+    static constexpr uint32_t G4 = P / 4;                             // plane words per strip row and channel
+    static constexpr uint32_t G2 = P / 8;                             // units per window
+    static constexpr uint32_t RW = 32 / (3 * G2);                     // source rows per warp and iteration
+    static constexpr uint32_t NW = 3 * RW;                            // windows per warp and iteration
+    static constexpr uint32_t NC = (12 * (G4 + 1) + 12 + 15) / 16;    // 16-byte chunks per window (bound)
+    static constexpr uint32_t NCH = NW * NC;                          // chunks per warp and iteration
+    static constexpr uint32_t CPL = (NCH + 31) / 32;                  // chunks per lane
+};
+
+// Shared memory of the gather route for a strip of height h and width P: the strip, the per-warp staging
+// buffers and the row-rotation table.
+__host__ __device__ constexpr size_t gather_stage_bytes(uint32_t P) {
+    return (size_t)kGatherWarps * 16 *
+           (P == 16 ? GatherShape<16>::NCH : P == 32 ? GatherShape<32>::NCH : GatherShape<64>::NCH);
+}
+
+__device__ __forceinline__ uint32_t plane_word(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t s1, uint32_t s2) {
+    return __byte_perm(__byte_perm(w0, w1, s1), w2, s2);
+}
+
+// Row rotation of a channel row with distance d for the gather: the source window of output plane word g
+// starts at plane word (g + du) mod W4 and the four rotated bytes are the funnel shift by fs (1..32) of
+// that plane word and the next.
+struct RowRot {
+    uint32_t du, fs;
+};
+__device__ __forceinline__ RowRot row_rot(uint32_t d, uint32_t w, const FastMod &modW8) {
+    const uint32_t sh = modW8.mod(d);
+    const uint32_t s0 = w - 1 - (sh >> 3);   // first source pixel of output pixel 0: (-a - 1) mod w
+    return {s0 >> 2, 8 * (s0 & 3) + 8 - (sh & 7)};
+}
+
+template <int P>
+__device__ __forceinline__ void gather_phase1(const FrameDesc &fd, uint32_t j0, uint32_t Pe, uint8_t *S,
+                                              uint8_t *stage_all, const uint16_t *tab) {
+    using GS = GatherShape<P>;
+    const uint32_t h = fd.h, w = fd.w, rowB = 3 * w, W4 = w >> 2, RP = 3 * P, hRP = h * RP;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint4 *stage = reinterpret_cast<uint4 *>(stage_all) + warp * GS::NCH;
+    const FastMod modH(h), modW8(8 * w);
+    const uint32_t Ge2 = Pe >> 3;
+    // window lane (lane < NW): window `lane` of an iteration is source row base + lane / 3, channel lane % 3
+    const uint32_t wr = lane / 3, wc = lane - 3 * wr;
+    // unit lane (lane < NW * G2): window lane / G2, unit g of it
+    const uint32_t uwi = lane / GS::G2, g = lane - uwi * GS::G2;
+    const uint32_t ur = uwi / 3, c = uwi - 3 * ur;
+    const bool unit = lane < GS::NW * GS::G2 && g < Ge2;
+    const uint32_t s1 = c == 0 ? 0x0630u : c == 1 ? 0x0741u : 0x0052u;
+    const uint32_t s2 = c == 0 ? 0x5210u : c == 1 ? 0x6210u : 0x7410u;
+    uint32_t ab[8];   // strip offset of byte m of source row 0: its rotated row s_v, times RP, plus its column
+#pragma unroll
+    for (int m = 0; m < 8; ++m)
+        ab[m] = (unit ? modH.mod(fd.D[3ull * h + (uint64_t)c * w + j0 + 8 * g + m]) : 0) * RP + (8 * g + m) * 3 + c;
+    const uint32_t rows_per_it = GS::RW * kGatherWarps;
+    const uint32_t iters = (h + rows_per_it - 1) / rows_per_it;
+    const uint8_t *src = fd.src;
+
+    // Window parameters of iteration it (window lanes): aligned start A of the window in its row, the
+    // offset of the window's first plane word past A, the funnel shift.
+    auto params = [&](uint32_t it, uint32_t &A, uint32_t &off, uint32_t &fs) {
+        const uint32_t i = (it * kGatherWarps + warp) * GS::RW + wr;
+        A = off = 0;
+        fs = 32;
+        if (lane < GS::NW && i < h) {
+            RowRot r;
+            if (tab) {
+                const uint32_t v = tab[wc * h + i];
+                r.du = v >> 5;
+                r.fs = (v & 31) + 1;
+            } else {
+                r = row_rot(fd.D[(uint64_t)wc * h + i], w, modW8);
+            }
+            uint32_t us = (j0 >> 2) + r.du;
+            us = us >= W4 ? us - W4 : us;
+            const uint32_t b0 = 12 * us;
+            A = b0 & ~15u;
+            off = b0 - A;
+            fs = r.fs;
+        }
+    };
+    // Chunk k of this lane in an iteration: window cw[k] (its row cr[k] within the iteration's rows), byte
+    // 16 ck[k] of the window; fixed per lane.
+    uint32_t cw[GS::CPL], cr[GS::CPL], ck16[GS::CPL];
+#pragma unroll
+    for (uint32_t k = 0; k < GS::CPL; ++k) {
+        const uint32_t q = lane + 32 * k;
+        const uint32_t wi = q < GS::NCH ? q / GS::NC : 0;
+        cw[k] = wi;
+        cr[k] = q < GS::NCH ? wi / 3 : h;   // row h: never loaded
+        ck16[k] = 16 * (q - wi * GS::NC);
+    }
+    const bool short_row = 16 * GS::NC > rowB;   // the window may wrap around the row end more than once
+    auto fetch = [&](uint32_t it, uint32_t A, uint4 (&reg)[GS::CPL]) {
+        const uint32_t base = (it * kGatherWarps + warp) * GS::RW;
+#pragma unroll
+        for (uint32_t k = 0; k < GS::CPL; ++k) {
+            const uint32_t Aw = __shfl_sync(0xffffffffu, A, cw[k]);
+            const uint32_t i = base + cr[k];
+            reg[k] = make_uint4(0, 0, 0, 0);
+            if (i < h) {
+                uint32_t o = Aw + ck16[k];
+                o = o >= rowB ? o - rowB : o;
+                if (short_row)
+                    while (o >= rowB) o -= rowB;
+                // F rows serve several strips: keep them in L2
+                reg[k] = __ldcg(reinterpret_cast<const uint4 *>(src + i * rowB + o));
+            }
+        }
+    };
+    uint32_t A, off, fs;
+    uint4 reg[GS::CPL];
+    params(0, A, off, fs);
+    fetch(0, A, reg);
+    for (uint32_t it = 0; it < iters; ++it) {
+        // the staging buffer takes iteration it's chunks once the previous iteration has read it
+        __syncwarp();
+#pragma unroll
+        for (uint32_t k = 0; k < GS::CPL; ++k)
+            if (lane + 32 * k < GS::NCH) stage[lane + 32 * k] = reg[k];
+        const uint32_t cur_off = off, cur_fs = fs;
+        if (it + 1 < iters) {   // next iteration's window parameters and chunk loads, in flight meanwhile
+            params(it + 1, A, off, fs);
+            fetch(it + 1, A, reg);
+        }
+        __syncwarp();
+        const uint32_t uoff = __shfl_sync(0xffffffffu, cur_off, uwi < GS::NW ? uwi : 0);
+        const uint32_t ufs = __shfl_sync(0xffffffffu, cur_fs, uwi < GS::NW ? uwi : 0);
+        const uint32_t i = (it * kGatherWarps + warp) * GS::RW + ur;
+        if (unit && i < h) {
+            const uint32_t *wd = reinterpret_cast<const uint32_t *>(
+                reinterpret_cast<const uint8_t *>(stage + uwi * GS::NC) + uoff + 24 * g);
+            const uint32_t x0 = plane_word(wd[0], wd[1], wd[2], s1, s2);
+            const uint32_t x1 = plane_word(wd[3], wd[4], wd[5], s1, s2);
+            const uint32_t x2 = plane_word(wd[6], wd[7], wd[8], s1, s2);
+            const uint32_t q0 = __funnelshift_rc(x0, x1, ufs);
+            const uint32_t q1 = __funnelshift_rc(x1, x2, ufs);
+            const uint32_t iRP = i * RP;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                uint32_t a = iRP + ab[m];
+                a = a >= hRP ? a - hRP : a;
+                S[a] = (uint8_t)((m < 4 ? q0 : q1) >> (8 * (m & 3)));
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kGatherThreads, 2) gather_encrypt_kernel(const __grid_constant__ Batch b,
+                                                                           uint32_t cta_base, int use_tab) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const uint32_t cta = cta_base + blockIdx.x;
+    const FrameDesc &fd = b.f[find_frame<false>(b, cta)];
+    const uint32_t h = fd.h, w = fd.w, P = fd.P;
+    const uint32_t j0 = (cta - fd.cta0) * P;
+    const uint32_t Pe = min(P, w - j0);
+    const uint32_t RP = 3 * P, QC = 3 * Pe, rowB = 3 * w;
+    const uint32_t t = threadIdx.x;
+    uint8_t *S = smem;
+    uint8_t *stage = smem + (((size_t)h * RP + 15) & ~(size_t)15);
+    uint16_t *tab = use_tab ? reinterpret_cast<uint16_t *>(stage + gather_stage_bytes(P)) : nullptr;
+    if (tab) {   // [c * h + i] = du << 5 | (fs - 1); du < W4 <= 1024
+        const FastMod modW8(8 * w);
+        for (uint32_t k = t; k < 3 * h; k += kGatherThreads) {
+            const RowRot r = row_rot(fd.D[k], w, modW8);
+            tab[k] = (uint16_t)((r.du << 5) | (r.fs - 1));
+        }
+        __syncthreads();
+    }
+    if (P == 16) gather_phase1<16>(fd, j0, Pe, S, stage, tab);
+    else if (P == 32) gather_phase1<32>(fd, j0, Pe, S, stage, tab);
+    else gather_phase1<64>(fd, j0, Pe, S, stage, tab);
+    __syncthreads();
+
+    // ---- phase 2: E = S ^ B, row by row, 16-byte vectors
+    const uint32_t nv = QC / 16;
+    const uint32_t RT = kGatherThreads / nv;
+    if (t >= nv * RT) return;
+    const uint32_t tv = t % nv, tr = t / nv;
+    const uint64_t base = (uint64_t)j0 * 3 + 16 * tv;
+    for (uint32_t ib = tr; ib < h; ib += kRowsV * RT) {
+        uint4 v[kRowsV], k4[kRowsV];
+#pragma unroll
+        for (int k = 0; k < kRowsV; ++k) {
+            const uint32_t i = ib + k * RT;
+            if (i < h) {
+                v[k] = *reinterpret_cast<const uint4 *>(S + (size_t)i * RP + 16 * tv);
+                k4[k] = __ldcs(reinterpret_cast<const uint4 *>(fd.B + (uint64_t)i * rowB + base));
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kRowsV; ++k) {
+            const uint32_t i = ib + k * RT;
+            if (i < h) {
+                uint4 o = v[k];
+                o.x ^= k4[k].x; o.y ^= k4[k].y; o.z ^= k4[k].z; o.w ^= k4[k].w;
+                __stcs(reinterpret_cast<uint4 *>(fd.dst + (uint64_t)i * rowB + base), o);
+            }
+        }
+    }
+}
+
 }  // namespace
 
 size_t strip_smem_bytes(uint32_t h, uint32_t P, uint32_t C) { return ((size_t)h * P * C + 15) & ~(size_t)15; }
@@ -417,8 +638,9 @@ uint32_t strip_width(uint32_t h, uint32_t w, uint32_t C) {
 }
 
 cudaError_t permute_prepare() {
-    const void *fns[4] = {(const void *)strip_kernel<true>, (const void *)strip_kernel<false>,
-                          (const void *)row_kernel<true>, (const void *)row_kernel<false>};
+    const void *fns[5] = {(const void *)strip_kernel<true>, (const void *)strip_kernel<false>,
+                          (const void *)row_kernel<true>, (const void *)row_kernel<false>,
+                          (const void *)gather_encrypt_kernel};
     for (const void *f : fns) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
         if (e != cudaSuccess) return e;
@@ -426,10 +648,31 @@ cudaError_t permute_prepare() {
     return cudaSuccess;
 }
 
-// Encrypt: row pass then column pass; decrypt: column pass then row pass.
-// (Running the passes per group of frames, so that a group's intermediate
-// frames stay in L2 between its two passes, measured slower: the smaller
-// launches lose more to wave tails than L2 residency saves.)
+static int g_route = FHD_ROUTE_TWO_PASS;
+
+int set_encrypt_route(int route) {
+    if (route != FHD_ROUTE_TWO_PASS && route != FHD_ROUTE_SINGLE_PASS) return -1;
+    g_route = route;
+    return 0;
+}
+
+// The single pass takes a batch whose every frame is interleaved RGB with w % 16 == 0, a strip width that
+// is a multiple of 16 and 16-byte aligned source, destination and keystream.
+static bool single_pass_ok(const Batch &b) {
+    auto al = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    for (uint32_t k = 0; k < b.count; ++k) {
+        const FrameDesc &f = b.f[k];
+        if (f.C != 3 || f.w % 16 || (f.P != 16 && f.P != 32 && f.P != 64) || !al(f.src) || !al(f.dst) || !al(f.B))
+            return false;
+    }
+    return true;
+}
+
+// Encrypt: row pass then column pass, or one gather pass (FHD_ROUTE_SINGLE_PASS) where the batch allows
+// it; decrypt: column
+// pass then row pass.  (Running the two passes per group of frames, so that a group's intermediate
+// frames stay in L2 between its two passes, measured slower: the smaller launches lose more to wave
+// tails than L2 residency saves.)
 cudaError_t launch_permute(const Batch &b, bool encrypt, cudaStream_t s) {
     if (!b.count || !b.perm_ctas) return cudaSuccess;
     size_t ssm = 0, rsm = 0;
@@ -440,6 +683,26 @@ cudaError_t launch_permute(const Batch &b, bool encrypt, cudaStream_t s) {
         rsm = rsm > r ? rsm : r;
     }
     cudaError_t e;
+    if (encrypt && g_route == FHD_ROUTE_SINGLE_PASS && single_pass_ok(b)) {
+        // Strip + staging buffers, and the rotation table (3h 16-bit entries) where every frame's plane-word
+        // offsets fit in it and it costs no CTA per SM.
+        size_t gsm = 0, tsm = 0;
+        bool tab = true;
+        for (uint32_t k = 0; k < b.count; ++k) {
+            const FrameDesc &f = b.f[k];
+            const size_t g = strip_smem_bytes(f.h, f.P, f.C) + gather_stage_bytes(f.P);
+            gsm = gsm > g ? gsm : g;
+            tsm = tsm > g + 6ull * f.h ? tsm : g + 6ull * f.h;
+            tab = tab && f.w / 4 <= 1024;
+        }
+        constexpr size_t kSmPerSm = 233472, kReserved = 1024;
+        tab = tab && tsm <= kSmemLimit && kSmPerSm / (tsm + kReserved) >= kSmPerSm / (gsm + kReserved);
+        if (gsm <= kSmemLimit) {
+            gather_encrypt_kernel<<<b.perm_ctas, kGatherThreads, tab ? tsm : gsm, s>>>(b, 0, tab ? 1 : 0);
+            note_launch();
+            return cudaGetLastError();
+        }
+    }
     if (encrypt) {
         row_kernel<true><<<b.row_ctas, kRowThreads, rsm, s>>>(b, 0);
         note_launch();

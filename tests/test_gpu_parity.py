@@ -272,3 +272,78 @@ def test_receiver_side_verification():
     Hbad[0] ^= 0x80
     ok = dec.verify_frames([(rid, e, r, h) for e, r, h in zip(E, R, [H[0], H[1], Hbad])])
     assert host(ok).tolist() == [1, 0, 0]
+
+
+# ---- the single-pass encryption (gather route) against the two passes and the oracle ----
+
+GATHER_SHAPES = [(1, 16, 3), (2, 32, 3), (37, 48, 3), (64, 112, 3), (200, 320, 3), (480, 640, 3),
+                 (720, 1280, 3), (3, 4096, 3)]
+
+
+@pytest.mark.parametrize("shape", GATHER_SHAPES)
+@pytest.mark.parametrize("P", [0, 16, 32, 64, 128])
+def test_single_pass_encrypt_matches_two_passes_and_oracle(shape, P):
+    """Every strip width the single pass takes (0 = the built-in choice), full and tail strips
+    (w % P != 0), one-row and one-strip frames: bit-exact with the oracle and with the two-pass route."""
+    h, w, C = shape
+    if P and (h * P * C + 15) // 16 * 16 > 232448:
+        pytest.skip("strip does not fit shared memory")
+    F, D, B = _rand(h, w, C, seed=h + w + P)
+    ref = oracle.permute_encrypt(F, D, B)
+    if P:
+        fhd.fhd_set_strip_width(h, w, C, P)
+    try:
+        outs = {}
+        for route in ("single_pass", "two_pass"):
+            fhd.fhd_set_encrypt_route(route)
+            outs[route] = host(fhd.fhd_permute_encrypt(to_dev(F), d16(D), to_dev(B)))
+    finally:
+        fhd.fhd_set_encrypt_route("two_pass")
+        fhd.fhd_set_strip_width(h, w, C, 0)
+    assert np.array_equal(outs["single_pass"], ref)
+    assert np.array_equal(outs["two_pass"], ref)
+
+
+def test_single_pass_in_a_mixed_batch_of_streams():
+    """A batch whose frames all take the single pass (several sizes, strip widths and streams, chained
+    frames of one stream), and the same batch with one frame that does not (w % 16 != 0), which sends
+    the whole batch through the two passes: both equal the oracle streams."""
+    fhd.fhd_set_encrypt_route("single_pass")
+    try:
+        _mixed_batches_match_oracle()
+    finally:
+        fhd.fhd_set_encrypt_route("two_pass")
+
+
+@pytest.mark.parametrize("shape", [(1080, 1920, 3), (2160, 3840, 3)])
+def test_single_pass_encrypt_full_size(shape):
+    F, D, B = _rand(*shape, seed=sum(shape))
+    fhd.fhd_set_encrypt_route("single_pass")
+    try:
+        E = host(fhd.fhd_permute_encrypt(to_dev(F), d16(D), to_dev(B)))
+    finally:
+        fhd.fhd_set_encrypt_route("two_pass")
+    assert np.array_equal(E, oracle.permute_encrypt(F, D, B))
+
+
+def _mixed_batches_match_oracle():
+    for shapes in ([(48, 64, 3), (30, 96, 3), (16, 16, 3), (72, 160, 3)],
+                   [(48, 64, 3), (30, 96, 3), (20, 36, 3), (72, 160, 3)]):
+        keys = [si.key(900 + k) for k in range(3)]
+        c = fhd.Cipher(keys[0], n_workers=5)
+        sids = [c.open_stream(k) for k in keys]
+        refs = [oracle.Stream.from_key(k, n=5) for k in keys]
+        items, frames = [], []
+        for t, s in enumerate(shapes):
+            st = t % 3 if t < 3 else 0           # frames 0 and 3 are consecutive frames of stream 0
+            F = si.gradient_frame(*s, t=t, seed=31)
+            frames.append((st, F))
+            items.append((sids[st], to_dev(F), torch.empty(s, dtype=torch.uint8, device=dev()),
+                          torch.empty(32, dtype=torch.uint8, device=dev())))
+        c.encrypt_frames(items)
+        torch.cuda.synchronize()
+        for (st, F), it in zip(frames, items):
+            E_ref, H_ref = refs[st].encrypt(F)
+            assert bytes(host(it[3])) == H_ref
+            assert np.array_equal(host(it[2]), E_ref)
+        c.close()
