@@ -1,0 +1,328 @@
+// Device code of the Lorenz hyperchaotic iterations (Eq. (1), RK4) shared by the chaining and worker kernels
+// and the persistent batch kernel: the lane-packed RK4 steps, the reconstruction, LHCS_m of one stream and
+// one warp of worker pairs.  See chaos.cu for the design.
+#pragma once
+#include "common.cuh"
+#include "sha256_core.cuh"
+
+namespace fhd {
+namespace {
+
+constexpr double kSigma = 10.0;
+constexpr double kRho = 28.0;
+constexpr double kBeta = 8.0 / 3.0;
+
+struct Rk4 {
+    double h, hh, h6;
+};
+
+constexpr int kChainsPerWarp = 6;   // lanes 0..23
+constexpr int kPairsPerWarp = 3;
+constexpr int kLaneZero = 24;       // holds +0
+constexpr int kLaneOne = 25;        // holds 1.0
+
+// Per-lane operand sources and coefficients of the component template.
+struct LaneRole {
+    double Pb, B2, kS;
+    int sPa, sPc, sQa, sQb, sP2;
+};
+
+__device__ __forceinline__ LaneRole lane_role(int lane, double gamma) {
+    LaneRole r;
+    const int v = lane & 3, base = lane & ~3;
+    if (lane >= 4 * kChainsPerWarp) {   // constant lanes: every operand +0, k = +0
+        r.Pb = r.B2 = r.kS = 0.0;
+        r.sPa = r.sPc = r.sQa = r.sQb = r.sP2 = kLaneZero;
+        return r;
+    }
+    r.Pb = v == 0 ? 1.0 : v == 1 ? kRho : v == 2 ? kBeta : gamma;
+    r.B2 = v == 0 ? kSigma : v == 2 ? -1.0 : 1.0;
+    r.kS = (v == 0 || v == 2) ? 1.0 : -1.0;
+    r.sPa = base + (v == 0 ? 1 : v == 1 ? 0 : v);                 // Y, X, Z, W
+    r.sPc = v == 0 ? base : kLaneZero;                            // X, +0, +0, +0
+    r.sQa = base + (v == 0 ? 3 : v == 3 ? 1 : 0);                 // W, X, X, Y
+    r.sQb = v == 0 ? kLaneOne : base + (v == 2 ? 1 : 2);          // 1, Z, Y, Z
+    r.sP2 = v == 1 ? base + 1 : kLaneZero;                        // +0, Y, +0, +0
+    return r;
+}
+
+// Initial value of a lane: the chain variable, or the constant a constant lane holds.
+__device__ __forceinline__ double lane_init(int lane, double chain_value) {
+    return lane < 4 * kChainsPerWarp ? chain_value : (lane == kLaneOne ? 1.0 : 0.0);
+}
+
+// One RK4 step of the warp's six chains; s is this lane's variable.  All 32
+// lanes of the warp must call it together.
+__device__ __forceinline__ void rk4_step_lanes(double &s, const LaneRole &r, const Rk4 &c) {
+    double tin = s, acc = 0.0;
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+        const double Pa = __shfl_sync(0xffffffffu, tin, r.sPa);
+        const double Pc = __shfl_sync(0xffffffffu, tin, r.sPc);
+        const double Qa = __shfl_sync(0xffffffffu, tin, r.sQa);
+        const double Qb = __shfl_sync(0xffffffffu, tin, r.sQb);
+        const double P2 = __shfl_sync(0xffffffffu, tin, r.sP2);
+        const double p = __fma_rn(Pa, r.Pb, -Pc);
+        const double q = __fma_rn(Qa, Qb, -0.0);
+        const double p2 = __fma_rn(p, r.B2, -P2);
+        const double k = __fma_rn(q, r.kS, p2);
+        if (st < 3) {
+            tin = __dadd_rn(s, __dmul_rn(st == 2 ? c.h : c.hh, k));
+            acc = st == 0 ? k : __fma_rn(k, 2.0, acc);
+        } else {
+            acc = __dadd_rn(acc, k);
+            s = __dadd_rn(s, __dmul_rn(c.h6, acc));
+        }
+    }
+}
+
+// The same step with eight chains per warp (all 32 lanes carry variables, so
+// no lane holds a constant): three shuffles per stage, and the operands that
+// are a variable on some lanes and a constant on others are selected:
+//   v = x: p = fma(Y, 1, -X), q = fma(W, 1, -0);  v = y: p = fma(X, rho, -0), p2 = fma(p, 1, -Y);
+//   v = z: p = fma(Z, beta, -0), p2 = -p;          v = w: p = fma(W, gamma, -0);
+// q = X Z, X Y, Y Z for y, z, w.  The first fma's shuffled operand is a factor
+// on every lane and its addend a select on the lane's own value (-X or -0),
+// so no select sits between the shuffles and the first fma.  Fewer binary64
+// instructions per chain step (27 per eight chains), a longer step (selects).
+struct LaneRole8 {
+    double Pb, B2, kS;
+    int s1, s2, s3;
+    bool vx, vy;
+};
+
+__device__ __forceinline__ LaneRole8 lane_role8(int lane, double gamma) {
+    LaneRole8 r;
+    const int v = lane & 3, base = lane & ~3;
+    r.Pb = v == 0 ? 1.0 : v == 1 ? kRho : v == 2 ? kBeta : gamma;
+    r.B2 = v == 0 ? kSigma : v == 2 ? -1.0 : 1.0;
+    r.kS = (v == 0 || v == 2) ? 1.0 : -1.0;
+    r.s1 = base + (v == 0 ? 1 : v == 1 ? 0 : v);           // Y, X, Z, W
+    r.s2 = base + (v == 0 ? 3 : v == 3 ? 1 : 0);           // W, X, X, Y
+    r.s3 = base + ((v == 0 || v == 2) ? 1 : 2);            // Y, Z, Y, Z
+    r.vx = v == 0;
+    r.vy = v == 1;
+    return r;
+}
+
+// `after_fetch(s)` runs once the first stage's operands are fetched, with the state at the start of the
+// step: the worker kernel emits the previous step's stream bytes there, so that their integer work follows
+// the shuffles that start this step instead of delaying them.
+template <class F>
+__device__ __forceinline__ void rk4_step_lanes8(double &s, const LaneRole8 &r, const Rk4 &c, F &&after_fetch) {
+    double tin = s, acc = 0.0;
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+        const double a = __shfl_sync(0xffffffffu, tin, r.s1);
+        const double b = __shfl_sync(0xffffffffu, tin, r.s2);
+        const double d = __shfl_sync(0xffffffffu, tin, r.s3);
+        if (st == 0) after_fetch(tin);
+        const double Pc = r.vx ? tin : 0.0;
+        const double Qb = r.vx ? 1.0 : d;
+        const double P2 = r.vy ? tin : 0.0;
+        const double p = __fma_rn(a, r.Pb, -Pc);
+        const double q = __fma_rn(b, Qb, -0.0);
+        const double p2 = __fma_rn(p, r.B2, -P2);
+        const double k = __fma_rn(q, r.kS, p2);
+        if (st < 3) {
+            tin = __dadd_rn(s, __dmul_rn(st == 2 ? c.h : c.hh, k));
+            acc = st == 0 ? k : __fma_rn(k, 2.0, acc);
+        } else {
+            acc = __dadd_rn(acc, k);
+            s = __dadd_rn(s, __dmul_rn(c.h6, acc));
+        }
+    }
+}
+
+// Sec. II-A, Fig. 1a: reconstruct one initial condition from 8 digest bytes
+// (two for the integer part mod u, six for the 48-bit fraction), v by
+// magnitude; non-finite or |v| >= 2^52 contributes 0 and 0.
+__device__ __forceinline__ double reconstruct(double v, const uint8_t *hb, uint32_t u) {
+    double a = fabs(v);
+    unsigned long long I = 0, F48 = 0;
+    if (a < 0x1p52) {
+        I = __double2ull_rz(a);
+        double F = __dsub_rn(a, __ull2double_rn(I));
+        F48 = __double2ull_rz(__dmul_rn(F, 0x1p48));
+    }
+    unsigned long long hi16 = (unsigned long long)hb[0] | ((unsigned long long)hb[1] << 8);
+    unsigned long long h48 = 0;
+#pragma unroll
+    for (int i = 5; i >= 0; --i) h48 = (h48 << 8) | hb[2 + i];
+    unsigned long long ip = ((I & 0xffffull) ^ hi16) % u;
+    double fp = __dmul_rn(__ull2double_rn(F48 ^ h48), 0x1p-48);
+    return __dadd_rn(__ull2double_rn(ip), fp);
+}
+
+__device__ __forceinline__ bool finite(double x) { return isfinite(x); }
+
+// Reconstruct from (state, H), run LHCS_m 2n steps writing IR.  The chain
+// lives in lanes 0..3 of the warp (lane = variable); s is this lane's value.
+__device__ void master_frame(double &s, int lane, const LaneRole &role, const uint8_t *H_smem, const uint32_t *u,
+                             uint32_t n, const Rk4 &c, double *IR) {
+    if (lane < 4) s = reconstruct(s, H_smem + 8 * lane, u[lane]);
+    __syncwarp();
+    for (uint32_t t = 0; t < 2 * n; ++t) {
+        rk4_step_lanes(s, role, c);
+        if (lane < 4) IR[4 * t + lane] = s;
+    }
+}
+
+// Mask of the transmitted digest (masked transport, an option of this library; Sec. V sends the hashes
+// encrypted without giving the mechanism): M = SHA-256("FHDMASK1" || LE64(x) || LE64(y) || LE64(z) ||
+// LE64(w) || LE64(gamma)) of the chaining state before the frame, 48 bytes in one block.  M is returned as
+// the 8 little-endian words of its big-endian byte string, ready to XOR with the stored digest words.
+__device__ void digest_mask(double x, double y, double z, double w, double gamma, uint32_t M[8]) {
+    uint32_t wd[16];
+    wd[0] = 0x4648444Du;   // "FHDM"
+    wd[1] = 0x41534B31u;   // "ASK1"
+    const double v[5] = {x, y, z, w, gamma};
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(v[m]);
+        wd[2 + 2 * m] = __byte_perm((uint32_t)bits, 0, 0x0123);           // bytes 0..3, big-endian word
+        wd[3 + 2 * m] = __byte_perm((uint32_t)(bits >> 32), 0, 0x0123);   // bytes 4..7
+    }
+    wd[12] = 0x80000000u;
+    wd[13] = 0u;
+    wd[14] = 0u;
+    wd[15] = 48u * 8u;
+    uint32_t h[8];
+    sha256_init(h);
+    sha256_compress(h, wd);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) M[q] = __byte_perm(h[q], 0, 0x0123);
+}
+
+// K2b worker geometry of one frame.
+struct WorkerSlice {
+    uint64_t d0, nd, b0, nb;
+};
+__device__ __forceinline__ WorkerSlice worker_slice(uint64_t LD, uint64_t LB, uint32_t n, uint32_t p) {
+    WorkerSlice w;
+    w.d0 = (uint64_t)(((unsigned __int128)LD * p) / n);
+    w.nd = (uint64_t)(((unsigned __int128)LD * (p + 1)) / n) - w.d0;
+    w.b0 = (uint64_t)(((unsigned __int128)LB * p) / n);
+    w.nb = (uint64_t)(((unsigned __int128)LB * (p + 1)) / n) - w.b0;
+    return w;
+}
+
+// Bytes of one step: the pair's XOR of the 6 low mantissa bytes of each
+// variable; this lane writes its half (3 bytes) at stream position pos0 on.
+__device__ __forceinline__ void emit_bytes(double s, bool active, uint64_t pos0, uint64_t need, uint64_t ndb, int half,
+                                           uint8_t *Dbytes, uint8_t *Bp) {
+    const unsigned long long mine = (unsigned long long)__double_as_longlong(s) & 0xffffffffffffull;
+    const unsigned long long x = mine ^ __shfl_xor_sync(0xffffffffu, mine, 4);
+    if (active && pos0 < need) {
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) {
+            const uint64_t pos = pos0 + half + bb;
+            const uint8_t byte = (uint8_t)(x >> (8 * (half + bb)));
+            if (pos < ndb) Dbytes[pos] = byte;
+            else if (pos < need) Bp[pos - ndb] = byte;
+        }
+    }
+}
+
+// Worker pairs pg * kPairs .. pg * kPairs + kPairs - 1 of frame fd (Algorithm 2), run by one warp (lane = its
+// lane): lane 4c + v holds variable v of chain c, chains 2q and 2q + 1 are pair q, so the partner of a lane
+// is lane ^ 4.  Every warp of the frame runs the frame's uniform trip count (its longest slice).
+template <int kPairs>
+__device__ void keystream_warp(const FrameDesc &fd, uint32_t n, const Rk4 &c, uint32_t pg, int lane) {
+    const int v = lane & 3, ch = lane >> 2;
+    const uint32_t p = pg * kPairs + (ch >> 1);
+    const bool active = lane < 8 * kPairs && p < n;
+    const uint64_t LD = (uint64_t)fd.C * (fd.h + fd.w);
+    const uint64_t LB = fd.N;
+    WorkerSlice ws{0, 0, 0, 0};
+    if (active) ws = worker_slice(LD, LB, n, p);
+    const uint64_t need = 2 * ws.nd + ws.nb;
+    // Uniform trip count: the longest slice of the frame.
+    const uint64_t need_max = 2 * ((LD + n - 1) / n) + (LB + n - 1) / n;
+    const uint64_t T = (need_max + 23) / 24;
+    const double chain_value = active ? fd.IR[4 * (2 * p + (ch & 1)) + v] : 0.0;
+    uint8_t *Dbytes = reinterpret_cast<uint8_t *>(fd.D) + 2 * ws.d0;
+    uint8_t *Bp = fd.B + ws.b0;
+    const uint64_t ndb = 2 * ws.nd;
+    const int half = (ch & 1) * 3;
+    if (kPairs == kPairsPerWarp) {
+        const LaneRole role = lane_role(lane, fd.gamma);
+        double s = lane_init(lane, chain_value);
+        for (uint64_t t = 0; t < T; ++t) {
+            rk4_step_lanes(s, role, c);
+            emit_bytes(s, active, 24 * t + 6 * v, need, ndb, half, Dbytes, Bp);
+        }
+    } else {
+        // The bytes of step t (the state after it) are emitted during step t + 1, and the last step's after
+        // the loop: the same bytes at the same positions.
+        const LaneRole8 role = lane_role8(lane, fd.gamma);
+        double s = chain_value;
+        for (uint64_t t = 0; t < T; ++t) {
+            rk4_step_lanes8(s, role, c, [&](double prev) {
+                if (t) emit_bytes(prev, active, 24 * (t - 1) + 6 * v, need, ndb, half, Dbytes, Bp);
+            });
+        }
+        if (T) emit_bytes(s, active, 24 * (T - 1) + 6 * v, need, ndb, half, Dbytes, Bp);
+    }
+}
+
+// LHCS_m of stream group g of a batch (Algorithm 1), one warp (lane = its lane), the group's frames in call
+// order: reconstruct from the chaining state and the frame's digest, 2n RK4 steps into the frame's IR, and
+// chain on.  before(f) runs on every lane before frame f and may refuse it (false ends the group and keeps
+// the state of the frames done); after(f) runs once frame f's iterates are written.  H is 32 bytes of
+// shared memory of this warp.
+template <class BatchT, class Before, class After>
+__device__ void master_stream(const BatchT &b, uint32_t g, StreamState *states, unsigned *status, uint8_t *H,
+                              int lane, Before before, After after) {
+    const Rk4 c{b.hstep, b.hhalf, b.hsixth};
+    const uint32_t first = b.group_begin[g], last = b.group_begin[g + 1];
+    const uint32_t slot = b.f[b.order[first]].slot;
+    StreamState *st = states + slot;
+    const double gamma = b.f[b.order[first]].gamma;
+    const LaneRole role = lane_role(lane, gamma);
+    double s = lane_init(lane, lane < 4 ? st->v[lane] : 0.0);
+    uint32_t done = 0;
+    for (uint32_t k = first; k < last; ++k) {
+        const FrameDesc &fd = b.f[b.order[k]];
+        if (!before(b.order[k])) break;   // a dependency of the frame did not arrive (a bounded wait gave up)
+        if (lane < 8)   // the frame's digest: folded by the digest stage, or the transmitted one
+            reinterpret_cast<uint32_t *>(H)[lane] = reinterpret_cast<const uint32_t *>(fd.digest)[lane];
+        __syncwarp();
+        if (b.digest_masked) {
+            // Lanes 0..3 hold the chaining state before this frame.  Encryption transmits H xor M (the
+            // keystream still derives from H); decryption unmasks the transmitted digest and leaves H in
+            // the frame's digest for the receiver-side check.
+            const double x = __shfl_sync(0xffffffffu, s, 0), y = __shfl_sync(0xffffffffu, s, 1);
+            const double z = __shfl_sync(0xffffffffu, s, 2), w = __shfl_sync(0xffffffffu, s, 3);
+            if (lane == 0) {
+                uint32_t M[8];
+                digest_mask(x, y, z, w, gamma, M);
+                uint32_t *hw = reinterpret_cast<uint32_t *>(H);
+                uint32_t *dg = reinterpret_cast<uint32_t *>(fd.digest);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const uint32_t t = hw[q] ^ M[q];
+                    if (b.encrypt) {
+                        dg[q] = t;
+                    } else {
+                        hw[q] = t;
+                        dg[q] = t;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        master_frame(s, lane, role, H, b.u, b.n, c, fd.IR);
+        __syncwarp();
+        ++done;
+        after(b.order[k]);
+    }
+    if (lane < 4) {
+        st->v[lane] = s;
+        if (!finite(s)) atomicOr(status, kStatusNonFinite);
+        if (lane == 0) st->frames += done;
+    }
+}
+
+}  // namespace
+}  // namespace fhd

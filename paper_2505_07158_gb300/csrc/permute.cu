@@ -25,32 +25,13 @@
 // global access is a coalesced vector; the intermediate frame G lives in the
 // keystream scratch.  Decryption runs the column pass first (E ^ B scattered
 // to un-rotated rows) and then the row pass rotating right.
-#include "common.cuh"
+#include "permute_dev.cuh"
 
 namespace fhd {
 namespace {
 
 constexpr int kStripThreads = 512;
 constexpr int kRowThreads = 256;
-constexpr int kRowsV = 4;                 // row segments per batch of independent vector loads
-constexpr int kRowsW = 8;                 // strip rows per batch of independent word loads (column pass)
-constexpr size_t kSmemLimit = 232448;     // opt-in dynamic shared memory per CTA on sm_100/sm_103
-constexpr size_t kRowSmemTarget = 32768;  // row pass: bands of 2 rows at 1080p
-
-// n mod d for n < 2^16, 1 <= d <= 2^18, by one 64-bit multiply: with
-// M = floor(2^40/d) + 1 and e = M d - 2^40 in (0, d], n M / 2^40 exceeds n/d
-// by n e / (d 2^40) < 1/d, so its floor is floor(n/d).
-struct FastMod {
-    uint32_t d;
-    unsigned long long M;
-    __device__ __forceinline__ explicit FastMod(uint32_t dd) : d(dd), M((1ull << 40) / dd + 1) {}
-    __device__ __forceinline__ uint32_t mod(uint32_t n) const {
-        uint32_t q = (uint32_t)(((unsigned long long)n * M) >> 40);
-        return n - q * d;
-    }
-};
-
-// Last frame whose first CTA (strip or row numbering) is <= cta.
 template <bool kRow>
 __device__ __forceinline__ uint32_t find_frame(const Batch &b, uint32_t cta) {
     uint32_t lo = 0, hi = b.count;
@@ -61,308 +42,20 @@ __device__ __forceinline__ uint32_t find_frame(const Batch &b, uint32_t cta) {
     return lo;
 }
 
-__device__ __forceinline__ bool aligned(const void *p, uintptr_t a) {
-    return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0;
-}
-
-// Vector width (1, 4 or 16 bytes) usable for contiguous strip rows.
-__device__ __forceinline__ uint32_t strip_vec(uint64_t rowB, uint32_t P, uint32_t C, uint32_t Pe, const void *p0,
-                                              const void *p1, const void *p2) {
-    if (rowB % 16 == 0 && (P * C) % 16 == 0 && (Pe * C) % 16 == 0 && aligned(p0, 16) && aligned(p1, 16) &&
-        aligned(p2, 16))
-        return 16;
-    if (rowB % 4 == 0 && (P * C) % 4 == 0 && (Pe * C) % 4 == 0 && aligned(p0, 4) && aligned(p1, 4) && aligned(p2, 4))
-        return 4;
-    return 1;
-}
-
-// Column pass.  Encrypt: S[(i + s_v) mod h][q] = G[i][q]; E = S ^ B.
-// Decrypt: S[(i - s_v) mod h][q] = (E ^ B)[i][q]; G = S.
 template <bool kEnc>
 __global__ void __launch_bounds__(kStripThreads, 2) strip_kernel(const __grid_constant__ Batch b, uint32_t cta_base) {
     extern __shared__ __align__(16) uint8_t smem[];
     const uint32_t cta = cta_base + blockIdx.x;
     const FrameDesc &fd = b.f[find_frame<false>(b, cta)];
-    const uint32_t h = fd.h, w = fd.w, C = fd.C, P = fd.P;
-    const uint32_t j0 = (cta - fd.cta0) * P;
-    const uint32_t Pe = min(P, w - j0);
-    const uint32_t RP = P * C;
-    const uint32_t QC = Pe * C;
-    const uint64_t rowB = (uint64_t)w * C;
-    const uint64_t base = (uint64_t)j0 * C;
-    const uint8_t *src = kEnc ? fd.G : fd.src;
-    uint8_t *out = kEnc ? fd.dst : fd.G;
-    const uint16_t *Dv = fd.D + (uint64_t)C * h;
-    const FastMod modH(h);
-    uint8_t *S = smem;
-
-    // ---- phase 1: loads of the strip rows, bytes scattered to their rotated rows.  With 4-byte-aligned
-    // rows a lane owns one 32-bit word of the strip row (the lanes of a warp hold consecutive words), so
-    // in each byte store the lanes hit consecutive banks up to the row term 16 d (mod 32): at most two
-    // lanes share a bank.
-    const uint32_t vec = strip_vec(rowB, P, C, Pe, src, out, fd.B);
-    if (vec >= 4) {
-        const uint32_t nw = QC / 4;                    // words per strip row
-        const uint32_t RT = blockDim.x / nw;           // rows in parallel
-        if (threadIdx.x < nw * RT) {
-            const uint32_t j = threadIdx.x % nw, tr = threadIdx.x / nw;
-            uint32_t ht[4];   // row offset of each byte: s_v (encrypt) or h - s_v (decrypt)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint32_t q = 4 * j + k, jj = q / C, c = q - jj * C;
-                const uint32_t t = modH.mod(Dv[(uint64_t)c * w + j0 + jj]);
-                ht[k] = kEnc ? t : h - t;
-            }
-            const uint8_t *sp = src + base + 4 * j;
-            const uint8_t *bp = fd.B + base + 4 * j;
-            for (uint32_t ib = tr; ib < h; ib += kRowsW * RT) {
-                uint32_t e[kRowsW];
-#pragma unroll
-                for (int k = 0; k < kRowsW; ++k) {
-                    const uint32_t i = ib + k * RT;
-                    if (i < h) {
-                        e[k] = __ldcs(reinterpret_cast<const unsigned int *>(sp + (uint64_t)i * rowB));
-                        if (!kEnc) e[k] ^= __ldcs(reinterpret_cast<const unsigned int *>(bp + (uint64_t)i * rowB));
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < kRowsW; ++k) {
-                    const uint32_t i = ib + k * RT;
-                    if (i < h) {
-#pragma unroll
-                        for (int bb = 0; bb < 4; ++bb) {
-                            uint32_t d = i + ht[bb];
-                            d = d >= h ? d - h : d;
-                            S[(size_t)d * RP + 4 * j + bb] = (uint8_t)(e[k] >> (8 * bb));
-                        }
-                    }
-                }
-            }
-        }
-    } else {
-        const uint32_t RT = blockDim.x / QC;
-        if (threadIdx.x < QC * RT) {
-            const uint32_t q = threadIdx.x % QC, tr = threadIdx.x / QC;
-            const uint32_t jj = q / C, c = q - jj * C;
-            const uint32_t t = modH.mod(Dv[(uint64_t)c * w + j0 + jj]);
-            const uint32_t ht = kEnc ? t : h - t;
-            for (uint32_t i = tr; i < h; i += RT) {
-                const uint64_t o = (uint64_t)i * rowB + base + q;
-                uint8_t e = src[o];
-                if (!kEnc) e ^= fd.B[o];
-                uint32_t d = i + ht;
-                d = d >= h ? d - h : d;
-                S[(size_t)d * RP + q] = e;
-            }
-        }
-    }
-    __syncthreads();
-
-    // ---- phase 2: the strip leaves row by row (XORed with B when encrypting)
-    const uint32_t nv = QC / vec;
-    const uint32_t RT = blockDim.x / nv;
-    if (threadIdx.x >= nv * RT) return;
-    const uint32_t tv = threadIdx.x % nv, tr = threadIdx.x / nv;
-    if (vec == 16) {
-        for (uint32_t ib = tr; ib < h; ib += kRowsV * RT) {
-            uint4 g[kRowsV], k4[kRowsV];
-#pragma unroll
-            for (int k = 0; k < kRowsV; ++k) {
-                const uint32_t i = ib + k * RT;
-                if (i < h) {
-                    g[k] = *reinterpret_cast<const uint4 *>(S + (size_t)i * RP + 16 * tv);
-                    if (kEnc) k4[k] = __ldcs(reinterpret_cast<const uint4 *>(fd.B + (uint64_t)i * rowB + base + 16 * tv));
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < kRowsV; ++k) {
-                const uint32_t i = ib + k * RT;
-                if (i < h) {
-                    uint4 v = g[k];
-                    if (kEnc) { v.x ^= k4[k].x; v.y ^= k4[k].y; v.z ^= k4[k].z; v.w ^= k4[k].w; }
-                    uint4 *dstp = reinterpret_cast<uint4 *>(out + (uint64_t)i * rowB + base + 16 * tv);
-                    if (kEnc) __stcs(dstp, v); else *dstp = v;
-                }
-            }
-        }
-    } else if (vec == 4) {
-        for (uint32_t i = tr; i < h; i += RT) {
-            const uint64_t o = (uint64_t)i * rowB + base + 4 * tv;
-            uint32_t g = *reinterpret_cast<const uint32_t *>(S + (size_t)i * RP + 4 * tv);
-            if (kEnc) g ^= *reinterpret_cast<const uint32_t *>(fd.B + o);
-            *reinterpret_cast<uint32_t *>(out + o) = g;
-        }
-    } else {
-        for (uint32_t i = tr; i < h; i += RT) {
-            const uint64_t o = (uint64_t)i * rowB + base + tv;
-            uint8_t g = S[(size_t)i * RP + tv];
-            if (kEnc) g ^= fd.B[o];
-            out[o] = g;
-        }
-    }
+    strip_pass<kEnc>(fd, cta - fd.cta0, smem, threadIdx.x, blockDim.x, [] { __syncthreads(); });
 }
 
-// Row pass over a band of RB whole rows.  Encrypt: G = left rotation of each
-// channel row of F by s_h bits.  Decrypt: output = right rotation of each
-// channel row of G by s_h bits.
-//
-// Interleaved RGB rows with w % 4 == 0 take a planar route: a thread
-// produces one 4-pixel group (12 bytes): for each channel the two words of
-// the channel plane that hold its source bytes are deinterleaved from the
-// staged row with __byte_perm (the five source bytes sit in two adjacent
-// plane words), one 64-to-32-bit funnel shift by 8*(byte offset) + bit shift
-// gives the four rotated bytes, and the three channels' words are
-// interleaved back.  Other shapes take the byte-wise route.
 template <bool kEnc>
 __global__ void __launch_bounds__(kRowThreads) row_kernel(const __grid_constant__ Batch b, uint32_t cta_base) {
     extern __shared__ __align__(16) uint8_t smem[];
     const uint32_t cta = cta_base + blockIdx.x;
     const FrameDesc &fd = b.f[find_frame<true>(b, cta)];
-    const uint32_t h = fd.h, w = fd.w, C = fd.C, RB = fd.RB;
-    const uint32_t i0 = (cta - fd.rcta0) * RB;
-    const uint32_t nr = min(RB, h - i0);
-    const uint32_t rowB = w * C;
-    const uint32_t pitch = (rowB + 15) & ~15u;
-    const uint8_t *src = (kEnc ? fd.src : fd.G) + (uint64_t)i0 * rowB;
-    uint8_t *dst = (kEnc ? fd.G : fd.dst) + (uint64_t)i0 * rowB;
-    uint8_t *In = smem;                                          // RB rows
-    uint8_t *Out = smem + (size_t)RB * pitch;                    // RB rows
-    uint32_t *sh = reinterpret_cast<uint32_t *>(smem + 2 * (size_t)RB * pitch);   // row shifts [r * C + c]
-    const FastMod modW8(8 * w);
-
-    // ---- load the band (rows are contiguous in global memory)
-    const bool v16 = rowB % 16 == 0 && aligned(src, 16) && aligned(dst, 16);
-    if (v16) {
-        const uint32_t nvr = rowB / 16;
-        for (uint32_t k = threadIdx.x; k < nr * nvr; k += blockDim.x) {
-            const uint32_t r = k / nvr, v = k - r * nvr;
-            *reinterpret_cast<uint4 *>(In + (size_t)r * pitch + 16 * v) =
-                __ldcs(reinterpret_cast<const uint4 *>(src + (uint64_t)r * rowB + 16 * v));
-        }
-    } else {
-        for (uint32_t k = threadIdx.x; k < nr * rowB; k += blockDim.x) {
-            const uint32_t r = k / rowB, q = k - r * rowB;
-            In[(size_t)r * pitch + q] = src[(uint64_t)r * rowB + q];
-        }
-    }
-    for (uint32_t k = threadIdx.x; k < nr * C; k += blockDim.x) {
-        const uint32_t r = k / C, c = k - r * C;
-        sh[k] = modW8.mod(fd.D[(uint64_t)c * h + i0 + r]);
-    }
-    __syncthreads();
-
-    if (C == 3 && (w & 3) == 0 && v16) {
-        // ---- planar route, one pass: a thread builds the 12 output bytes of one 4-pixel group.  For each
-        // channel the two source words of its plane are deinterleaved on the fly from the staged row (a
-        // plane word u is the channel's bytes of the interleaved words 3u .. 3u+2), rotated with one
-        // funnel shift, and the three rotated plane words are interleaved back into Out.  With w % 4 == 0
-        // the source offset within a plane word is the same for every group of a channel row, so a row
-        // needs only a word offset and a shift amount per channel.
-        const uint32_t W4 = w >> 2;
-        uint8_t *Outp = Out;
-        for (uint32_t r = 0; r < nr; ++r) {
-            const uint32_t *row = reinterpret_cast<const uint32_t *>(In + (size_t)r * pitch);
-            uint32_t *orow = reinterpret_cast<uint32_t *>(Outp + (size_t)r * pitch);
-            uint32_t du[3], fs[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const uint32_t sc = sh[r * 3 + c];
-                const uint32_t a = sc >> 3, rr = sc & 7;
-                // first source byte of the plane for output pixel 0: -a-1 (encrypt) or a (decrypt), mod w
-                int s0 = kEnc ? -(int)a - 1 : (int)a;
-                if (s0 < 0) s0 += (int)w;
-                du[c] = (uint32_t)s0 >> 2;
-                const uint32_t o = (uint32_t)s0 & 3;
-                fs[c] = kEnc ? 8 * o + 8 - rr : 8 * o + rr;
-            }
-            for (uint32_t g = threadIdx.x; g < W4; g += blockDim.x) {
-                uint32_t q[3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    uint32_t u = g + du[c];
-                    u = u >= W4 ? u - W4 : u;
-                    const uint32_t u1 = u + 1 == W4 ? 0 : u + 1;
-                    const uint32_t a0 = row[3 * u], a1 = row[3 * u + 1], a2 = row[3 * u + 2];
-                    const uint32_t b0 = row[3 * u1], b1 = row[3 * u1 + 1], b2 = row[3 * u1 + 2];
-                    uint32_t lo, hi;
-                    if (c == 0) {
-                        lo = __byte_perm(__byte_perm(a0, a1, 0x0630), a2, 0x5210);
-                        hi = __byte_perm(__byte_perm(b0, b1, 0x0630), b2, 0x5210);
-                    } else if (c == 1) {
-                        lo = __byte_perm(__byte_perm(a0, a1, 0x0741), a2, 0x6210);
-                        hi = __byte_perm(__byte_perm(b0, b1, 0x0741), b2, 0x6210);
-                    } else {
-                        lo = __byte_perm(__byte_perm(a0, a1, 0x0052), a2, 0x7410);
-                        hi = __byte_perm(__byte_perm(b0, b1, 0x0052), b2, 0x7410);
-                    }
-                    q[c] = __funnelshift_rc(lo, hi, fs[c]);
-                }
-                uint32_t *wp = orow + 3 * g;
-                wp[0] = __byte_perm(__byte_perm(q[0], q[1], 0x1040), q[2], 0x3410);
-                wp[1] = __byte_perm(__byte_perm(q[1], q[0], 0x2601), q[2], 0x3250);
-                wp[2] = __byte_perm(__byte_perm(q[2], q[0], 0x3072), q[1], 0x3710);
-            }
-        }
-        __syncthreads();
-        const uint32_t nvr = rowB / 16;
-        for (uint32_t r = 0; r < nr; ++r)
-            for (uint32_t v = threadIdx.x; v < nvr; v += blockDim.x)
-                *reinterpret_cast<uint4 *>(dst + (uint64_t)r * rowB + 16 * v) =
-                    *reinterpret_cast<const uint4 *>(Outp + (size_t)r * pitch + 16 * v);
-        return;
-    }
-
-    // ---- byte-wise route: four output bytes of one channel per thread, one funnel shift each
-    const uint32_t nq = (w + 3) >> 2;
-    for (uint32_t rc = 0; rc < nr * C; ++rc) {
-        const uint32_t r = rc / C, c = rc - r * C;
-        const uint32_t s = sh[rc];
-        const uint32_t a = s >> 3, rr = s & 7;
-        const uint8_t *row = In + (size_t)r * pitch + c;
-        uint8_t *orow0 = Out + (size_t)r * pitch + c;
-        for (uint32_t k = threadIdx.x; k < nq; k += blockDim.x) {
-            const uint32_t j = 4 * k;
-            const uint32_t nm = min(4u, w - j);
-            // first source pixel: j - a - 1 (encrypt) or j + a (decrypt), mod w
-            int p0 = kEnc ? (int)j - (int)a - 1 : (int)(j + a);
-            if (p0 < 0) p0 += (int)w;
-            if (p0 >= (int)w) p0 -= (int)w;
-            uint32_t A0, A1, A2, A3, A4;
-            if ((uint32_t)p0 + 4 < w) {
-                const uint8_t *p = row + (uint32_t)p0 * C;
-                A0 = p[0]; A1 = p[C]; A2 = p[2 * C]; A3 = p[3 * C]; A4 = p[4 * C];
-            } else {
-                uint32_t q = (uint32_t)p0;
-                A0 = row[q * C]; q = q + 1 == w ? 0 : q + 1;
-                A1 = row[q * C]; q = q + 1 == w ? 0 : q + 1;
-                A2 = row[q * C]; q = q + 1 == w ? 0 : q + 1;
-                A3 = row[q * C]; q = q + 1 == w ? 0 : q + 1;
-                A4 = row[q * C];
-            }
-            const uint32_t X = A0 | (A1 << 8) | (A2 << 16) | (A3 << 24);
-            const uint32_t o = __funnelshift_r(X, A4, kEnc ? 8 - rr : rr);
-            uint8_t *orow = orow0 + j * C;
-#pragma unroll
-            for (int m = 0; m < 4; ++m)
-                if ((uint32_t)m < nm) orow[(uint32_t)m * C] = (uint8_t)(o >> (8 * m));
-        }
-    }
-    __syncthreads();
-
-    // ---- store the band
-    if (v16) {
-        const uint32_t nvr = rowB / 16;
-        for (uint32_t k = threadIdx.x; k < nr * nvr; k += blockDim.x) {
-            const uint32_t r = k / nvr, v = k - r * nvr;
-            *reinterpret_cast<uint4 *>(dst + (uint64_t)r * rowB + 16 * v) =
-                *reinterpret_cast<const uint4 *>(Out + (size_t)r * pitch + 16 * v);
-        }
-    } else {
-        for (uint32_t k = threadIdx.x; k < nr * rowB; k += blockDim.x) {
-            const uint32_t r = k / rowB, q = k - r * rowB;
-            dst[(uint64_t)r * rowB + q] = Out[(size_t)r * pitch + q];
-        }
-    }
+    row_pass<kEnc>(fd, cta - fd.rcta0, smem, threadIdx.x, blockDim.x, [] { __syncthreads(); });
 }
 
 // Single-pass encryption (row rotation, column rotation and XOR in one kernel) for interleaved RGB frames
