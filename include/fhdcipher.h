@@ -219,6 +219,42 @@ int decrypt_frames_sched(fhd_cipher *c, uint32_t count, const fhd_frame *frames,
  * (synchronises that stream), so that later calls on it never allocate.
  * frame_scratch_bytes() gives the scratch one frame needs. */
 int cipher_reserve(fhd_cipher *c, void *stream, uint64_t bytes);
+
+/* Persistent batched launch (the paper runs one frame at a time; this is a
+ * batching option of this library).  The whole of Algorithm 1 for `count`
+ * frames (at most 64; frames of any size and stream, several frames of one
+ * stream in call order) runs as ONE kernel launch with one CTA per SM that
+ * pulls its tasks from device queues: the sub-frame digest pipelines (Sec.
+ * II-A, largest frames first), LHCS_m of every stream (Algorithm 1), the
+ * worker warps (Algorithm 2; one chain warp per SM sub-partition), and the
+ * confusion + XOR passes (Sec. II-C, Algos 3-7) of each frame as soon as its
+ * keystream exists.  Per-frame dependency counters order the tasks; every
+ * wait is bounded (cipher_set_persistent_limits, default 2 s), after which
+ * the launch ends with the batch unfinished and cipher_sync_status returns
+ * FHD_ERR_TIMEOUT.  Results, chaining and digests are those of
+ * encrypt_frames / decrypt_frames.  Asynchronous on `stream`; the handle's
+ * scratch for `stream` is sized like encrypt_frames' (a first call outside
+ * CUDA graph capture sizes it and the launch's counters, after which the call
+ * can be captured and replayed).  Strip widths and row bands are those of the
+ * other calls where they fit the launch's shared memory, smaller otherwise. */
+int encrypt_frames_persistent(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream);
+int decrypt_frames_persistent(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream);
+
+/* Sender and receiver in one persistent launch: `sender` encrypts enc_frames
+ * and `receiver` decrypts dec_frames, where dec_frames[k].src and .digest must
+ * be enc_frames[k].dst and .digest (same shape).  The receiver's LHCS_m of a
+ * frame waits only for the sender's LHCS_m of it (which has written the
+ * transmitted digest), its inverse permutation for the frame's ciphertext, so
+ * the two sides' chaotic stages overlap.  Both handles must share n_workers,
+ * rk4_h, u_bound, digest mode and transport (FHD_ERR_INVALID_ARG otherwise);
+ * a timeout is reported by both handles' cipher_sync_status. */
+int cipher_round_trip_persistent(fhd_cipher *sender, fhd_cipher *receiver, uint32_t count,
+                                 const fhd_frame *enc_frames, const fhd_frame *dec_frames, void *stream);
+
+/* Wait limit of this handle's persistent launches (timeout_ns, 1 ms .. 60 s)
+ * and a test hook: hold_frame >= 0 withholds that frame's digest, so that the
+ * waits on it run out (-1: none). */
+int cipher_set_persistent_limits(fhd_cipher *c, uint64_t timeout_ns, int hold_frame);
 uint64_t fhd_frame_scratch_bytes(uint32_t n_workers, uint32_t height, uint32_t width, uint32_t channels);
 
 /* Receiver-side integrity check (the paper transmits the digests with the

@@ -38,7 +38,8 @@ EXPORTS = (
     "decrypt_frames_split", "encrypt_frames_split", "cipher_profile_spans", "cipher_set_partition",
     "cipher_get_partition", "cipher_set_layout", "fhd_stats_histogram", "fhd_stats_npcr_uaci",
     "fhd_stats_correlation", "fhd_stats_local_entropy", "encrypt_frames_sched", "decrypt_frames_sched",
-    "fhd_frame_digest_tree", "fhd_fp64_probe", "fhd_set_encrypt_route",
+    "fhd_frame_digest_tree", "fhd_fp64_probe", "fhd_set_encrypt_route", "encrypt_frames_persistent",
+    "decrypt_frames_persistent", "cipher_round_trip_persistent", "cipher_set_persistent_limits",
 )
 KERNEL_KINDS = ("sha", "master", "keystream", "encrypt", "decrypt")
 
@@ -135,6 +136,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "fhd_frame_scratch_bytes": (u64, [u32, u32, u32, u32]),
             "fhd_fp64_probe": (i32, [u32, u32, P, ctypes.POINTER(u64), P]),
             "fhd_set_encrypt_route": (i32, [i32]),
+            "encrypt_frames_persistent": (i32, [P, u32, P, P]),
+            "decrypt_frames_persistent": (i32, [P, u32, P, P]),
+            "cipher_round_trip_persistent": (i32, [P, P, u32, P, P, P]),
+            "cipher_set_persistent_limits": (i32, [P, u64, i32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -300,6 +305,31 @@ class Cipher:
         self._run(lib.decrypt_frames, lib.decrypt_frames_sched, items, stream, False, key_waits=tuple(wait_events),
                   worker_waits=tuple(worker_wait_events), data_events=tuple(data_events), master_event=master_event,
                   keystream_event=keystream_event)
+
+    def encrypt_frames_persistent(self, items: Iterable, stream=None):
+        """encrypt_frames as one persistent kernel launch (at most 64 frames)."""
+        arr, n = self._frames(items)
+        _check(load().encrypt_frames_persistent(self._handle(), n, arr, _stream_ptr(stream)), self._h)
+
+    def decrypt_frames_persistent(self, items: Iterable, stream=None):
+        """decrypt_frames as one persistent kernel launch (at most 64 frames)."""
+        arr, n = self._frames(items)
+        _check(load().decrypt_frames_persistent(self._handle(), n, arr, _stream_ptr(stream)), self._h)
+
+    def round_trip_persistent(self, receiver: "Cipher", enc_items: Iterable, dec_items: Iterable, stream=None):
+        """This handle encrypts enc_items and ``receiver`` decrypts dec_items, frame k of dec_items being the
+        ciphertext (and digest) of frame k of enc_items, in one persistent kernel launch."""
+        ea, n = self._frames(enc_items)
+        da, m = self._frames(dec_items)
+        if n != m:
+            raise ValueError("enc_items and dec_items differ in length")
+        _check(load().cipher_round_trip_persistent(self._handle(), receiver._handle(), n, ea, da,
+                                                   _stream_ptr(stream)), self._h)
+
+    def set_persistent_limits(self, timeout_ns: int = 2_000_000_000, hold_frame: int = -1):
+        """Wait limit of the persistent launches of this handle; hold_frame >= 0 (a test hook) withholds that
+        frame's digest so that the waits on it run out."""
+        _check(load().cipher_set_persistent_limits(self._handle(), int(timeout_ns), int(hold_frame)), self._h)
 
     def verify_frames(self, items: Iterable, stream=None) -> torch.Tensor:
         """Receiver-side check: 1 per frame whose decrypted ``dst`` re-hashes to its ``digest``."""

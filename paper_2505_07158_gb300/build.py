@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfhdcipher.so")
-SOURCES = ["api.cu", "sha256.cu", "chaos.cu", "permute.cu", "stats.cu", "probe.cu"]
+SOURCES = ["api.cu", "sha256.cu", "chaos.cu", "permute.cu", "stats.cu", "probe.cu", "persist.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "--expt-relaxed-constexpr",
               "-Xcompiler", "-fPIC,-ffp-contract=off", "-Xptxas", "-warn-spills"]

@@ -3,6 +3,7 @@
 // batch (K1 sub-frame SHA-256, K2a master LHCS, K2b worker LHCS pairs,
 // K3/K4 fused permutation).  Every step of the cipher runs in the kernels;
 // the host only validates, lays out descriptors and enqueues.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
@@ -48,6 +49,10 @@ struct fhd_cipher {
     uint32_t digest_mode = FHD_DIGEST_XOR;
     uint32_t transport = FHD_TRANSPORT_PLAIN;
     cudaStream_t last_stream = nullptr;
+    // Persistent launches: the dependency counters of the launch (device), its wait limit and test hook.
+    fhd::PCounters *d_pcnt = nullptr;
+    unsigned long long p_timeout_ns = 2000000000ull;
+    int p_hold = -1;
     std::string err;
     bool prof = false;
     struct Rec { int kind; cudaEvent_t a, b; };
@@ -550,6 +555,159 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
     return FHD_OK;
 }
 
+// Checks shared by the batched entry points: pointers, dimensions, open streams, no src/dst overlap.
+int check_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames) {
+    for (uint32_t k = 0; k < count; ++k) {
+        const fhd_frame &f = frames[k];
+        std::string why;
+        if (!f.src || !f.dst || !f.digest) return fail(c, FHD_ERR_INVALID_ARG, "frame " + std::to_string(k) + ": null pointer");
+        if (!check_dims(f.height, f.width, f.channels, why)) return fail(c, FHD_ERR_INVALID_ARG, "frame " + std::to_string(k) + ": " + why);
+        if (f.stream_id >= c->open.size() || !c->open[f.stream_id])
+            return fail(c, FHD_ERR_BAD_STREAM, "frame " + std::to_string(k) + ": stream not open");
+        const uint64_t N = (uint64_t)f.height * f.width * f.channels;
+        if (f.src < f.dst + N && f.dst < f.src + N) return fail(c, FHD_ERR_INVALID_ARG, "frame " + std::to_string(k) + ": src and dst overlap");
+    }
+    return FHD_OK;
+}
+
+// One side of a persistent launch: descriptors (scratch of this handle on stream s), stream groups, and
+// the strip widths and row bands that fit the launch's permutation shared memory.
+int persistent_side(fhd_cipher *c, uint32_t count, const fhd_frame *frames, bool encrypt, cudaStream_t s,
+                    fhd::PSide &S, size_t &mem_smem) {
+    const size_t lim = fhd::persistent_mem_smem_limit();
+    std::memset(&S, 0, sizeof S);
+    S.count = count;
+    S.n = c->n;
+    S.digest_mode = c->digest_mode;
+    S.digest_masked = c->transport == FHD_TRANSPORT_MASKED;
+    S.encrypt = encrypt;
+    S.hstep = c->h;
+    S.hhalf = c->h / 2.0;
+    S.hsixth = c->h / 6.0;
+    for (int q = 0; q < 4; ++q) S.u[q] = c->u[q];
+    S.states = c->d_states;
+    S.status = c->d_status;
+    uint64_t need = 0;
+    for (uint32_t k = 0; k < count; ++k)
+        need += frame_scratch(c->n, frames[k].height, frames[k].width, frames[k].channels);
+    uint8_t *p = nullptr;
+    int rc = ensure_scratch(c, s, need, &p);
+    if (rc != FHD_OK) return rc;
+    for (uint32_t k = 0; k < count; ++k) {
+        const fhd_frame &f = frames[k];
+        FrameDesc &d = S.f[k];
+        d.src = f.src;
+        d.dst = f.dst;
+        d.digest = f.digest;
+        d.h = f.height;
+        d.w = f.width;
+        d.C = f.channels;
+        d.N = (uint64_t)f.height * f.width * f.channels;
+        d.slot = f.stream_id;
+        d.gamma = c->mirror[f.stream_id].gamma;
+        d.part = p; p += align16(32ull * c->n);
+        d.IR = reinterpret_cast<double *>(p); p += align16(64ull * c->n);
+        d.D = reinterpret_cast<uint16_t *>(p); p += align16(2ull * d.C * (d.h + d.w));
+        d.B = p; p += align16(d.N);
+        d.G = p; p += align16(d.N);
+        // at most 64 pixels: the column pass of 384 threads covers a strip row of up to 384 bytes per pass
+        uint32_t P = std::min(fhd::strip_width(d.h, d.w, d.C), 64u);
+        while (P > 1 && fhd::strip_smem_bytes(d.h, P, d.C) > lim) P /= 2;
+        if (fhd::strip_smem_bytes(d.h, P, d.C) > lim)
+            return fail(c, FHD_ERR_TOO_LARGE, "frame " + std::to_string(k) + ": too tall for a persistent launch");
+        d.P = P;
+        const size_t pitch = ((size_t)d.w * d.C + 15) & ~(size_t)15;
+        uint32_t RB = (uint32_t)(lim / (2 * pitch + 4 * d.C));
+        RB = RB > 16 ? 16 : RB;
+        if (RB < 1) return fail(c, FHD_ERR_TOO_LARGE, "frame " + std::to_string(k) + ": too wide for a persistent launch");
+        d.RB = RB;
+        S.strips[k] = fhd::permute_strips(d.w, P);
+        S.bands[k] = (d.h + RB - 1) / RB;
+        const size_t a = fhd::strip_smem_bytes(d.h, P, d.C), r = fhd::row_smem_bytes(d.w, d.C, RB);
+        mem_smem = std::max(mem_smem, std::max(a, r));
+    }
+    std::vector<uint32_t> seen;
+    uint32_t pos = 0;
+    for (uint32_t k = 0; k < count; ++k) {
+        const uint32_t sid = S.f[k].slot;
+        bool dup = false;
+        for (uint32_t x : seen) if (x == sid) { dup = true; break; }
+        if (dup) continue;
+        seen.push_back(sid);
+        S.group_begin[S.groups++] = (uint16_t)pos;
+        for (uint32_t k2 = k; k2 < count; ++k2)
+            if (S.f[k2].slot == sid) S.order[pos++] = (uint16_t)k2;
+    }
+    S.group_begin[S.groups] = (uint16_t)pos;
+    return FHD_OK;
+}
+
+// A persistent launch of one direction (c1 == nullptr) or of a round trip: c0 encrypts frames0 and c1
+// decrypts frames1, frame k of frames1 being the ciphertext of frame k of frames0.
+int run_persistent(fhd_cipher *c0, fhd_cipher *c1, uint32_t count, const fhd_frame *f0, const fhd_frame *f1,
+                   bool encrypt0, void *stream) {
+    if (!c0 || (f1 && !c1)) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
+    if (count == 0) return FHD_OK;
+    if (!f0 || (c1 && !f1)) return fail(c0, FHD_ERR_INVALID_ARG, "null frames");
+    if (count > (uint32_t)fhd::kPMax) return fail(c0, FHD_ERR_TOO_LARGE, "more than 64 frames in a persistent launch");
+    int rc = check_frames(c0, count, f0);
+    if (rc == FHD_OK && c1) rc = check_frames(c1, count, f1);
+    if (rc != FHD_OK) return rc;
+    if (c1) {
+        if (c0->n != c1->n || c0->h != c1->h || std::memcmp(c0->u, c1->u, sizeof c0->u) ||
+            c0->digest_mode != c1->digest_mode || c0->transport != c1->transport)
+            return fail(c0, FHD_ERR_INVALID_ARG, "sender and receiver protocol parameters differ");
+        for (uint32_t k = 0; k < count; ++k)
+            if (f1[k].src != f0[k].dst || f1[k].digest != f0[k].digest || f1[k].height != f0[k].height ||
+                f1[k].width != f0[k].width || f1[k].channels != f0[k].channels)
+                return fail(c0, FHD_ERR_INVALID_ARG, "frame " + std::to_string(k) +
+                                                       ": the receiver's frame is not the sender's ciphertext");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = prepare_device();
+    if (e != cudaSuccess) return cuda_fail(c0, e, "prepare");
+    if (!c0->d_pcnt) {
+        if (capturing(s))
+            return fail(c0, FHD_ERR_STATE, "persistent launch during CUDA graph capture: run the batch once uncaptured first");
+        e = cudaMalloc(&c0->d_pcnt, sizeof(fhd::PCounters));
+        if (e != cudaSuccess) { c0->d_pcnt = nullptr; return fail(c0, FHD_ERR_OOM, "cudaMalloc persistent counters"); }
+    }
+    static thread_local fhd::PLaunch L;
+    std::memset(&L, 0, sizeof L);
+    size_t mem_smem = 0;
+    rc = persistent_side(c0, count, f0, encrypt0, s, L.s[0], mem_smem);
+    if (rc == FHD_OK && c1) rc = persistent_side(c1, count, f1, false, s, L.s[1], mem_smem);
+    if (rc != FHD_OK) return rc;
+    L.sides = c1 ? 2 : 1;
+    L.wpf = (c0->n + 2) / 3;
+    L.sha_units = encrypt0 ? (uint32_t)(((uint64_t)count * c0->n + 31) / 32) : 0;
+    L.chain_tasks = L.s[0].groups + (c1 ? L.s[1].groups : 0) + L.sides * L.wpf * count;
+    std::vector<uint32_t> idx(count);
+    for (uint32_t k = 0; k < count; ++k) idx[k] = k;
+    std::stable_sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) { return L.s[0].f[a].N > L.s[0].f[b].N; });
+    for (uint32_t k = 0; k < count; ++k) {
+        L.prio[k] = idx[k];
+        L.mprio[k] = idx[count - 1 - k];
+    }
+    L.memb_begin[0] = 0;
+    for (uint32_t r = 0; r < count; ++r) {
+        const uint32_t f = L.mprio[r];
+        uint32_t blk = L.s[0].strips[f] + L.s[0].bands[f];
+        if (c1) blk += L.s[1].strips[f] + L.s[1].bands[f];
+        L.memb_begin[r + 1] = L.memb_begin[r] + blk;
+    }
+    L.mem_tasks = L.memb_begin[count];
+    L.timeout_ns = c0->p_timeout_ns;
+    L.hold_frame = c0->p_hold;
+    L.cnt = c0->d_pcnt;
+    if ((e = cudaMemsetAsync(c0->d_pcnt, 0, sizeof(fhd::PCounters), s)) != cudaSuccess)
+        return cuda_fail(c0, e, "reset persistent counters");
+    if ((e = fhd::launch_persistent(L, mem_smem, s)) != cudaSuccess) return cuda_fail(c0, e, "persistent launch");
+    c0->last_stream = s;
+    if (c1) c1->last_stream = s;
+    return FHD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -752,6 +910,30 @@ int cipher_import_state(fhd_cipher *c, uint32_t stream_id, const void *buf, size
     if (e == cudaSuccess) e = cudaMemcpy(c->d_states + stream_id, &st, sizeof st, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(c, e, "import state");
     c->mirror[stream_id] = st;
+    return FHD_OK;
+}
+
+int encrypt_frames_persistent(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream) {
+    return run_persistent(c, nullptr, count, frames, nullptr, true, stream);
+}
+
+int decrypt_frames_persistent(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream) {
+    return run_persistent(c, nullptr, count, frames, nullptr, false, stream);
+}
+
+int cipher_round_trip_persistent(fhd_cipher *sender, fhd_cipher *receiver, uint32_t count,
+                                 const fhd_frame *enc_frames, const fhd_frame *dec_frames, void *stream) {
+    if (!sender || !receiver) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
+    return run_persistent(sender, receiver, count, enc_frames, dec_frames, true, stream);
+}
+
+int cipher_set_persistent_limits(fhd_cipher *c, uint64_t timeout_ns, int hold_frame) {
+    if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
+    if (timeout_ns < 1000000ull || timeout_ns > 60000000000ull)
+        return fail(c, FHD_ERR_INVALID_ARG, "timeout_ns must be 1 ms .. 60 s");
+    if (hold_frame < -1 || hold_frame >= fhd::kPMax) return fail(c, FHD_ERR_INVALID_ARG, "hold_frame must be -1 .. 63");
+    c->p_timeout_ns = timeout_ns;
+    c->p_hold = hold_frame;
     return FHD_OK;
 }
 
@@ -963,6 +1145,7 @@ void cipher_destroy(fhd_cipher *c) {
     }
     cudaFree(c->d_states);
     cudaFree(c->d_status);
+    cudaFree(c->d_pcnt);
     delete c;
 }
 

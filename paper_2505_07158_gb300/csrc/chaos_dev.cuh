@@ -240,7 +240,7 @@ __device__ void keystream_warp(const FrameDesc &fd, uint32_t n, const Rk4 &c, ui
     // Uniform trip count: the longest slice of the frame.
     const uint64_t need_max = 2 * ((LD + n - 1) / n) + (LB + n - 1) / n;
     const uint64_t T = (need_max + 23) / 24;
-    const double chain_value = active ? fd.IR[4 * (2 * p + (ch & 1)) + v] : 0.0;
+    const double chain_value = active ? __ldcg(fd.IR + 4 * (2 * p + (ch & 1)) + v) : 0.0;   // written by LHCS_m
     uint8_t *Dbytes = reinterpret_cast<uint8_t *>(fd.D) + 2 * ws.d0;
     uint8_t *Bp = fd.B + ws.b0;
     const uint64_t ndb = 2 * ws.nd;
@@ -286,7 +286,7 @@ __device__ void master_stream(const BatchT &b, uint32_t g, StreamState *states, 
         const FrameDesc &fd = b.f[b.order[k]];
         if (!before(b.order[k])) break;   // a dependency of the frame did not arrive (a bounded wait gave up)
         if (lane < 8)   // the frame's digest: folded by the digest stage, or the transmitted one
-            reinterpret_cast<uint32_t *>(H)[lane] = reinterpret_cast<const uint32_t *>(fd.digest)[lane];
+            reinterpret_cast<uint32_t *>(H)[lane] = __ldcg(reinterpret_cast<const uint32_t *>(fd.digest) + lane);
         __syncwarp();
         if (b.digest_masked) {
             // Lanes 0..3 hold the chaining state before this frame.  Encryption transmits H xor M (the

@@ -47,6 +47,55 @@ struct Batch {
     FrameDesc f[kMaxBatch];
 };
 
+// ---- Persistent batch launch (persist.cu): one kernel pulls the digest, chaining, worker and permutation
+// tasks of a batch -- of one direction, or of an encryption and the decryption of its ciphertext -- from
+// device queues with per-frame dependency counters.
+constexpr int kPMax = 64;   // frames per side
+
+// One direction of a persistent launch.  The fields master_stream reads have the names of Batch's.
+struct PSide {
+    uint32_t count, n, groups;
+    uint32_t digest_mode, digest_masked, encrypt;
+    double hstep, hhalf, hsixth;
+    uint32_t u[4];
+    uint16_t order[kPMax];
+    uint16_t group_begin[kPMax + 1];
+    uint32_t strips[kPMax];   // column-pass strips of frame k
+    uint32_t bands[kPMax];    // row-pass bands of frame k
+    struct StreamState *states;
+    unsigned *status;
+    FrameDesc f[kPMax];
+};
+
+// Dependency counters and queue heads of one launch (device memory, zeroed before it).
+struct PCounters {
+    unsigned sha_next, chain_next, mem_next, abort;
+    unsigned sha_msgs[kPMax];          // side 0 (encrypting): sub-frame messages hashed, per frame
+    unsigned digest_ready[kPMax];      // side 0: frame digest written
+    unsigned master_done[2][kPMax];    // LHCS_m iterates of the frame written
+    unsigned ks_done[2][kPMax];        // worker warps of the frame done
+    unsigned rows_done[2][kPMax];      // row-pass bands of the frame done
+    unsigned strips_done[2][kPMax];    // column-pass strips of the frame done
+};
+
+struct PLaunch {
+    uint32_t sides;            // 1: one direction; 2: side 0 encrypts, side 1 decrypts side 0's ciphertexts
+    uint32_t wpf;              // worker warps per frame (three worker pairs each)
+    uint32_t sha_units;        // digest pipelines of side 0 when it encrypts (32 messages each), else 0
+    uint32_t chain_tasks;      // masters of both sides, then worker warps
+    uint32_t mem_tasks;
+    uint32_t prio[kPMax];      // frame indices by decreasing size: digest and worker order
+    uint32_t mprio[kPMax];     // frame indices by increasing size: permutation order
+    uint32_t memb_begin[kPMax + 1];   // permutation queue: first task of each frame (mprio order)
+    unsigned long long timeout_ns;    // limit of every dependency wait
+    int hold_frame;            // test hook: side 0's digest of this frame is never published (-1: none)
+    PCounters *cnt;
+    PSide s[2];
+};
+
+cudaError_t launch_persistent(const PLaunch &L, size_t mem_smem, cudaStream_t s);
+size_t persistent_mem_smem_limit();   // shared memory the permutation tasks of a persistent launch may use
+
 // Chaining state of one video stream (Sec. II-A): x, y, z, w, gamma, frames done.
 struct StreamState {
     double v[4];

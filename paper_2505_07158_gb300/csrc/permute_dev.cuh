@@ -27,6 +27,14 @@ struct FastMod {
 };
 
 // Last frame whose first CTA (strip or row numbering) is <= cta.
+// Loads of the passes.  kL2 (the persistent kernel, whose inputs other CTAs of the same launch produce):
+// through L2 only, never a possibly stale L1 line; otherwise streaming loads (read once, evict first).
+template <bool kL2, class T>
+__device__ __forceinline__ T pass_ld(const T *p) {
+    if (kL2) return __ldcg(p);
+    return __ldcs(p);
+}
+
 __device__ __forceinline__ bool aligned(const void *p, uintptr_t a) {
     return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0;
 }
@@ -46,7 +54,7 @@ __device__ __forceinline__ uint32_t strip_vec(uint64_t rowB, uint32_t P, uint32_
 // Decrypt: S[(i - s_v) mod h][q] = (E ^ B)[i][q]; G = S.
 // Column pass over strip `strip` of frame fd by the nthr threads (tid = 0..nthr-1) of a group that meets at
 // sync(); smem holds the strip (strip_smem_bytes).
-template <bool kEnc, class Sync>
+template <bool kEnc, bool kL2 = false, class Sync>
 __device__ void strip_pass(const FrameDesc &fd, uint32_t strip, uint8_t *smem, uint32_t tid, uint32_t nthr, Sync sync) {
     const uint32_t h = fd.h, w = fd.w, C = fd.C, P = fd.P;
     const uint32_t j0 = strip * P;
@@ -75,7 +83,7 @@ __device__ void strip_pass(const FrameDesc &fd, uint32_t strip, uint8_t *smem, u
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const uint32_t q = 4 * j + k, jj = q / C, c = q - jj * C;
-                const uint32_t t = modH.mod(Dv[(uint64_t)c * w + j0 + jj]);
+                const uint32_t t = modH.mod(pass_ld<kL2>(Dv + (uint64_t)c * w + j0 + jj));
                 ht[k] = kEnc ? t : h - t;
             }
             const uint8_t *sp = src + base + 4 * j;
@@ -86,8 +94,8 @@ __device__ void strip_pass(const FrameDesc &fd, uint32_t strip, uint8_t *smem, u
                 for (int k = 0; k < kRowsW; ++k) {
                     const uint32_t i = ib + k * RT;
                     if (i < h) {
-                        e[k] = __ldcs(reinterpret_cast<const unsigned int *>(sp + (uint64_t)i * rowB));
-                        if (!kEnc) e[k] ^= __ldcs(reinterpret_cast<const unsigned int *>(bp + (uint64_t)i * rowB));
+                        e[k] = pass_ld<kL2>(reinterpret_cast<const unsigned int *>(sp + (uint64_t)i * rowB));
+                        if (!kEnc) e[k] ^= pass_ld<kL2>(reinterpret_cast<const unsigned int *>(bp + (uint64_t)i * rowB));
                     }
                 }
 #pragma unroll
@@ -109,12 +117,12 @@ __device__ void strip_pass(const FrameDesc &fd, uint32_t strip, uint8_t *smem, u
         if (tid < QC * RT) {
             const uint32_t q = tid % QC, tr = tid / QC;
             const uint32_t jj = q / C, c = q - jj * C;
-            const uint32_t t = modH.mod(Dv[(uint64_t)c * w + j0 + jj]);
+            const uint32_t t = modH.mod(pass_ld<kL2>(Dv + (uint64_t)c * w + j0 + jj));
             const uint32_t ht = kEnc ? t : h - t;
             for (uint32_t i = tr; i < h; i += RT) {
                 const uint64_t o = (uint64_t)i * rowB + base + q;
-                uint8_t e = src[o];
-                if (!kEnc) e ^= fd.B[o];
+                uint8_t e = pass_ld<kL2>(src + o);
+                if (!kEnc) e ^= pass_ld<kL2>(fd.B + o);
                 uint32_t d = i + ht;
                 d = d >= h ? d - h : d;
                 S[(size_t)d * RP + q] = e;
@@ -136,7 +144,7 @@ __device__ void strip_pass(const FrameDesc &fd, uint32_t strip, uint8_t *smem, u
                 const uint32_t i = ib + k * RT;
                 if (i < h) {
                     g[k] = *reinterpret_cast<const uint4 *>(S + (size_t)i * RP + 16 * tv);
-                    if (kEnc) k4[k] = __ldcs(reinterpret_cast<const uint4 *>(fd.B + (uint64_t)i * rowB + base + 16 * tv));
+                    if (kEnc) k4[k] = pass_ld<kL2>(reinterpret_cast<const uint4 *>(fd.B + (uint64_t)i * rowB + base + 16 * tv));
                 }
             }
 #pragma unroll
@@ -154,14 +162,14 @@ __device__ void strip_pass(const FrameDesc &fd, uint32_t strip, uint8_t *smem, u
         for (uint32_t i = tr; i < h; i += RT) {
             const uint64_t o = (uint64_t)i * rowB + base + 4 * tv;
             uint32_t g = *reinterpret_cast<const uint32_t *>(S + (size_t)i * RP + 4 * tv);
-            if (kEnc) g ^= *reinterpret_cast<const uint32_t *>(fd.B + o);
+            if (kEnc) g ^= pass_ld<kL2>(reinterpret_cast<const uint32_t *>(fd.B + o));
             *reinterpret_cast<uint32_t *>(out + o) = g;
         }
     } else {
         for (uint32_t i = tr; i < h; i += RT) {
             const uint64_t o = (uint64_t)i * rowB + base + tv;
             uint8_t g = S[(size_t)i * RP + tv];
-            if (kEnc) g ^= fd.B[o];
+            if (kEnc) g ^= pass_ld<kL2>(fd.B + o);
             out[o] = g;
         }
     }
@@ -178,7 +186,7 @@ __device__ void strip_pass(const FrameDesc &fd, uint32_t strip, uint8_t *smem, u
 // plane words), one 64-to-32-bit funnel shift by 8*(byte offset) + bit shift
 // gives the four rotated bytes, and the three channels' words are
 // interleaved back.  Other shapes take the byte-wise route.
-template <bool kEnc, class Sync>
+template <bool kEnc, bool kL2 = false, class Sync>
 __device__ void row_pass(const FrameDesc &fd, uint32_t band, uint8_t *smem, uint32_t tid, uint32_t nthr, Sync sync) {
     const uint32_t h = fd.h, w = fd.w, C = fd.C, RB = fd.RB;
     const uint32_t i0 = band * RB;
@@ -199,17 +207,17 @@ __device__ void row_pass(const FrameDesc &fd, uint32_t band, uint8_t *smem, uint
         for (uint32_t k = tid; k < nr * nvr; k += nthr) {
             const uint32_t r = k / nvr, v = k - r * nvr;
             *reinterpret_cast<uint4 *>(In + (size_t)r * pitch + 16 * v) =
-                __ldcs(reinterpret_cast<const uint4 *>(src + (uint64_t)r * rowB + 16 * v));
+                pass_ld<kL2>(reinterpret_cast<const uint4 *>(src + (uint64_t)r * rowB + 16 * v));
         }
     } else {
         for (uint32_t k = tid; k < nr * rowB; k += nthr) {
             const uint32_t r = k / rowB, q = k - r * rowB;
-            In[(size_t)r * pitch + q] = src[(uint64_t)r * rowB + q];
+            In[(size_t)r * pitch + q] = pass_ld<kL2>(src + (uint64_t)r * rowB + q);
         }
     }
     for (uint32_t k = tid; k < nr * C; k += nthr) {
         const uint32_t r = k / C, c = k - r * C;
-        sh[k] = modW8.mod(fd.D[(uint64_t)c * h + i0 + r]);
+        sh[k] = modW8.mod(pass_ld<kL2>(fd.D + (uint64_t)c * h + i0 + r));
     }
     sync();
 

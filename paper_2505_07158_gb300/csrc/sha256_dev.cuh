@@ -214,12 +214,12 @@ __device__ void tree_digest(const uint8_t *part, uint32_t n, uint32_t h[8]) {
     uint32_t i = 0;
     for (; i + 16 <= words; i += 16) {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) w[k] = bswap(p[i + k]);
+        for (int k = 0; k < 16; ++k) w[k] = bswap(__ldcg(p + i + k));
         sha256_compress(st.h, w);
     }
     const uint32_t rem = words - i;   // 0 or 8
 #pragma unroll
-    for (int k = 0; k < 16; ++k) w[k] = (uint32_t)k < rem ? bswap(p[i + k]) : 0u;
+    for (int k = 0; k < 16; ++k) w[k] = (uint32_t)k < rem ? bswap(__ldcg(p + i + k)) : 0u;
     w[rem] = 0x80000000u;
     const uint64_t bits = 256ull * n;
     w[14] = (uint32_t)(bits >> 32);
