@@ -72,9 +72,13 @@ def parse():
     ap.add_argument("--no-probe", action="store_true", help="skip the binary64 peak probe (profiling runs)")
     ap.add_argument("--repeats", type=int, default=5,
                     help="timed regions of --steps steps each; value is the median region")
-    ap.add_argument("--serve-seconds", type=float, default=6.0, help="length of each serving run (60 s = full config)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="length of each serving run (60 s: the full workload)")
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed-batch, serving and stress measurements")
     ap.add_argument("--no-stress", action="store_true", help="skip the 256 x 8K stress round trip")
+    ap.add_argument("--extras", default=",".join(EXTRAS),
+                    help="comma list of the other workloads to run: " + ",".join(EXTRAS))
+    ap.add_argument("--encrypt-route", default="two_pass", choices=["two_pass", "single_pass"],
+                    help="route of the encryption's confusion + XOR in the headline")
     ap.add_argument("--gate", default="chain", choices=["permute", "keystream", "chain", "window"],
                     help="what the next clip's LHCS_m waits for besides the chaining state (see round_trip)")
     ap.add_argument("--partition", action="store_true",
@@ -346,6 +350,7 @@ def run_ours(args):
 
     from paper_2505_07158_gb300 import autotune
     tuned = autotune.tune([(HGT, WID, CH)])
+    fhd.fhd_set_encrypt_route(args.encrypt_route)
     clip = si.clip(FRAMES, HGT, WID, CH, seed=rank)
     host = torch.from_numpy(clip).pin_memory()
     key = si.key(rank)
@@ -584,7 +589,7 @@ def run_ours(args):
             ms_r, n_r = tmp.profile_read()["encrypt"]
             tmp.close()
         finally:
-            fhd.fhd_set_encrypt_route("two_pass")
+            fhd.fhd_set_encrypt_route(args.encrypt_route)
         routes[route] = {"ms": ms_r / max(n_r, 1), "launches": n_r, "outs": outs}
     routes_equal = all(torch.equal(a, b) for a, b in zip(routes["single_pass"]["outs"], routes["two_pass"]["outs"]))
 
@@ -680,7 +685,7 @@ def run_ours(args):
                                    "decrypt_frames on the receiver's (its chaotic stage waits for the digests, its "
                                    "inverse permutation for the ciphertext)",
                        "clips_in_flight": INF, "next_clip_gate": args.gate, "worker_window": WW,
-                       "worker_layout": args.layout,
+                       "worker_layout": args.layout, "encrypt_route": args.encrypt_route,
                        "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),
                        "sm_partition": {"lhcs_m_sms": enc.partition()[0], "other_sms": enc.partition()[1]},
                        "frames_per_step": FRAMES * world, "l2": "inputs larger than L2 (~560 MB live per step)",
@@ -718,12 +723,35 @@ MIXED = [(480, 640, 3), (720, 1280, 3), (1080, 1920, 3), (2160, 3840, 3)]
 SERVE_RES = [(480, 640, 3), (720, 1280, 3), (1080, 1920, 3)]
 
 
+EXTRAS = ("batched", "serving", "sweep", "digest", "stats", "stress")
+
+
 def run_extras(args, rank, fhd, torch):
-    """Batched mixed-resolution graph launch (64 frames) and the serving loop."""
-    from paper_2505_07158_gb300 import autotune, batching, serving
-    dev = torch.device("cuda", torch.cuda.current_device())
+    """The other workloads, by --extras: the batched mixed-resolution launches (64 frames), the serving loop,
+    the worker-count sweep, the digest modes, the frame statistics and the 8K stress round trip."""
+    want = set(args.extras.split(",")) if args.extras else set()
     out = {}
-    # ---- 64 frames: 16 each of VGA, 720p, 1080p, 4K; one stream (own key) per frame
+    if "batched" in want:
+        out["batched_mixed64"] = run_batched(rank, fhd, torch)
+    if "serving" in want:
+        out["serving"] = run_serving(args, rank, fhd, torch)
+    if "sweep" in want:
+        out["worker_count_sweep"] = run_n_sweep(rank, fhd, torch)
+    if "digest" in want:
+        out["digest_modes"] = run_digest_modes(rank, fhd, torch)
+    if "stats" in want:
+        out["frame_statistics"] = run_stats(rank, fhd, torch)
+    if "stress" in want and not args.no_stress:
+        out["stress_8k"] = run_stress(rank, fhd, torch)
+    return out
+
+
+def run_batched(rank, fhd, torch):
+    """64 frames, 16 each of VGA, 720p, 1080p, 4K, one stream (own key) per frame: the seven-kernel batched
+    calls as one CUDA graph per direction, the same frames one call per frame, and the persistent round trip
+    (one launch for both sides) in a CUDA graph."""
+    from paper_2505_07158_gb300 import autotune, batching
+    dev = torch.device("cuda", torch.cuda.current_device())
     autotune.tune(MIXED)
     shapes = [s for s in MIXED for _ in range(16)]
     frames = [torch.from_numpy(si.gradient_frame(*s, t=k, seed=rank + 11)).to(dev) for k, s in enumerate(shapes)]
@@ -754,17 +782,40 @@ def run_extras(args, rank, fhd, torch):
     b.record()
     b.synchronize()
     plain_ms = a.elapsed_time(b)
-    out["batched_mixed64"] = {
+    # the same batch as one persistent round-trip launch (sender and receiver), captured in a CUDA graph
+    pers = batching.PersistentRoundTrip(enc, dec, enc_items, dec_items, graph=True)
+    pers.replay()
+    torch.cuda.synchronize()
+    pers_ok = all(torch.equal(it[2], fr) for it, fr in zip(dec_items, frames))
+    a.record()
+    for _ in range(reps):
+        pers.replay()
+    b.record()
+    b.synchronize()
+    pers_ms = a.elapsed_time(b) / reps
+    enc.sync_status()
+    dec.sync_status()
+    res = {
         "workload": "64 frames (16 x 640x480, 720p, 1080p, 2160p x3 uint8), one stream and key per frame, "
                     "encrypt + decrypt as two CUDA-graph replays",
         "frames_per_s": len(shapes) / (ms / 1000.0), "GB_per_s": 2 * nbytes / (ms / 1000.0) / 1e9,
         "ms_per_batch_round_trip": ms, "plain_per_frame_frames_per_s": len(shapes) / (plain_ms / 1000.0),
         "kernels_per_replay": g_enc.kernels_per_replay + g_dec.kernels_per_replay, "round_trip_ok": bool(ok),
+        "persistent": {"frames_per_s": len(shapes) / (pers_ms / 1000.0), "ms_per_batch_round_trip": pers_ms,
+                       "GB_per_s": 2 * nbytes / (pers_ms / 1000.0) / 1e9, "kernels_per_replay": 1,
+                       "round_trip_ok": bool(pers_ok),
+                       "note": "cipher_round_trip_persistent: one launch for both sides, captured in a CUDA graph"},
         "strip_widths": {f"{h}x{w}x{c}": fhd.fhd_strip_width(h, w, c) for (h, w, c) in MIXED}}
     enc.close(); dec.close()
-    del frames, enc_items, dec_items, g_enc, g_dec
+    del frames, enc_items, dec_items, g_enc, g_dec, pers
     torch.cuda.empty_cache()
-    # ---- serving: 32 streams, resolutions drawn from VGA / 720p / 1080p, Poisson arrivals
+    return res
+
+
+def run_serving(args, rank, fhd, torch):
+    """32 streams, resolutions drawn from VGA / 720p / 1080p, Poisson arrivals at 24, 30 and 60 fps."""
+    from paper_2505_07158_gb300 import serving
+    dev = torch.device("cuda", torch.cuda.current_device())
     g = si.rng(77 + rank)
     sshapes = [SERVE_RES[int(g.integers(3))] for _ in range(32)]
     skeys = [si.key(5000 + 100 * rank + k) for k in range(32)]
@@ -779,17 +830,12 @@ def run_extras(args, rank, fhd, torch):
                           n_workers=N_WORKERS, budget_bytes=20 << 30, mode="plain")
     srv.close()
     serve["plain_30fps"] = st
-    out["serving"] = {"workload": f"32 streams, resolutions uniform over 640x480 / 1280x720 / 1920x1080 x3, "
+    res = {"workload": f"32 streams, resolutions uniform over 640x480 / 1280x720 / 1920x1080 x3, "
                                   f"Poisson arrivals, 20 GB HBM budget, {args.serve_seconds:g} s per rate "
                                   f"(plain: one frame per call, one CUDA stream)", **serve}
     del pool
     torch.cuda.empty_cache()
-    out["worker_count_sweep"] = run_n_sweep(rank, fhd, torch)
-    out["digest_modes"] = run_digest_modes(rank, fhd, torch)
-    out["frame_statistics"] = run_stats(rank, fhd, torch)
-    if not args.no_stress:
-        out["stress_8k"] = run_stress(rank, fhd, torch)
-    return out
+    return res
 
 
 def run_stats(rank, fhd, torch, frames=30, reps=10):

@@ -2,10 +2,10 @@
 
 * The 64-frame mixed batch (16 each of 640x480, 1280x720, 1920x1080, 3840x2160, RGB; one video stream and
   key per frame; the autotuned strip widths installed) is captured as one CUDA graph per direction and
-  replayed twice, as the benchmark does.  Every frame's transmitted digest and ciphertext on both replays
-  (each replay is the next frame of every stream) equal the oracle's: ciphertexts compared by SHA-256 of
-  their bytes for all 64 frames, byte for byte for one frame of each size; every decrypted frame equals
-  its plaintext.
+  replayed twice, then as one persistent round-trip launch in a CUDA graph and replayed twice more, as the
+  benchmark does.  Every frame's transmitted digest and ciphertext on all four replays (each replay is the
+  next frame of every stream) equal the oracle's: ciphertexts compared by SHA-256 of their bytes for all
+  64 frames, byte for byte for one frame of each size; every decrypted frame equals its plaintext.
 * The continuous-batching server (8 streams over 1920x1080 / 1280x720 / 640x480 RGB, Poisson arrivals,
   32 workers, 20 GB budget) keeps a copy of every frame it serves; every served digest equals the oracle's,
   and the first, a middle and the last frame of every stream equal the oracle's ciphertext byte for byte
@@ -43,8 +43,8 @@ def test_mixed64_graph_replays_match_oracle_at_full_sizes():
     recipes = [("gradient", s, k, 11) for k, s in enumerate(shapes)]
     keys = [si.key(1000 + k) for k in range(len(shapes))]
     full = {16 * q for q in range(4)}                     # the first frame of each size, compared in full
-    jobs = [oracle_pool.pool().submit(oracle_pool.stream_job, keys[k], [recipes[k]] * 2,
-                                      {0, 1} if k in full else set())
+    jobs = [oracle_pool.pool().submit(oracle_pool.stream_job, keys[k], [recipes[k]] * 4,
+                                      {0, 1, 2, 3} if k in full else set())
             for k in range(len(shapes))]
     autotune.tune(MIXED)
     frames = [to_dev(si.gradient_frame(*s, t=k, seed=11)) for k, s in enumerate(shapes)]
@@ -52,10 +52,16 @@ def test_mixed64_graph_replays_match_oracle_at_full_sizes():
     enc_items, dec_items, dec = batching.mixed_batch(shapes, keys, enc, frames, dev())
     g_enc = batching.GraphedCall(enc, enc_items, encrypt=True)
     g_dec = batching.GraphedCall(dec, dec_items, encrypt=False)
+    persistent = None
     got = []
-    for rep in range(2):
-        g_enc.replay()
-        g_dec.replay()
+    for rep in range(4):
+        if rep < 2:      # the seven-kernel batched calls, one graph per direction
+            g_enc.replay()
+            g_dec.replay()
+        else:            # the persistent round trip (one launch), captured in a graph
+            if persistent is None:
+                persistent = batching.PersistentRoundTrip(enc, dec, enc_items, dec_items, graph=True)
+            persistent.replay()
         torch.cuda.synchronize()
         rec = []
         for k, (sid, F, E, H) in enumerate(enc_items):
@@ -66,7 +72,7 @@ def test_mixed64_graph_replays_match_oracle_at_full_sizes():
     dec.sync_status()
     for k, job in enumerate(jobs):
         ref = job.result()
-        for rep in range(2):
+        for rep in range(4):
             H_ref, sha_ref, E_ref = ref[rep]
             H, sha, E = got[rep][k]
             assert H == H_ref, (rep, k, shapes[k])
