@@ -85,6 +85,7 @@ def parse():
                     help="run LHCS_m on its own 8-SM partition (green contexts) instead of beside the workers")
     ap.add_argument("--no-partition", action="store_true", help="(the default) LHCS_m on the same SMs as the rest")
     ap.add_argument("--layout", default="throughput", choices=["latency", "throughput"], help="worker warp layout")
+    ap.add_argument("--worker-cta", type=int, default=1, choices=[1, 2, 4, 8], help="worker warps per CTA")
     ap.add_argument("--inflight", type=int, default=5,
                     help="clips in flight on separate buffers: later clips' digest stage and LHCS_m overlap earlier "
                          "clips' keystreams")
@@ -360,6 +361,8 @@ def run_ours(args):
         dec.set_partition(False)
     enc.set_layout(args.layout)
     dec.set_layout(args.layout)
+    enc.set_worker_cta(args.worker_cta)
+    dec.set_worker_cta(args.worker_cta)
     sid, rid = enc.open_stream(), dec.open_stream()
     stream = torch.cuda.current_stream()
 
@@ -685,7 +688,8 @@ def run_ours(args):
                                    "decrypt_frames on the receiver's (its chaotic stage waits for the digests, its "
                                    "inverse permutation for the ciphertext)",
                        "clips_in_flight": INF, "next_clip_gate": args.gate, "worker_window": WW,
-                       "worker_layout": args.layout, "encrypt_route": args.encrypt_route,
+                       "worker_layout": args.layout, "worker_warps_per_cta": args.worker_cta,
+                       "encrypt_route": args.encrypt_route,
                        "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),
                        "sm_partition": {"lhcs_m_sms": enc.partition()[0], "other_sms": enc.partition()[1]},
                        "frames_per_step": FRAMES * world, "l2": "inputs larger than L2 (~560 MB live per step)",

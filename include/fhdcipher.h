@@ -242,7 +242,8 @@ int decrypt_frames_persistent(fhd_cipher *c, uint32_t count, const fhd_frame *fr
 
 /* Sender and receiver in one persistent launch: `sender` encrypts enc_frames
  * and `receiver` decrypts dec_frames, where dec_frames[k].src and .digest must
- * be enc_frames[k].dst and .digest (same shape).  The receiver's LHCS_m of a
+ * be enc_frames[k].dst and .digest (same shape), and two receiver frames
+ * share a stream exactly when the two sender frames do.  The receiver's LHCS_m of a
  * frame waits only for the sender's LHCS_m of it (which has written the
  * transmitted digest), its inverse permutation for the frame's ciphertext, so
  * the two sides' chaotic stages overlap.  Both handles must share n_workers,
@@ -255,6 +256,15 @@ int cipher_round_trip_persistent(fhd_cipher *sender, fhd_cipher *receiver, uint3
  * and a test hook: hold_frame >= 0 withholds that frame's digest, so that the
  * waits on it run out (-1: none). */
 int cipher_set_persistent_limits(fhd_cipher *c, uint64_t timeout_ns, int hold_frame);
+
+/* Timeline of this handle's last persistent launch (instrumentation; waits
+ * for the handle's CUDA streams): for frame k < count (call order, at most
+ * 64), ms[9k + 0] = when its digest was published, and for side s (0: this
+ * handle's direction, 1: the receiver of a round trip) ms[9k + 1 + 4s ..
+ * 9k + 4 + 4s] = when its LHCS_m iterates, its last worker warp, its last row
+ * band and its last column strip were done, in milliseconds after the
+ * launch's start; -1 where that never happened (e.g. no such side). */
+int cipher_persistent_trace(fhd_cipher *c, uint32_t count, double *ms);
 uint64_t fhd_frame_scratch_bytes(uint32_t n_workers, uint32_t height, uint32_t width, uint32_t channels);
 
 /* Receiver-side integrity check (the paper transmits the digests with the
@@ -387,6 +397,12 @@ int cipher_get_partition(fhd_cipher *c, uint32_t *chain_sms, uint32_t *bulk_sms)
  * share the FP64 pipes (clips in flight, many concurrent streams). */
 enum { FHD_LAYOUT_LATENCY = 0, FHD_LAYOUT_THROUGHPUT = 1 };
 int cipher_set_layout(fhd_cipher *c, int layout);
+
+/* Worker warps per CTA of the worker kernel (1 -- the default --, 2, 4 or 8):
+ * the warps of one CTA are consecutive worker groups of a frame, spread over
+ * the SM's four sub-partitions (binary64 pipes) together.  Results are the
+ * same for every value; FHD_ERR_INVALID_ARG for another value. */
+int cipher_set_worker_cta(fhd_cipher *c, uint32_t warps);
 
 
 /* ---- Frame statistics of the paper's evaluation (Sec. III and IV-B) ----

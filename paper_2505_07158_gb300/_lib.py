@@ -40,6 +40,7 @@ EXPORTS = (
     "fhd_stats_correlation", "fhd_stats_local_entropy", "encrypt_frames_sched", "decrypt_frames_sched",
     "fhd_frame_digest_tree", "fhd_fp64_probe", "fhd_set_encrypt_route", "encrypt_frames_persistent",
     "decrypt_frames_persistent", "cipher_round_trip_persistent", "cipher_set_persistent_limits",
+    "cipher_set_worker_cta", "cipher_persistent_trace",
 )
 KERNEL_KINDS = ("sha", "master", "keystream", "encrypt", "decrypt")
 
@@ -140,6 +141,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "decrypt_frames_persistent": (i32, [P, u32, P, P]),
             "cipher_round_trip_persistent": (i32, [P, P, u32, P, P, P]),
             "cipher_set_persistent_limits": (i32, [P, u64, i32]),
+            "cipher_set_worker_cta": (i32, [P, u32]),
+            "cipher_persistent_trace": (i32, [P, u32, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -326,6 +329,15 @@ class Cipher:
         _check(load().cipher_round_trip_persistent(self._handle(), receiver._handle(), n, ea, da,
                                                    _stream_ptr(stream)), self._h)
 
+    PTRACE = ("digest", "master", "keystream", "rows", "strips", "rx_master", "rx_keystream", "rx_rows", "rx_strips")
+
+    def persistent_trace(self, count: int):
+        """Timeline of the last persistent launch: (count, 9) ms after its start, columns PTRACE (-1: never)."""
+        import numpy as np
+        out = np.zeros((count, 9), dtype=np.float64)
+        _check(load().cipher_persistent_trace(self._handle(), count, ctypes.c_void_p(out.ctypes.data)), self._h)
+        return out
+
     def set_persistent_limits(self, timeout_ns: int = 2_000_000_000, hold_frame: int = -1):
         """Wait limit of the persistent launches of this handle; hold_frame >= 0 (a test hook) withholds that
         frame's digest so that the waits on it run out."""
@@ -401,6 +413,10 @@ class Cipher:
     def set_layout(self, layout: str):
         """Worker warp layout: "latency" (six chains per warp) or "throughput" (eight)."""
         _check(load().cipher_set_layout(self._handle(), {"latency": 0, "throughput": 1}[layout]), self._h)
+
+    def set_worker_cta(self, warps: int):
+        """Worker warps per CTA of the worker kernel (1, 2, 4 or 8); same results for every value."""
+        _check(load().cipher_set_worker_cta(self._handle(), int(warps)), self._h)
 
     def partition(self) -> tuple:
         """(SMs of the LHCS_m partition, SMs of the rest); (0, 0) when off."""

@@ -46,6 +46,7 @@ struct fhd_cipher {
     std::vector<Scratch> scratch;
     bool partition = false;
     int layout = FHD_LAYOUT_LATENCY;
+    uint32_t worker_cta = 1;   // worker warps per CTA of the keystream kernel
     uint32_t digest_mode = FHD_DIGEST_XOR;
     uint32_t transport = FHD_TRANSPORT_PLAIN;
     cudaStream_t last_stream = nullptr;
@@ -538,7 +539,7 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
             for (uint32_t k = 0; k < hk.n_worker_waits; ++k)
                 if (hk.worker_waits[k] && (e = cudaStreamWaitEvent(sb, (cudaEvent_t)hk.worker_waits[k], 0)) != cudaSuccess)
                     return cuda_fail(c, e, "wait worker event");
-        if ((e = timed(c, FHD_K_KEYSTREAM, sb, [&] { return fhd::launch_keystream(b, sb, c->layout == FHD_LAYOUT_THROUGHPUT); })) != cudaSuccess)
+        if ((e = timed(c, FHD_K_KEYSTREAM, sb, [&] { return fhd::launch_keystream(b, sb, c->layout == FHD_LAYOUT_THROUGHPUT, c->worker_cta); })) != cudaSuccess)
             return cuda_fail(c, e, "keystream launch");
         if (keystream_done && base + m >= count && (e = cudaEventRecord(keystream_done, sb)) != cudaSuccess)
             return cuda_fail(c, e, "record keystream event");
@@ -610,7 +611,7 @@ int persistent_side(fhd_cipher *c, uint32_t count, const fhd_frame *frames, bool
         d.D = reinterpret_cast<uint16_t *>(p); p += align16(2ull * d.C * (d.h + d.w));
         d.B = p; p += align16(d.N);
         d.G = p; p += align16(d.N);
-        // at most 64 pixels: the column pass of 384 threads covers a strip row of up to 384 bytes per pass
+        // at most 64 pixels: the persistent column pass (352 threads) covers a strip row (<= 256 bytes) per pass
         uint32_t P = std::min(fhd::strip_width(d.h, d.w, d.C), 64u);
         while (P > 1 && fhd::strip_smem_bytes(d.h, P, d.C) > lim) P /= 2;
         if (fhd::strip_smem_bytes(d.h, P, d.C) > lim)
@@ -657,11 +658,17 @@ int run_persistent(fhd_cipher *c0, fhd_cipher *c1, uint32_t count, const fhd_fra
         if (c0->n != c1->n || c0->h != c1->h || std::memcmp(c0->u, c1->u, sizeof c0->u) ||
             c0->digest_mode != c1->digest_mode || c0->transport != c1->transport)
             return fail(c0, FHD_ERR_INVALID_ARG, "sender and receiver protocol parameters differ");
-        for (uint32_t k = 0; k < count; ++k)
+        for (uint32_t k = 0; k < count; ++k) {
             if (f1[k].src != f0[k].dst || f1[k].digest != f0[k].digest || f1[k].height != f0[k].height ||
                 f1[k].width != f0[k].width || f1[k].channels != f0[k].channels)
                 return fail(c0, FHD_ERR_INVALID_ARG, "frame " + std::to_string(k) +
                                                        ": the receiver's frame is not the sender's ciphertext");
+            // the receiver's streams mirror the sender's: frames k and k2 share a stream on one side iff on both
+            for (uint32_t k2 = 0; k2 < k; ++k2)
+                if ((f0[k].stream_id == f0[k2].stream_id) != (f1[k].stream_id == f1[k2].stream_id))
+                    return fail(c0, FHD_ERR_INVALID_ARG, "frame " + std::to_string(k) +
+                                                           ": the receiver's streams do not mirror the sender's");
+        }
     }
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = prepare_device();
@@ -681,13 +688,31 @@ int run_persistent(fhd_cipher *c0, fhd_cipher *c1, uint32_t count, const fhd_fra
     L.sides = c1 ? 2 : 1;
     L.wpf = (c0->n + 2) / 3;
     L.sha_units = encrypt0 ? (uint32_t)(((uint64_t)count * c0->n + 31) / 32) : 0;
-    L.chain_tasks = L.s[0].groups + (c1 ? L.s[1].groups : 0) + L.sides * L.wpf * count;
+
     std::vector<uint32_t> idx(count);
     for (uint32_t k = 0; k < count; ++k) idx[k] = k;
     std::stable_sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) { return L.s[0].f[a].N > L.s[0].f[b].N; });
     for (uint32_t k = 0; k < count; ++k) {
         L.prio[k] = idx[k];
         L.mprio[k] = idx[count - 1 - k];
+    }
+    // chain queue: the LHCS_m tasks of all stream groups (in the order of each group's earliest frame in
+    // mprio order), then per frame in mprio order its worker warps: every task after those it waits for
+    {
+        std::vector<uint32_t> rank(count);
+        for (uint32_t r = 0; r < count; ++r) rank[L.mprio[r]] = r;
+        for (uint32_t k = 0; k < count; ++k) L.chain_masters[k] = 0;
+        for (uint32_t g = 0; g < L.s[0].groups; ++g) {
+            uint32_t best = L.s[0].order[L.s[0].group_begin[g]];
+            for (uint32_t q = L.s[0].group_begin[g]; q < L.s[0].group_begin[g + 1]; ++q)
+                if (rank[L.s[0].order[q]] < rank[best]) best = L.s[0].order[q];
+            L.chain_masters[best] = (uint16_t)L.sides;
+            L.chain_group[best] = (uint16_t)g;
+        }
+        L.chain_begin[0] = 0;
+        for (uint32_t r = 0; r < count; ++r) L.chain_begin[r + 1] = L.chain_begin[r] + L.chain_masters[L.mprio[r]];
+        L.chain_masters_total = L.chain_begin[count];
+        L.chain_tasks = L.chain_masters_total + L.sides * L.wpf * count;
     }
     L.memb_begin[0] = 0;
     for (uint32_t r = 0; r < count; ++r) {
@@ -698,6 +723,17 @@ int run_persistent(fhd_cipher *c0, fhd_cipher *c1, uint32_t count, const fhd_fra
     }
     L.mem_tasks = L.memb_begin[count];
     L.timeout_ns = c0->p_timeout_ns;
+    // a digest CTA's pipeline may hash several tasks in turn: allow ~4 us per 64-byte block of all the
+    // digest work (far above its speed) beyond the dependency limit
+    {
+        int sms = 1;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c0->device);
+        uint64_t blocks = 0;
+        if (encrypt0)
+            for (uint32_t k = 0; k < count; ++k) blocks += L.s[0].f[k].N / 64 + 2ull * c0->n;
+        const uint64_t ctas = std::max<uint64_t>(1, std::min<uint64_t>(L.sha_units, (uint64_t)std::max(sms, 1)));
+        L.digest_wait_ns = L.timeout_ns + 4000ull * blocks / ctas;
+    }
     L.hold_frame = c0->p_hold;
     L.cnt = c0->d_pcnt;
     if ((e = cudaMemsetAsync(c0->d_pcnt, 0, sizeof(fhd::PCounters), s)) != cudaSuccess)
@@ -927,6 +963,28 @@ int cipher_round_trip_persistent(fhd_cipher *sender, fhd_cipher *receiver, uint3
     return run_persistent(sender, receiver, count, enc_frames, dec_frames, true, stream);
 }
 
+int cipher_persistent_trace(fhd_cipher *c, uint32_t count, double *ms) {
+    if (!c || (!ms && count)) return fail(c, FHD_ERR_INVALID_ARG, "null argument");
+    if (count > (uint32_t)fhd::kPMax) return fail(c, FHD_ERR_TOO_LARGE, "more than 64 frames");
+    if (!c->d_pcnt) return fail(c, FHD_ERR_STATE, "no persistent launch yet");
+    cudaError_t e = sync_all(c);
+    fhd::PCounters h;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, c->d_pcnt, sizeof h, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read persistent counters");
+    auto rel = [&](unsigned long long t) { return t ? (double)(long long)(t - h.t0) * 1e-6 : -1.0; };
+    for (uint32_t k = 0; k < count; ++k) {
+        double *o = ms + 9 * k;
+        o[0] = rel(h.t_digest[k]);
+        for (int s = 0; s < 2; ++s) {
+            o[1 + 4 * s] = rel(h.t_master[s][k]);
+            o[2 + 4 * s] = rel(h.t_ks[s][k]);
+            o[3 + 4 * s] = rel(h.t_rows[s][k]);
+            o[4 + 4 * s] = rel(h.t_strips[s][k]);
+        }
+    }
+    return FHD_OK;
+}
+
 int cipher_set_persistent_limits(fhd_cipher *c, uint64_t timeout_ns, int hold_frame) {
     if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
     if (timeout_ns < 1000000ull || timeout_ns > 60000000000ull)
@@ -1112,6 +1170,13 @@ int fhd_stats_local_entropy(const uint8_t *frames, uint32_t count, uint32_t heig
     cudaFreeAsync(ent, s);
     if (!status) cudaFreeAsync(st, s);
     if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("local entropy launch: ") + cudaGetErrorString(e));
+    return FHD_OK;
+}
+
+int cipher_set_worker_cta(fhd_cipher *c, uint32_t warps) {
+    if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
+    if (warps != 1 && warps != 2 && warps != 4 && warps != 8) return fail(c, FHD_ERR_INVALID_ARG, "warps must be 1, 2, 4 or 8");
+    c->worker_cta = warps;
     return FHD_OK;
 }
 

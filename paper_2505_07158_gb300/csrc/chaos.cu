@@ -67,13 +67,15 @@ __global__ void __launch_bounds__(32) master_raw_kernel(double *state5, const ui
 }
 
 // K2b: one warp per kPairs worker pairs of one frame (three with the six-chain step, four with the
-// eight-chain step).
+// eight-chain step); a CTA carries blockDim.x / 32 consecutive such warps (warps of one CTA are spread over
+// the SM's sub-partitions).
 template <int kPairs>
-__global__ void __launch_bounds__(32) keystream_kernel(const __grid_constant__ Batch b) {
+__global__ void __launch_bounds__(256) keystream_kernel(const __grid_constant__ Batch b) {
     const uint32_t wpf = (b.n + kPairs - 1) / kPairs;
-    const uint32_t f = blockIdx.x / wpf, pg = blockIdx.x % wpf;
+    const uint32_t task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint32_t f = task / wpf, pg = task % wpf;
     if (f >= b.count) return;
-    keystream_warp<kPairs>(b.f[f], b.n, Rk4{b.hstep, b.hhalf, b.hsixth}, pg, threadIdx.x);
+    keystream_warp<kPairs>(b.f[f], b.n, Rk4{b.hstep, b.hhalf, b.hsixth}, pg, threadIdx.x & 31);
 }
 
 }  // namespace
@@ -93,16 +95,17 @@ cudaError_t launch_master_raw(double *state5, const uint8_t *H, uint32_t n, doub
     return cudaGetLastError();
 }
 
-cudaError_t launch_keystream(const Batch &b, cudaStream_t s, bool dense) {
+cudaError_t launch_keystream(const Batch &b, cudaStream_t s, bool dense, uint32_t warps_per_cta) {
     if (!b.count) return cudaSuccess;
+    const uint32_t k = warps_per_cta ? warps_per_cta : 1;
     if (dense) {
-        const uint32_t wpf = (b.n + 3) / 4;
-        keystream_kernel<4><<<b.count * wpf, 32, 0, s>>>(b);
+        const uint32_t warps = b.count * ((b.n + 3) / 4);
+        keystream_kernel<4><<<(warps + k - 1) / k, 32 * k, 0, s>>>(b);
         note_launch();
         return cudaGetLastError();
     }
-    const uint32_t wpf = (b.n + kPairsPerWarp - 1) / kPairsPerWarp;
-    keystream_kernel<kPairsPerWarp><<<b.count * wpf, 32, 0, s>>>(b);
+    const uint32_t warps = b.count * ((b.n + kPairsPerWarp - 1) / kPairsPerWarp);
+    keystream_kernel<kPairsPerWarp><<<(warps + k - 1) / k, 32 * k, 0, s>>>(b);
     note_launch();
     return cudaGetLastError();
 }

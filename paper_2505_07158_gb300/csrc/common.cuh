@@ -76,18 +76,28 @@ struct PCounters {
     unsigned ks_done[2][kPMax];        // worker warps of the frame done
     unsigned rows_done[2][kPMax];      // row-pass bands of the frame done
     unsigned strips_done[2][kPMax];    // column-pass strips of the frame done
+    // %globaltimer at the launch's start and when each of the counters above reached its target
+    // (instrumentation: cipher_persistent_trace)
+    unsigned long long t0;
+    unsigned long long t_digest[kPMax];
+    unsigned long long t_master[2][kPMax], t_ks[2][kPMax], t_rows[2][kPMax], t_strips[2][kPMax];
 };
 
 struct PLaunch {
     uint32_t sides;            // 1: one direction; 2: side 0 encrypts, side 1 decrypts side 0's ciphertexts
     uint32_t wpf;              // worker warps per frame (three worker pairs each)
     uint32_t sha_units;        // digest pipelines of side 0 when it encrypts (32 messages each), else 0
-    uint32_t chain_tasks;      // masters of both sides, then worker warps
+    uint32_t chain_tasks;      // the LHCS_m tasks, then per frame (mprio order) its worker warps
+    uint32_t chain_masters_total;
     uint32_t mem_tasks;
     uint32_t prio[kPMax];      // frame indices by decreasing size: digest and worker order
     uint32_t mprio[kPMax];     // frame indices by increasing size: permutation order
     uint32_t memb_begin[kPMax + 1];   // permutation queue: first task of each frame (mprio order)
+    uint32_t chain_begin[kPMax + 1];  // chain queue: first LHCS_m task of the groups starting at each frame
+    uint16_t chain_masters[kPMax];    // LHCS_m tasks of the stream group whose earliest frame is f (0, 1 or 2)
+    uint16_t chain_group[kPMax];      // that stream group
     unsigned long long timeout_ns;    // limit of every dependency wait
+    unsigned long long digest_wait_ns;   // limit of a digest CTA's other workers' wait for its digest pipeline
     int hold_frame;            // test hook: side 0's digest of this frame is never published (-1: none)
     PCounters *cnt;
     PSide s[2];
@@ -139,7 +149,7 @@ uint32_t noalloc_max_digests();
 cudaError_t launch_master(const Batch &b, StreamState *states, unsigned *status, cudaStream_t s);
 cudaError_t launch_master_raw(double *state5, const uint8_t *H, uint32_t n, double hstep, const uint32_t u[4],
                               double *IR, unsigned *status, cudaStream_t s);
-cudaError_t launch_keystream(const Batch &b, cudaStream_t s, bool dense = false);
+cudaError_t launch_keystream(const Batch &b, cudaStream_t s, bool dense = false, uint32_t warps_per_cta = 1);
 cudaError_t launch_permute(const Batch &b, bool encrypt, cudaStream_t s);
 
 // Geometry of the permutation passes: strip width (column pass) and rows per

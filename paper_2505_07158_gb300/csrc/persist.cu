@@ -4,13 +4,15 @@
 // same frames through a sender's and a receiver's streams), runs as one kernel of one CTA per SM.  Each CTA
 // carries three kinds of workers, each pulling tasks from its own device queue (an atomic counter over a
 // task order fixed by the launch descriptor):
-//   * warps 0-1: a digest pipeline (the producer/consumer SHA-256 of Sec. II-A, 32 sub-frame messages per
-//     task, largest frames first); the pipeline that completes a frame's messages folds (Algorithm 1) or
-//     tree-hashes them into the frame digest and publishes it;
-//   * warps 2-5: chain workers, one per SM sub-partition, so that a chain has the sub-partition's binary64
-//     pipe to itself: first the LHCS_m task of every stream (Algorithm 1), then the worker warps of every
-//     frame (Algorithm 2, three worker pairs each, largest frames first, the two sides interleaved);
-//   * warps 6-17: a permutation group of 384 threads with the CTA's large shared memory: per frame,
+//   * warps 0 and 1: a digest pipeline (the producer/consumer SHA-256 of Sec. II-A, 32 sub-frame messages
+//     per task, largest frames first); the pipeline that completes a frame's messages folds (Algorithm 1)
+//     or tree-hashes them into the frame digest and publishes it;
+//   * warps 2, 3 and 5: chain workers, one on each of sub-partitions 1-3, so that a chain has its
+//     sub-partition's binary64 pipe, and its issue port, to itself; per frame, smallest first
+//     (the order in which their digests arrive): the LHCS_m task of every stream whose earliest frame it
+//     is (Algorithm 1), then the frame's worker warps (Algorithm 2, three worker pairs each, the two sides
+//     interleaved);
+//   * warps 4 and 6-15: a permutation group of 352 threads with the CTA's large shared memory: per frame,
 //     smallest first, the row bands and column strips of the encryption, then the decryption's column
 //     strips and row bands (Sec. II-C, Algos 3-7, and the inverse).
 // A task waits for its inputs on per-frame counters: LHCS_m for the frame digest (the decryption's for the
@@ -30,12 +32,21 @@
 namespace fhd {
 namespace {
 
-constexpr int kPWarps = 18;
+// Warp roles by SM sub-partition (warp w runs on sub-partition w mod 4): the digest pipeline's consumer
+// (warp 0) and producer (warp 1) on sub-partitions 0 and 1; the chain workers (warps 2, 3 and 5) on
+// sub-partitions 2, 3 and 1, one each -- in a digest CTA they start only after its pipeline (below), so
+// the integer-bound digest rounds never share an issue port with a binary64 chain; warps 4 and 6-15 form
+// the permutation group.  Four warps per sub-partition leave each of them 128 registers (a
+// sub-partition's register file holds 16K).
+constexpr int kPWarps = 16;
 constexpr int kPThreads = 32 * kPWarps;
-constexpr int kChainWarp0 = 2, kChainWarps = 4;
-constexpr int kMemWarp0 = 6, kMemThreads = 32 * (kPWarps - kMemWarp0);
+constexpr int kShaConsumer = 0, kShaProducer = 1;
+constexpr int kChainWarps = 3;   // warps 2, 3, 5
+constexpr int kMemThreads = 32 * (kPWarps - 2 - kChainWarps);
+__device__ __forceinline__ int chain_index(uint32_t warp) { return warp == 2 ? 0 : warp == 3 ? 1 : warp == 5 ? 2 : -1; }
+__device__ __forceinline__ uint32_t mem_index(uint32_t warp) { return warp == 4 ? 0 : warp - 5; }   // warps 4, 6..15
 constexpr unsigned kBarSha = 1, kBarMem = 2;
-constexpr size_t kPFixedSmem = sizeof(ShaSmem) + 32 * kChainWarps + 64;   // + broadcast slots
+constexpr size_t kPFixedSmem = sizeof(ShaSmem) + 32 * kChainWarps + 64 + 16;   // + broadcast slots, flag
 constexpr size_t kPSmemLimit = 232448;
 
 __device__ __forceinline__ unsigned long long globaltimer() {
@@ -50,9 +61,12 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     return v;
 }
 
-// Publish a task's results: the caller has fenced its (and its group's) writes before this.
-__device__ __forceinline__ void release_add(unsigned *p, unsigned v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+// Publish a task's results (the caller has fenced its, and its group's, writes before this): a release-add
+// that also stamps *t with %globaltimer when this add brings the counter to `target`.
+__device__ __forceinline__ void publish(unsigned *p, unsigned v, unsigned target, unsigned long long *t) {
+    unsigned old;
+    asm volatile("atom.release.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    if (old + v == target) *t = globaltimer();
 }
 
 __device__ __forceinline__ void bar_sync(unsigned id, unsigned n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
@@ -85,9 +99,27 @@ __device__ __forceinline__ uint32_t segment(const uint32_t *a, uint32_t m, uint3
     return lo;
 }
 
+// One digest task (32 sub-frame messages, frames in prio order) as a function of its own: its register
+// allocation is then that of the pipeline alone.
+__device__ __noinline__ void digest_task(const PLaunch &L, uint32_t task, uint32_t rtid, ShaSmem &sm) {
+    const PSide &S = L.s[0];
+    const uint32_t n = S.n;
+    sha_pipeline(
+        [&](uint32_t m, const uint8_t *&p, uint64_t &len, uint8_t *&out) {
+            const FrameDesc &fd = S.f[L.prio[m / n]];
+            const uint32_t i = m % n;
+            const uint64_t lo = (uint64_t)(((unsigned __int128)fd.N * i) / n);
+            const uint64_t hi = (uint64_t)(((unsigned __int128)fd.N * (i + 1)) / n);
+            p = fd.src + lo;
+            len = hi - lo;
+            out = fd.part + 32ull * i;
+        },
+        S.count * n, task, rtid, kBarSha, sm);
+}
+
 // ---- digest pipeline (warps 0-1)
 __device__ void digest_worker(const PLaunch &L, ShaSmem &sm, unsigned *slot) {
-    const uint32_t rtid = threadIdx.x;   // 0..63
+    const uint32_t rtid = (threadIdx.x >> 5) == kShaConsumer ? (threadIdx.x & 31) : 32 + (threadIdx.x & 31);
     const PSide &S = L.s[0];
     const uint32_t n = S.n, nmsg = S.count * n;
     for (;;) {
@@ -96,17 +128,7 @@ __device__ void digest_worker(const PLaunch &L, ShaSmem &sm, unsigned *slot) {
         const uint32_t task = slot[0];
         bar_sync(kBarSha, 64);
         if (task >= L.sha_units) return;
-        sha_pipeline(
-            [&](uint32_t m, const uint8_t *&p, uint64_t &len, uint8_t *&out) {
-                const FrameDesc &fd = S.f[L.prio[m / n]];
-                const uint32_t i = m % n;
-                const uint64_t lo = (uint64_t)(((unsigned __int128)fd.N * i) / n);
-                const uint64_t hi = (uint64_t)(((unsigned __int128)fd.N * (i + 1)) / n);
-                p = fd.src + lo;
-                len = hi - lo;
-                out = fd.part + 32ull * i;
-            },
-            nmsg, task, rtid, kBarSha, sm);
+        digest_task(L, task, rtid, sm);
         __threadfence();
         bar_sync(kBarSha, 64);
         if (rtid == 0) {
@@ -134,16 +156,31 @@ __device__ void digest_worker(const PLaunch &L, ShaSmem &sm, unsigned *slot) {
                     }
                 }
                 __threadfence();
-                if ((int)f != L.hold_frame) release_add(&L.cnt->digest_ready[f], 1u);
+                if ((int)f != L.hold_frame) publish(&L.cnt->digest_ready[f], 1u, 1u, &L.cnt->t_digest[f]);
             }
         }
     }
 }
 
+// The chain workers' two task bodies as separate functions, so that their register allocation is their own
+// and not that of the whole kernel (inlined into it, the worker loop was allocated with the permutation and
+// digest code's pressure).
+__device__ __noinline__ void keystream_task(const FrameDesc &fd, uint32_t n, const Rk4 &c, uint32_t pg, int lane) {
+    keystream_warp<3>(fd, n, c, pg, lane);
+}
+
+// The same for the permutation group's four task bodies.
+__device__ __noinline__ void mem_task(uint32_t kind, const FrameDesc &fd, uint32_t idx, uint8_t *smem, uint32_t mtid) {
+    auto sync = [] { bar_sync(kBarMem, kMemThreads); };
+    if (kind == 0) row_pass<true, true>(fd, idx, smem, mtid, kMemThreads, sync);
+    else if (kind == 1) strip_pass<true, true>(fd, idx, smem, mtid, kMemThreads, sync);
+    else if (kind == 2) strip_pass<false, true>(fd, idx, smem, mtid, kMemThreads, sync);
+    else row_pass<false, true>(fd, idx, smem, mtid, kMemThreads, sync);
+}
+
 // ---- chain workers (warps 2-5): LHCS_m tasks, then worker warps
 __device__ void chain_worker(const PLaunch &L, uint8_t *H) {
     const int lane = threadIdx.x & 31;
-    const uint32_t G0 = L.s[0].groups, G1 = L.sides > 1 ? L.s[1].groups : 0;
     // One lane waits; the warp learns the outcome.
     auto wait = [&](const unsigned *p, unsigned target) {
         int ok = 1;
@@ -155,37 +192,39 @@ __device__ void chain_worker(const PLaunch &L, uint8_t *H) {
         if (lane == 0) task = ld_acquire(&L.cnt->abort) ? L.chain_tasks : atomicAdd(&L.cnt->chain_next, 1u);
         task = __shfl_sync(0xffffffffu, task, 0);
         if (task >= L.chain_tasks) return;
-        if (task < G0 + G1) {
-            const uint32_t side = task < G0 ? 0 : 1, g = side ? task - G0 : task;
+        // first every LHCS_m task (the groups in the order of their earliest frame, side 0 then side 1),
+        // then per frame (smallest first) its worker warps, the sides interleaved
+        if (task < L.chain_masters_total) {
+            const uint32_t r = segment(L.chain_begin, L.s[0].count, task);
+            const uint32_t f = L.mprio[r], side = task - L.chain_begin[r], g = L.chain_group[f];
             const PSide &S = L.s[side];
             master_stream(
                 S, g, S.states, S.status, H, lane,
-                [&](uint32_t f) {
-                    if (side == 0) return S.encrypt ? wait(&L.cnt->digest_ready[f], 1u) : true;
-                    return wait(&L.cnt->master_done[0][f], 1u);   // the transmitted digest of the sender's frame
+                [&](uint32_t fr) {
+                    if (side == 0) return S.encrypt ? wait(&L.cnt->digest_ready[fr], 1u) : true;
+                    return wait(&L.cnt->master_done[0][fr], 1u);   // the transmitted digest of the sender's frame
                 },
-                [&](uint32_t f) {
+                [&](uint32_t fr) {
                     __threadfence();
                     __syncwarp();
-                    if (lane == 0) release_add(&L.cnt->master_done[side][f], 1u);
+                    if (lane == 0) publish(&L.cnt->master_done[side][fr], 1u, 1u, &L.cnt->t_master[side][fr]);
                 });
         } else {
-            const uint32_t k = task - G0 - G1, per = L.sides * L.wpf;
-            const uint32_t r = k / per, rem = k - r * per, side = rem / L.wpf, pg = rem - side * L.wpf;
-            const uint32_t f = L.prio[r];
+            const uint32_t per = L.sides * L.wpf, t2 = task - L.chain_masters_total, r = t2 / per;
+            const uint32_t f = L.mprio[r], k = t2 - r * per, side = k / L.wpf, pg = k - side * L.wpf;
             const PSide &S = L.s[side];
             if (wait(&L.cnt->master_done[side][f], 1u))
-                keystream_warp<3>(S.f[f], S.n, Rk4{S.hstep, S.hhalf, S.hsixth}, pg, lane);
+                keystream_task(S.f[f], S.n, Rk4{S.hstep, S.hhalf, S.hsixth}, pg, lane);
             __threadfence();
             __syncwarp();
-            if (lane == 0) release_add(&L.cnt->ks_done[side][f], 1u);
+            if (lane == 0) publish(&L.cnt->ks_done[side][f], 1u, L.wpf, &L.cnt->t_ks[side][f]);
         }
     }
 }
 
 // ---- permutation group (warps 6-17)
 __device__ void mem_worker(const PLaunch &L, uint8_t *smem, unsigned *slot) {
-    const uint32_t mtid = threadIdx.x - 32 * kMemWarp0;
+    const uint32_t mtid = 32 * mem_index(threadIdx.x >> 5) + (threadIdx.x & 31);
     auto sync = [] { bar_sync(kBarMem, kMemThreads); };
     const PSide &S0 = L.s[0];
     for (;;) {
@@ -243,34 +282,65 @@ __device__ void mem_worker(const PLaunch &L, uint8_t *smem, unsigned *slot) {
         if (t >= L.mem_tasks) return;
         const uint32_t kind = code & 3, side = (code >> 2) & 1;
         const FrameDesc &fd = L.s[side].f[f];
-        if (code & 8) {
-            if (kind == 0) row_pass<true, true>(fd, idx, smem, mtid, kMemThreads, sync);
-            else if (kind == 1) strip_pass<true, true>(fd, idx, smem, mtid, kMemThreads, sync);
-            else if (kind == 2) strip_pass<false, true>(fd, idx, smem, mtid, kMemThreads, sync);
-            else row_pass<false, true>(fd, idx, smem, mtid, kMemThreads, sync);
-        }
+        if (code & 8) mem_task(kind, fd, idx, smem, mtid);
         __threadfence();
         sync();
         if (mtid == 0 && (code & 8)) {
-            unsigned *c = kind == 0 || kind == 3 ? &L.cnt->rows_done[side][f] : &L.cnt->strips_done[side][f];
-            release_add(c, 1u);
+            if (kind == 0 || kind == 3)
+                publish(&L.cnt->rows_done[side][f], 1u, L.s[side].bands[f], &L.cnt->t_rows[side][f]);
+            else
+                publish(&L.cnt->strips_done[side][f], 1u, L.s[side].strips[f], &L.cnt->t_strips[side][f]);
         }
     }
 }
 
-__global__ void __launch_bounds__(kPThreads, 1) persistent_kernel(const __grid_constant__ PLaunch L) {
+// Digest CTAs: the first min(digest tasks, grid) CTAs run the digest pipelines, and their chain workers and
+// permutation group start only once those pipelines have found the digest queue empty.  The digest rounds
+// (integer work, shared-memory traffic) and binary64 chains slow each other down several times when they
+// share an SM, so while the digests of the large frames run, the chains of the frames whose digests are
+// done run on the other SMs; a digest CTA joins them when its last digest task ends.
+__device__ bool wait_digest_cta(const PLaunch &L, volatile unsigned *flag) {
+    const unsigned long long t0 = globaltimer();
+    const unsigned long long cap = L.digest_wait_ns / 64 + 65536;
+    for (unsigned long long it = 0; it < cap; ++it) {
+        if (*flag) return true;
+        if (ld_acquire(&L.cnt->abort)) return false;
+        if (globaltimer() - t0 > L.digest_wait_ns) break;
+        __nanosleep(256);
+    }
+    atomicOr(L.s[0].status, kStatusTimeout);
+    if (L.sides > 1) atomicOr(L.s[1].status, kStatusTimeout);
+    atomicExch(&L.cnt->abort, 1u);
+    return false;
+}
+
+// 16 warps x 128 registers fill the SM's register file: one CTA per SM, and no spills in the task bodies.
+__global__ void __maxnreg__(128) persistent_kernel(const __grid_constant__ PLaunch L) {
     extern __shared__ __align__(16) uint8_t smem[];
     ShaSmem &sm = *reinterpret_cast<ShaSmem *>(smem);
     uint8_t *H = smem + sizeof(ShaSmem);
-    unsigned *slot = reinterpret_cast<unsigned *>(H + 32 * kChainWarps);   // [0] digest, [4..7] permutation
+    unsigned *slot = reinterpret_cast<unsigned *>(H + 32 * kChainWarps);   // [0] digest, [4..7] permutation,
+    volatile unsigned *digest_cta_done = slot + 8;                          // [8] this CTA's digests finished
     uint8_t *mem = smem + kPFixedSmem;
     const uint32_t warp = threadIdx.x >> 5;
-    if (warp < kChainWarp0) {
-        if (L.sha_units) digest_worker(L, sm, slot);
-    } else if (warp < kMemWarp0) {
-        chain_worker(L, H + 32 * (warp - kChainWarp0));
+    const bool digest_cta = blockIdx.x < L.sha_units;
+    if (threadIdx.x == 0) {
+        *digest_cta_done = digest_cta ? 0u : 1u;
+        if (blockIdx.x == 0) L.cnt->t0 = globaltimer();
+    }
+    __syncthreads();
+    if (warp == kShaConsumer || warp == kShaProducer) {
+        if (digest_cta) {
+            digest_worker(L, sm, slot);
+            if (threadIdx.x == 0) {
+                __threadfence_block();
+                *digest_cta_done = 1u;
+            }
+        }
+    } else if (chain_index(warp) >= 0) {
+        if (wait_digest_cta(L, digest_cta_done)) chain_worker(L, H + 32 * chain_index(warp));
     } else {
-        mem_worker(L, mem, slot + 4);
+        if (wait_digest_cta(L, digest_cta_done)) mem_worker(L, mem, slot + 4);
     }
 }
 

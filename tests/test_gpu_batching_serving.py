@@ -318,17 +318,22 @@ def test_more_than_one_descriptor_group():
 
 
 @pytest.mark.parametrize("layout", ["latency", "throughput"])
-def test_worker_layouts_match_oracle(layout):
+@pytest.mark.parametrize("cta", [1, 4, 8])
+def test_worker_layouts_match_oracle(layout, cta):
     """Both warp layouts of the worker kernel (six chains per warp with constant lanes, eight with
-    selects) produce the oracle's bytes, for worker counts that fill and do not fill the last warp."""
+    selects), with 1, 4 or 8 worker warps per CTA (a CTA's last warps idle when the batch's warp count is
+    not a multiple), produce the oracle's bytes, for worker counts that fill and do not fill the last
+    warp."""
     shapes = [(40, 56, 3), (24, 40, 1)]
     for n in (5, 8, 32):
         key = si.key(650 + n)
         frames = [to_dev(si.uniform_frame(*s, seed=651 + n + k)) for k, s in enumerate(shapes)]
         c = fhd.Cipher(key, n_workers=n)
         c.set_layout(layout)
+        c.set_worker_cta(cta)
         d = fhd.Cipher(key, n_workers=n)
         d.set_layout(layout)
+        d.set_worker_cta(cta)
         sid, rid = c.open_stream(), d.open_stream()
         E = [torch.empty_like(f) for f in frames]
         R = [torch.empty_like(f) for f in frames]
