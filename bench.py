@@ -684,7 +684,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8+f64",
             "data": "synthetic",
             "config": {"workload": "30-frame 1920x1080x3 gradient+noise clip (sigma 8, 2 px/frame), one stream "
-                                   "per GPU, n=32 workers, RK4 h=0.001; per step encrypt_frames on the sender's CUDA stream and "
+                                   "per GPU, n=32 workers, RK4 h=0.01; per step encrypt_frames on the sender's CUDA stream and "
                                    "decrypt_frames on the receiver's (its chaotic stage waits for the digests, its "
                                    "inverse permutation for the ciphertext)",
                        "clips_in_flight": INF, "next_clip_gate": args.gate, "worker_window": WW,
@@ -799,6 +799,17 @@ def run_batched(rank, fhd, torch):
     pers_ms = a.elapsed_time(b) / reps
     enc.sync_status()
     dec.sync_status()
+    # timeline of the last launch: per frame size, when its digests, LHCS_m, keystreams and last
+    # permutation task were done (median over the 16 frames of the size; ms after the launch's start)
+    tr = enc.persistent_trace(len(shapes))
+    timeline = {}
+    for q, s in enumerate(MIXED):
+        t = tr[16 * q:16 * q + 16]
+        done = np.maximum(t[:, 3:5].max(axis=1), t[:, 7:9].max(axis=1))
+        timeline[f"{s[0]}x{s[1]}x{s[2]}"] = {
+            "digest": float(np.median(t[:, 0])), "lhcs_m": float(np.median(t[:, 1])),
+            "keystreams": float(np.median(np.maximum(t[:, 2], t[:, 6]))), "round_trip_done": float(np.median(done)),
+            "round_trip_done_max": float(done.max())}
     res = {
         "workload": "64 frames (16 x 640x480, 720p, 1080p, 2160p x3 uint8), one stream and key per frame, "
                     "encrypt + decrypt as two CUDA-graph replays",
@@ -807,7 +818,8 @@ def run_batched(rank, fhd, torch):
         "kernels_per_replay": g_enc.kernels_per_replay + g_dec.kernels_per_replay, "round_trip_ok": bool(ok),
         "persistent": {"frames_per_s": len(shapes) / (pers_ms / 1000.0), "ms_per_batch_round_trip": pers_ms,
                        "GB_per_s": 2 * nbytes / (pers_ms / 1000.0) / 1e9, "kernels_per_replay": 1,
-                       "round_trip_ok": bool(pers_ok),
+                       "round_trip_ok": bool(pers_ok), "speedup_vs_graph_replays": ms / pers_ms,
+                       "timeline_ms": timeline,
                        "note": "cipher_round_trip_persistent: one launch for both sides, captured in a CUDA graph"},
         "strip_widths": {f"{h}x{w}x{c}": fhd.fhd_strip_width(h, w, c) for (h, w, c) in MIXED}}
     enc.close(); dec.close()

@@ -62,7 +62,7 @@ typedef struct fhd_cipher fhd_cipher;
  * Sec. V).  A zero field takes its default. */
 typedef struct {
     uint32_t n_workers;  /* n: sub-frames per frame and worker pairs; default 32 (Tab. speedEvaluation) */
-    double rk4_h;        /* step of the RK4 integration of Eq. (1); default 0.001 */
+    double rk4_h;        /* step of the RK4 integration of Eq. (1); default 0.01 */
     uint32_t u_bound[4]; /* reconstruction upper bounds u_x, u_y, u_z, u_w; default 20, 20, 40, 20 */
     uint32_t digest_mode; /* how H is formed from the n sub-frame digests h_i: FHD_DIGEST_XOR (0, default) */
     uint32_t digest_transport; /* how H travels: FHD_TRANSPORT_PLAIN (0, default) or FHD_TRANSPORT_MASKED */

@@ -31,7 +31,7 @@ _lib = None
 # Xeon + RTX 3090 platform (Tab. speedEvaluation).  Integrator step and the
 # reconstruction upper bounds are readings (the paper gives no values).
 DEFAULT_N = 32
-DEFAULT_H = 0.001
+DEFAULT_H = 0.01
 DEFAULT_U = (20, 20, 40, 20)
 
 CFLAGS = ["-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]

@@ -168,7 +168,7 @@ def _stream_ptr(stream) -> ctypes.c_void_p:
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _params(n_workers=32, rk4_h=0.001, u_bound=(20, 20, 40, 20), digest_mode="xor", transport="plain") -> FhdParams:
+def _params(n_workers=32, rk4_h=0.01, u_bound=(20, 20, 40, 20), digest_mode="xor", transport="plain") -> FhdParams:
     p = FhdParams()
     p.n_workers = n_workers
     p.rk4_h = rk4_h
@@ -197,7 +197,7 @@ class Cipher:
     """A cipher handle: key, protocol parameters and device-resident streams."""
 
     def __init__(self, key: bytes | None = None, ic: Sequence[float] | None = None, n_workers: int = 32,
-                 rk4_h: float = 0.001, u_bound=(20, 20, 40, 20), digest_mode: str = "xor",
+                 rk4_h: float = 0.01, u_bound=(20, 20, 40, 20), digest_mode: str = "xor",
                  digest_transport: str = "plain"):
         lib = load()
         self.params = _params(n_workers, rk4_h, u_bound, digest_mode, digest_transport)
@@ -560,7 +560,7 @@ def fhd_frame_digest_noalloc(data: torch.Tensor, out: torch.Tensor, n: int = 32,
     return out
 
 
-def fhd_master(state5: torch.Tensor, H: torch.Tensor, n_workers=32, rk4_h=0.001, u_bound=(20, 20, 40, 20),
+def fhd_master(state5: torch.Tensor, H: torch.Tensor, n_workers=32, rk4_h=0.01, u_bound=(20, 20, 40, 20),
                IR: torch.Tensor | None = None, stream=None):
     """Reconstruct + 2n LHCS_m steps; ``state5`` (float64 x5, CUDA) is updated in place."""
     assert state5.is_cuda and state5.dtype == torch.float64 and state5.numel() == 5
@@ -573,7 +573,7 @@ def fhd_master(state5: torch.Tensor, H: torch.Tensor, n_workers=32, rk4_h=0.001,
 
 
 def fhd_keystream(IR: torch.Tensor, gamma: float, height: int, width: int, channels: int, n_workers=32,
-                  rk4_h=0.001, stream=None):
+                  rk4_h=0.01, stream=None):
     """Worker pairs -> (D int16[C*(h+w)] holding uint16 bits, B uint8[h*w*C])."""
     assert IR.is_cuda and IR.dtype == torch.float64 and IR.is_contiguous()
     D = torch.empty(channels * (height + width), dtype=torch.int16, device=IR.device)

@@ -22,7 +22,7 @@ using fhd::StreamState;
 struct fhd_cipher {
     int device = 0;
     uint32_t n = 32;
-    double h = 0.001;
+    double h = 0.01;
     uint32_t u[4] = {20, 20, 40, 20};
     double key_ic[5] = {0, 0, 0, 0, 0};
     std::vector<StreamState> mirror;   // host copy of gamma (and initial state)
@@ -103,7 +103,7 @@ int cuda_fail(fhd_cipher *c, cudaError_t e, const char *what) {
 
 bool resolve_params(const fhd_params *p, uint32_t &n, double &h, uint32_t u[4], std::string &why) {
     n = 32;
-    h = 0.001;
+    h = 0.01;
     const uint32_t du[4] = {20, 20, 40, 20};
     for (int m = 0; m < 4; ++m) u[m] = du[m];
     if (!p) return true;

@@ -10,7 +10,7 @@
 * frame chaining (Sec. VI-A): a one-bit flip in frame t changes frame t+1's
   ciphertext even though frame t+1 itself is unchanged;
 * key sensitivity (Sec. IV-A): x0 + 1e-14 fails to decrypt.  Under the
-  readings taken (RK4 with h = 0.001, no transient, the six low mantissa
+  readings taken (RK4 with h = 0.01, no transient, the six low mantissa
   bytes) a 1e-14 change only reaches the low mantissa bytes within a frame, so
   about 25-85 % of the bytes come out wrong, not the 99.6 % of unrelated
   frames; a change in a high key bit gives the full 99.6 %."""
@@ -134,3 +134,32 @@ def test_chaining_step_alone_leaves_the_state_encryption_leaves(mode):
     skipped = oracle.Stream.from_key(key, n=5, digest_mode=mode)
     skipped.advance(frames[0])
     assert not np.array_equal(skipped.encrypt(frames[2])[0], E_full)
+
+
+def _channel_stats(h, keys, size=512):
+    from oracle import stats
+    F = si.gradient_frame(size, size, 3, t=0, seed=3)
+    F2, _ = si.bit_flip(F, 3)
+    chi, uaci = [], []
+    for key in keys:
+        E = oracle.Stream.from_key(key, h=h).encrypt(F)[0]
+        E2 = oracle.Stream.from_key(key, h=h).encrypt(F2)[0]
+        chi.append([stats.chi_square(stats.histogram(E, c)) for c in range(3)])
+        uaci.append([stats.npcr_uaci(E, E2, c)[1] for c in range(3)])
+    return np.mean(chi, axis=0), np.mean(uaci, axis=0)
+
+
+def test_default_step_meets_the_papers_statistics():
+    """The RK4 step is a reading (the paper names no integrator): it is the one whose ciphertexts meet the
+    paper's Sec. III-A chi^2 bar (< 293.25 per channel, 512x512) and Sec. IV-B UACI interval
+    (33.3730 %, 33.5541 %), as the paper's own ciphertexts do.  Means over four keys of a 512x512 gradient
+    frame and its one-bit flip; ideal values 255 and 33.4635 %.  With h = 0.001 the third channel's
+    ciphertext is biased: consecutive iterates of the same trajectory feed each worker pair, and at that
+    step the XOR of their sixth mantissa byte is far from uniform."""
+    keys = [si.key(700 + k) for k in range(4)]
+    chi, uaci = _channel_stats(oracle.DEFAULT_H, keys)
+    assert oracle.DEFAULT_H == 0.01
+    assert (chi < 293.25).all(), chi
+    assert ((uaci > 33.3730) & (uaci < 33.5541)).all(), uaci
+    _, uaci_small = _channel_stats(0.001, keys)
+    assert uaci_small[2] < 33.3730, uaci_small

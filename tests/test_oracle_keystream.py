@@ -78,8 +78,9 @@ def test_workers_fed_from_one_master_trajectory_are_shifted_copies():
     """Documented consequence of the reading of Algorithm 2 (pair i starts at IR[2i] and IR[2i+1]):
     IR holds consecutive iterates of one trajectory of Eq. (1), and the workers iterate the same map,
     so chain 2i+1 is chain 2i one step ahead and worker i's byte stream is worker 0's stream shifted by
-    2i steps (48 i bytes).  The D/B slices then come from one sequence, and the XOR of adjacent
-    iterates leaves the sixth extracted byte (mantissa bits 40-47) far from uniform."""
+    2i steps (48 i bytes).  The D/B slices then come from one sequence.  With a small step (h = 0.001)
+    the XOR of adjacent iterates leaves the sixth extracted byte (mantissa bits 40-47) far from uniform;
+    at the default step (0.01) it is uniform."""
     key = si.key(21)
     ic = oracle.key_to_ic(key)
     F = si.gradient_frame(64, 96, 3, seed=21)
@@ -96,6 +97,14 @@ def test_workers_fed_from_one_master_trajectory_are_shifted_copies():
     s0 = stream(0, 2000)
     for i in (1, 5):
         assert np.array_equal(stream(i, 1000)[:24 * 900], s0[48 * i:48 * i + 24 * 900])
-    sixth = np.bincount(s0[5::6].astype(np.int64), minlength=256)
-    e = sixth.sum() / 256.0
-    assert ((sixth - e) ** 2 / e).sum() > 1000.0          # uniform bytes would give ~255
+
+    def sixth_chi2(h):   # a pair one step of h apart on one trajectory, as IR[0] and IR[1] are
+        a = oracle.rk4_trajectory(IR[0], ic[4], 2000, h)
+        b = oracle.rk4_trajectory(oracle.rk4_step(IR[0], ic[4], h), ic[4], 2000, h)
+        x = (a.view(np.uint64) ^ b.view(np.uint64)) >> np.uint64(40) & np.uint64(255)
+        z = np.bincount(x.reshape(-1).astype(np.int64), minlength=256)
+        e = z.sum() / 256.0
+        return ((z - e) ** 2 / e).sum()
+
+    assert sixth_chi2(0.001) > 1000.0                        # uniform bytes would give ~255
+    assert sixth_chi2(oracle.DEFAULT_H) < 330.0

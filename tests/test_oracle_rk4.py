@@ -92,7 +92,7 @@ def _py_rk4(s, gamma, h):
 def test_no_fma_contraction_in_build():
     s = [7.123456789, -3.3, 21.5, 1.25]
     gamma = -1.1
-    traj = oracle.rk4_trajectory(s, gamma, 2000)
+    traj = oracle.rk4_trajectory(s, gamma, 2000, 0.001)
     for t in range(2000):
         s = _py_rk4(s, gamma, 0.001)
         assert list(traj[t]) == s, t
