@@ -84,15 +84,20 @@ def parse():
     ap.add_argument("--partition", action="store_true",
                     help="run LHCS_m on its own 8-SM partition (green contexts) instead of beside the workers")
     ap.add_argument("--no-partition", action="store_true", help="(the default) LHCS_m on the same SMs as the rest")
-    ap.add_argument("--layout", default="throughput", choices=["latency", "throughput"], help="worker warp layout")
+    ap.add_argument("--layout", default=None, choices=["latency", "throughput"],
+                    help="worker warp layout (default: the tuned table's, else throughput)")
     ap.add_argument("--worker-cta", type=int, default=1, choices=[1, 2, 4, 8], help="worker warps per CTA")
-    ap.add_argument("--inflight", type=int, default=5,
+    ap.add_argument("--inflight", type=int, default=None,
                     help="clips in flight on separate buffers: later clips' digest stage and LHCS_m overlap earlier "
-                         "clips' keystreams")
-    ap.add_argument("--worker-window", type=int, default=3,
+                         "clips' keystreams (default: the tuned table's, else 5)")
+    ap.add_argument("--worker-window", type=int, default=None,
                     help="clip k's workers (both sides) wait for the workers of clip k - W, so about W clips' "
                          "workers share the FP64 pipes while later clips' digests and LHCS_m run ahead "
-                         "(0: no gate; needs more clips in flight than W)")
+                         "(0: no gate; needs more clips in flight than W; default: the tuned table's, else 3)")
+    ap.add_argument("--tune", default=None, metavar="OUT.json",
+                    help="time the tile shapes of every workload's frame sizes and the clip pipeline's work split "
+                         "(layout, clips in flight, worker window) and write the table to OUT.json "
+                         "(the library's tuned.json format); prints it and exits")
     ap.add_argument("--spans", default=None,
                     help="write the timed region's launch timeline (sender and receiver, ms from its start) as JSON")
     return ap.parse_args()
@@ -351,6 +356,16 @@ def run_ours(args):
 
     from paper_2505_07158_gb300 import autotune
     tuned = autotune.tune([(HGT, WID, CH)])
+    # the clip pipeline's work split: flags, else the tuned table for this GPU, else the built-in defaults
+    pipe = autotune.pipeline_defaults() or {}
+    split_source = {}
+    for name, attr, default in (("layout", "layout", "throughput"), ("inflight", "inflight", 5),
+                                ("worker_window", "worker_window", 3)):
+        if getattr(args, attr) is None:
+            setattr(args, attr, pipe.get(name, default))
+            split_source[name] = "tuned table" if name in pipe else "built-in default"
+        else:
+            split_source[name] = "flag"
     fhd.fhd_set_encrypt_route(args.encrypt_route)
     clip = si.clip(FRAMES, HGT, WID, CH, seed=rank)
     host = torch.from_numpy(clip).pin_memory()
@@ -694,7 +709,8 @@ def run_ours(args):
                        "sm_partition": {"lhcs_m_sms": enc.partition()[0], "other_sms": enc.partition()[1]},
                        "frames_per_step": FRAMES * world, "l2": "inputs larger than L2 (~560 MB live per step)",
                        "parallelism": f"replicas x{world} (independent streams)",
-                       "strip_width": tuned.get(f"{HGT}x{WID}x{CH}")},
+                       "strip_width": tuned[f"{HGT}x{WID}x{CH}"]["P"], "row_band": tuned[f"{HGT}x{WID}x{CH}"]["RB"],
+                       "tile_source": tuned[f"{HGT}x{WID}x{CH}"]["source"], "work_split_source": split_source},
             "verified_round_trip": bool(verified) and bool(e2e_ok) and bool(alone_ok),
             "kernels_alone_ms": {k: v[0] / v[1] for k, v in alone.items() if v[1]},
             "e2e": {"value": world * FRAMES / (e2e_ms / 1000.0), "unit": "frames/s",
@@ -1100,8 +1116,45 @@ def run_dry(args):
     return 0
 
 
+def run_tune(args):
+    """Tile shapes of every workload's frame sizes (timed afresh), then the clip pipeline's work split: the
+    headline under each candidate setting, each in its own process (a bench run of 15 steps, median of three
+    timed regions); the table goes to args.tune."""
+    import torch
+    from paper_2505_07158_gb300 import autotune
+    torch.cuda.set_device(0)
+    shapes = [(HGT, WID, CH)] + MIXED + SERVE_RES + [(4320, 7680, 3)]
+    tuned = autotune.tune(sorted(set(shapes)), force=True)
+    cache = autotune.load_cache()
+    gpu = autotune._gpu_name()
+    entries = {k: cache[gpu]["shapes"][k] for k in tuned}
+    grid = [("throughput", i, w) for i in (3, 4, 5, 6) for w in (2, 3, 4) if w < i] + [("latency", 5, 3)]
+    results = {}
+    for layout, inflight, window in grid:
+        cmd = [sys.executable, os.path.abspath(__file__), "--no-extras", "--no-cpu-baseline", "--no-probe",
+               "--steps", "15", "--repeats", "3", "--layout", layout, "--inflight", str(inflight),
+               "--worker-window", str(window)]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+        v = json.loads(lines[-1])["value"] if r.returncode == 0 and lines else None
+        results[f"{layout}/{inflight}/{window}"] = v
+        print(f"pipeline {layout} inflight={inflight} window={window}: {v}", flush=True)
+    best = max((k for k in results if results[k]), key=lambda k: results[k])
+    layout, inflight, window = best.split("/")
+    pipeline = {"layout": layout, "inflight": int(inflight), "worker_window": int(window),
+                "frames_per_s": results[best], "candidates": results,
+                "how": "bench.py headline, 15 steps, median of 3 timed regions per candidate, one process each"}
+    table = {gpu: {"shapes": entries, "pipeline": pipeline}}
+    with open(args.tune, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+    print(json.dumps(table))
+    return 0
+
+
 def main():
     args = parse()
+    if args.tune:
+        return run_tune(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:

@@ -356,6 +356,12 @@ int fhd_permute_decrypt(const uint8_t *src, uint8_t *dst, uint32_t height, uint3
 uint32_t fhd_strip_width(uint32_t height, uint32_t width, uint32_t channels);
 int fhd_set_strip_width(uint32_t height, uint32_t width, uint32_t channels, uint32_t P);
 
+/* Rows per CTA of the row pass for this shape, and its autotuner override
+ * (1..64 rows; 0 restores the built-in choice, bands of about 32 KB of shared
+ * memory).  An override whose band does not fit shared memory is ignored. */
+uint32_t fhd_row_band(uint32_t height, uint32_t width, uint32_t channels);
+int fhd_set_row_band(uint32_t height, uint32_t width, uint32_t channels, uint32_t RB);
+
 /* Route of the encryption's confusion + XOR (Sec. II-C), bit-identical either
  * way, process-wide.  FHD_ROUTE_TWO_PASS (default): a row pass (row
  * rotations, whole rows staged in shared memory) writes the row-rotated frame

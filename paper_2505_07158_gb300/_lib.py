@@ -40,7 +40,7 @@ EXPORTS = (
     "fhd_stats_correlation", "fhd_stats_local_entropy", "encrypt_frames_sched", "decrypt_frames_sched",
     "fhd_frame_digest_tree", "fhd_fp64_probe", "fhd_set_encrypt_route", "encrypt_frames_persistent",
     "decrypt_frames_persistent", "cipher_round_trip_persistent", "cipher_set_persistent_limits",
-    "cipher_set_worker_cta", "cipher_persistent_trace",
+    "cipher_set_worker_cta", "cipher_persistent_trace", "fhd_row_band", "fhd_set_row_band",
 )
 KERNEL_KINDS = ("sha", "master", "keystream", "encrypt", "decrypt")
 
@@ -114,6 +114,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "fhd_permute_decrypt": (i32, [P, P, u32, u32, u32, P, P, P]),
             "fhd_strip_width": (u32, [u32, u32, u32]),
             "fhd_set_strip_width": (i32, [u32, u32, u32, u32]),
+            "fhd_row_band": (u32, [u32, u32, u32]),
+            "fhd_set_row_band": (i32, [u32, u32, u32, u32]),
             "fhd_version": (ctypes.c_char_p, []),
             "cipher_profile": (i32, [P, i32]),
             "cipher_profile_read": (i32, [P, P, P]),
@@ -609,6 +611,14 @@ def fhd_strip_width(height: int, width: int, channels: int) -> int:
 
 def fhd_set_strip_width(height: int, width: int, channels: int, P: int):
     _check(load().fhd_set_strip_width(height, width, channels, P))
+
+
+def fhd_row_band(height: int, width: int, channels: int) -> int:
+    return int(load().fhd_row_band(height, width, channels))
+
+
+def fhd_set_row_band(height: int, width: int, channels: int, RB: int):
+    _check(load().fhd_set_row_band(height, width, channels, RB))
 
 
 def fhd_frame_scratch_bytes(n_workers: int, height: int, width: int, channels: int) -> int:

@@ -1,16 +1,23 @@
-"""Autotuner for the strip width of the fused permutation kernels.
+"""Autotuner of the permutation's tile shapes and of the clip pipeline's work split.
 
-The column pass of the confusion + XOR gives each CTA a full-height strip of
-P pixel columns held in shared memory.  Wide strips amortise the per-row gather
-overhead; narrow strips let two or more CTAs share an SM and hide memory
-latency.  The best P depends on the frame shape, so it is measured: for each
-(height, width, channels) every power-of-two P whose strip fits shared memory
-is timed (encrypt + decrypt per frame of a batch of up to 30 frames, CUDA
-events, median of several runs), the fastest is installed in the library with ``fhd_set_strip_width``
-and remembered in a JSON cache keyed by the GPU name.
+Per frame shape (height, width, channels) it chooses, by timing:
 
-The chosen P only changes the schedule: outputs are bit-identical for every P
-(the GPU tests check this)."""
+* P, the strip width of the column pass: each CTA holds a full-height strip of P pixel columns in shared
+  memory.  Wide strips amortise the per-row work; narrow ones let two or more CTAs share an SM and hide
+  memory latency.  Every power-of-two P whose strip fits is timed.
+* RB, the rows per CTA of the row pass (bands of whole rows staged in shared memory), at the chosen P.
+
+Each candidate is timed as the batched encrypt + decrypt permutation launches per frame of a batch of up to
+30 frames (CUDA events the library records on the launch stream, median of several runs); the fastest is
+installed with ``fhd_set_strip_width`` / ``fhd_set_row_band``.  Outputs are bit-identical for every
+choice (the GPU tests check this).
+
+The clip pipeline's work split (worker warp layout, clips in flight, worker window) is tuned by
+``bench.py --tune``, which times the headline under each setting and stores the best here.
+
+Two tables, both keyed by the GPU name: ``tuned.json`` beside this file holds the choices measured on the
+GPUs this library was tuned on (committed with it, so a fresh machine of the same kind starts from them),
+and ``_build/autotune.json`` holds this machine's own measurements of shapes not in the first."""
 from __future__ import annotations
 
 import json
@@ -21,7 +28,9 @@ import torch
 
 from . import _lib
 
-DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+HERE = os.path.dirname(os.path.abspath(__file__))
+COMMITTED = os.path.join(HERE, "tuned.json")
+DEFAULT_CACHE = os.path.join(HERE, "_build", "autotune.json")
 SMEM_LIMIT = 232448
 
 
@@ -34,6 +43,11 @@ def candidates(h: int, w: int, C: int):
             out.append(P)
         P *= 2
     return out
+
+
+def row_band_candidates(h: int, w: int, C: int):
+    pitch = (w * C + 15) & ~15
+    return [rb for rb in (1, 2, 4, 8, 16) if rb <= h and 2 * rb * pitch + 4 * rb * C <= SMEM_LIMIT]
 
 
 def _key(h, w, C):
@@ -60,13 +74,17 @@ def save_cache(cache: dict, path: str = DEFAULT_CACHE):
     os.replace(tmp, path)
 
 
-def time_shape(h: int, w: int, C: int, P: int, reps: int = 3, frames: int = 8) -> float:
-    """Milliseconds per frame of the batched encrypt + decrypt permutation launches at strip width P.
+def _shapes_of(table: dict, gpu: str) -> dict:
+    return table.get(gpu, {}).get("shapes", {})
 
-    The frames go through encrypt_frames / decrypt_frames exactly as in
-    production; only the permutation launches are timed (CUDA events the
-    library records on the launch stream).  A large worker count keeps the
-    chaotic chains short: the permutation kernels do not depend on it."""
+
+def time_shape(h: int, w: int, C: int, P: int, RB: int = 0, reps: int = 3, frames: int = 8) -> float:
+    """Milliseconds per frame of the batched encrypt + decrypt permutation launches at strip width P and
+    row band RB (0: the built-in band).
+
+    The frames go through encrypt_frames / decrypt_frames exactly as in production; only the permutation
+    launches are timed (CUDA events the library records on the launch stream).  A large worker count keeps
+    the chaotic chains short: the permutation kernels do not depend on it."""
     dev = torch.device("cuda", torch.cuda.current_device())
     g = torch.Generator(device=dev)
     g.manual_seed(h * 7919 + w * 31 + C)
@@ -79,6 +97,7 @@ def time_shape(h: int, w: int, C: int, P: int, reps: int = 3, frames: int = 8) -
     R = [torch.empty_like(f) for f in F]
     Hd = [torch.empty(32, dtype=torch.uint8, device=dev) for _ in F]
     _lib.fhd_set_strip_width(h, w, C, P)
+    _lib.fhd_set_row_band(h, w, C, RB)
     try:
         def once():
             enc.encrypt_frames([(sid, F[k], E[k], Hd[k]) for k in range(frames)])
@@ -93,10 +112,11 @@ def time_shape(h: int, w: int, C: int, P: int, reps: int = 3, frames: int = 8) -
             ts.append(t / frames)
         torch.cuda.synchronize()
         if not all(torch.equal(R[k], F[k]) for k in range(frames)):
-            raise RuntimeError(f"strip width {P} failed the round trip for {h}x{w}x{C}")
+            raise RuntimeError(f"strip width {P}, row band {RB} failed the round trip for {h}x{w}x{C}")
         return statistics.median(ts)
     finally:
         _lib.fhd_set_strip_width(h, w, C, 0)
+        _lib.fhd_set_row_band(h, w, C, 0)
         enc.close()
         dec.close()
 
@@ -108,35 +128,72 @@ def batch_frames(h: int, w: int, C: int) -> int:
     return max(4, min(30, int(1.5e9 // (h * w * C))))
 
 
-def tune_shape(h: int, w: int, C: int, reps: int = 7) -> tuple[int, dict]:
+def tune_shape(h: int, w: int, C: int, reps: int = 7) -> dict:
+    """Time every strip width, then every row band at the best width: {"P", "RB", "ms", "rb_ms"}."""
     n = batch_frames(h, w, C)
-    times = {P: time_shape(h, w, C, P, reps, frames=n) for P in candidates(h, w, C)}
+    times = {P: time_shape(h, w, C, P, 0, reps, frames=n) for P in candidates(h, w, C)}
     best = min(times, key=times.get)
-    return best, times
+    rb_times = {RB: time_shape(h, w, C, best, RB, reps, frames=n) for RB in row_band_candidates(h, w, C)}
+    rb = min(rb_times, key=rb_times.get) if rb_times else 0
+    return {"P": best, "RB": rb, "ms": {str(p): t for p, t in times.items()},
+            "rb_ms": {str(r): t for r, t in rb_times.items()}}
 
 
-def tune(shapes, cache_path: str = DEFAULT_CACHE, force: bool = False) -> dict:
-    """Tune (or fetch from the cache) every shape and install the choices."""
-    cache = load_cache(cache_path)
+def _install(h, w, C, entry):
+    _lib.fhd_set_strip_width(h, w, C, int(entry.get("P", 0)))
+    _lib.fhd_set_row_band(h, w, C, int(entry.get("RB", 0)))
+
+
+def tune(shapes, cache_path: str = DEFAULT_CACHE, force: bool = False, committed: str = COMMITTED) -> dict:
+    """Install the tile shapes of every shape: from the committed table for this GPU, else this machine's
+    cache, else by timing (recorded in the cache).  force=True times every shape again.  Returns
+    {shape key: {"P", "RB", "source"}}."""
     gpu = _gpu_name()
-    table = cache.setdefault(gpu, {})
+    fixed = {} if force else _shapes_of(load_cache(committed), gpu)
+    cache = load_cache(cache_path)
+    table = cache.setdefault(gpu, {}).setdefault("shapes", {})
     changed = False
+    out = {}
     for (h, w, C) in shapes:
         k = _key(h, w, C)
-        if force or k not in table:
-            best, times = tune_shape(h, w, C)
-            table[k] = {"P": best, "ms": {str(p): t for p, t in times.items()}}
+        if k in fixed:
+            entry, src = fixed[k], "committed"
+        elif not force and k in table and "RB" in table[k]:
+            entry, src = table[k], "cache"
+        else:
+            entry, src = tune_shape(h, w, C), "timed"
+            table[k] = entry
             changed = True
-        _lib.fhd_set_strip_width(h, w, C, table[k]["P"])
+        _install(h, w, C, entry)
+        out[k] = {"P": int(entry["P"]), "RB": int(entry.get("RB", 0)), "source": src}
     if changed:
         save_cache(cache, cache_path)
-    return {k: v["P"] for k, v in table.items()}
+    return out
 
 
-def apply_cache(cache_path: str = DEFAULT_CACHE):
-    """Install every cached choice for this GPU (no timing)."""
-    table = load_cache(cache_path).get(_gpu_name(), {})
-    for k, v in table.items():
+def apply_cache(cache_path: str = DEFAULT_CACHE, committed: str = COMMITTED) -> dict:
+    """Install every recorded choice for this GPU (no timing); the committed table wins."""
+    gpu = _gpu_name()
+    merged = dict(_shapes_of(load_cache(cache_path), gpu))
+    merged.update(_shapes_of(load_cache(committed), gpu))
+    for k, v in merged.items():
         h, w, C = (int(x) for x in k.split("x"))
-        _lib.fhd_set_strip_width(h, w, C, v["P"])
-    return table
+        _install(h, w, C, v)
+    return merged
+
+
+def pipeline_defaults(committed: str = COMMITTED) -> dict | None:
+    """The clip pipeline's tuned work split for this GPU ({"layout", "inflight", "worker_window", ...}), if
+    recorded."""
+    return load_cache(committed).get(_gpu_name(), {}).get("pipeline")
+
+
+def record(shapes: dict | None = None, pipeline: dict | None = None, committed: str = COMMITTED):
+    """Write tuned shapes ({key: entry}) and/or the pipeline's work split into the committed table."""
+    table = load_cache(committed)
+    ent = table.setdefault(_gpu_name(), {})
+    if shapes:
+        ent.setdefault("shapes", {}).update(shapes)
+    if pipeline:
+        ent["pipeline"] = pipeline
+    save_cache(table, committed)

@@ -485,7 +485,7 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
             d.P = fhd::strip_width(d.h, d.w, d.C);
             d.cta0 = ctas;
             ctas += fhd::permute_strips(d.w, d.P);
-            d.RB = fhd::row_band(d.w, d.C);
+            d.RB = fhd::row_band(d.h, d.w, d.C);
             d.rcta0 = rctas;
             rctas += (d.h + d.RB - 1) / d.RB;
         }
@@ -1342,7 +1342,7 @@ static int permute_one(const uint8_t *src, uint8_t *dst, uint32_t height, uint32
     d.P = fhd::strip_width(height, width, channels);
     d.cta0 = 0;
     b.perm_ctas = fhd::permute_strips(width, d.P);
-    d.RB = fhd::row_band(width, channels);
+    d.RB = fhd::row_band(height, width, channels);
     d.rcta0 = 0;
     b.row_ctas = (height + d.RB - 1) / d.RB;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1362,6 +1362,18 @@ int fhd_permute_encrypt(const uint8_t *src, uint8_t *dst, uint32_t height, uint3
 int fhd_permute_decrypt(const uint8_t *src, uint8_t *dst, uint32_t height, uint32_t width, uint32_t channels,
                         const uint16_t *D, const uint8_t *B, void *stream) {
     return permute_one(src, dst, height, width, channels, D, B, stream, false);
+}
+
+uint32_t fhd_row_band(uint32_t height, uint32_t width, uint32_t channels) {
+    if (!height || !width || !channels || channels > 4) return 0;
+    return fhd::row_band(height, width, channels);
+}
+
+int fhd_set_row_band(uint32_t height, uint32_t width, uint32_t channels, uint32_t RB) {
+    if (!height || !width || !channels || channels > 4 || RB > 64)
+        return fail(nullptr, FHD_ERR_INVALID_ARG, "bad row band override");
+    return fhd::set_row_band_override(height, width, channels, RB) == 0 ? FHD_OK
+                                                                          : fail(nullptr, FHD_ERR_TOO_LARGE, "override table full");
 }
 
 uint32_t fhd_strip_width(uint32_t height, uint32_t width, uint32_t channels) {

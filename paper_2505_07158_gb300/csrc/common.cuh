@@ -157,7 +157,7 @@ cudaError_t launch_permute(const Batch &b, bool encrypt, cudaStream_t s);
 uint32_t strip_width(uint32_t h, uint32_t w, uint32_t C);
 size_t strip_smem_bytes(uint32_t h, uint32_t P, uint32_t C);
 uint32_t permute_strips(uint32_t w, uint32_t P);
-uint32_t row_band(uint32_t w, uint32_t C);
+uint32_t row_band(uint32_t h, uint32_t w, uint32_t C);
 size_t row_smem_bytes(uint32_t w, uint32_t C, uint32_t RB);
 cudaError_t permute_prepare();   // opt in to large dynamic shared memory
 // Binary64 pipe probe (probe.cu): one CTA of 4 * warps_per_subpartition warps per SM; *lane_ops = binary64
@@ -165,6 +165,7 @@ cudaError_t permute_prepare();   // opt in to large dynamic shared memory
 cudaError_t launch_fp64_probe(uint32_t warps_per_subpartition, uint32_t iters, double *sink, uint64_t *lane_ops,
                               cudaStream_t s);
 int set_strip_override(uint32_t h, uint32_t w, uint32_t C, uint32_t P);
+int set_row_band_override(uint32_t h, uint32_t w, uint32_t C, uint32_t RB);
 int set_encrypt_route(int route);   // FHD_ROUTE_TWO_PASS or FHD_ROUTE_SINGLE_PASS; -1 on a bad value
 
 }  // namespace fhd

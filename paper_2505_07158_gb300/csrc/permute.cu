@@ -283,14 +283,6 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_encrypt_kernel(const
 
 size_t strip_smem_bytes(uint32_t h, uint32_t P, uint32_t C) { return ((size_t)h * P * C + 15) & ~(size_t)15; }
 
-uint32_t row_band(uint32_t w, uint32_t C) {
-    const size_t pitch = ((size_t)w * C + 15) & ~(size_t)15;
-    size_t rb = kRowSmemTarget / (2 * pitch + 16);
-    if (rb < 1) rb = 1;
-    if (rb > 16) rb = 16;
-    return (uint32_t)rb;
-}
-
 // Two row-sized buffers per row (input and output) and the row shifts.
 size_t row_smem_bytes(uint32_t w, uint32_t C, uint32_t RB) {
     const size_t pitch = ((size_t)w * C + 15) & ~(size_t)15;
@@ -299,22 +291,50 @@ size_t row_smem_bytes(uint32_t w, uint32_t C, uint32_t RB) {
 
 uint32_t permute_strips(uint32_t w, uint32_t P) { return (w + P - 1) / P; }
 
+// Autotuner overrides per frame shape: strip width P of the column pass and rows per CTA RB of the row
+// pass (0: the built-in choice).
 static uint32_t g_override_key[64][3];
 static uint32_t g_override_P[64];
+static uint32_t g_override_RB[64];
 static int g_overrides = 0;
 
-int set_strip_override(uint32_t h, uint32_t w, uint32_t C, uint32_t P) {
+static int override_slot(uint32_t h, uint32_t w, uint32_t C) {
     for (int k = 0; k < g_overrides; ++k)
-        if (g_override_key[k][0] == h && g_override_key[k][1] == w && g_override_key[k][2] == C) {
-            g_override_P[k] = P;
-            return 0;
-        }
+        if (g_override_key[k][0] == h && g_override_key[k][1] == w && g_override_key[k][2] == C) return k;
     if (g_overrides >= 64) return -1;
     g_override_key[g_overrides][0] = h;
     g_override_key[g_overrides][1] = w;
     g_override_key[g_overrides][2] = C;
-    g_override_P[g_overrides++] = P;
+    g_override_P[g_overrides] = g_override_RB[g_overrides] = 0;
+    return g_overrides++;
+}
+
+int set_strip_override(uint32_t h, uint32_t w, uint32_t C, uint32_t P) {
+    const int k = override_slot(h, w, C);
+    if (k < 0) return -1;
+    g_override_P[k] = P;
     return 0;
+}
+
+int set_row_band_override(uint32_t h, uint32_t w, uint32_t C, uint32_t RB) {
+    const int k = override_slot(h, w, C);
+    if (k < 0) return -1;
+    g_override_RB[k] = RB;
+    return 0;
+}
+
+// Bands of about kRowSmemTarget bytes of shared memory (2 rows at 1080p), 1..16 rows; an autotuner override
+// (if any and if it fits) wins.
+uint32_t row_band(uint32_t h, uint32_t w, uint32_t C) {
+    for (int k = 0; k < g_overrides; ++k)
+        if (g_override_key[k][0] == h && g_override_key[k][1] == w && g_override_key[k][2] == C && g_override_RB[k] &&
+            g_override_RB[k] <= 64 && row_smem_bytes(w, C, g_override_RB[k]) <= kSmemLimit)
+            return g_override_RB[k];
+    const size_t pitch = ((size_t)w * C + 15) & ~(size_t)15;
+    size_t rb = kRowSmemTarget / (2 * pitch + 16);
+    if (rb < 1) rb = 1;
+    if (rb > 16) rb = 16;
+    return (uint32_t)rb;
 }
 
 // Widest power-of-two strip (<= 128 pixels, no wider than the frame needs)
