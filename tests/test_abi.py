@@ -122,3 +122,23 @@ def test_digest_wrappers_reject_a_size_that_count_does_not_divide():
         fhd.fhd_frame_digest(data, n=2, count=3)
     with pytest.raises(ValueError, match="multiple of count"):
         fhd._lib.fhd_frame_digest_noalloc(data, torch.zeros(96, dtype=torch.uint8), n=2, count=3)
+
+
+def test_host_side_checks_of_the_persistent_and_tuning_calls(lib):
+    """The persistent launches, their limits and trace, the worker CTA size, the encryption route and the
+    row-band override reject bad arguments before any device work."""
+    import paper_2505_07158_gb300 as fhd
+    assert lib.encrypt_frames_persistent(None, 1, None, None) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.decrypt_frames_persistent(None, 1, None, None) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.cipher_round_trip_persistent(None, None, 1, None, None, None) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.cipher_set_persistent_limits(None, 10**9, -1) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.cipher_persistent_trace(None, 1, None) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.cipher_set_worker_cta(None, 4) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.fhd_set_encrypt_route(7) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.fhd_set_row_band(0, 16, 3, 2) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.fhd_set_row_band(16, 16, 3, 65) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.fhd_row_band(0, 16, 3) == 0
+    assert lib.fhd_set_row_band(24, 24, 3, 3) == fhd.FHD_OK
+    assert lib.fhd_row_band(24, 24, 3) == 3
+    assert lib.fhd_set_row_band(24, 24, 3, 0) == fhd.FHD_OK
+    assert lib.fhd_row_band(24, 24, 3) == 16

@@ -347,3 +347,20 @@ def _mixed_batches_match_oracle():
             assert bytes(host(it[3])) == H_ref
             assert np.array_equal(host(it[2]), E_ref)
         c.close()
+
+
+@pytest.mark.parametrize("RB", [1, 3, 7, 16, 64])
+def test_permute_row_band_overrides(RB):
+    """Every row band the autotuner may install (including bands taller than the frame, ragged last
+    bands and the byte-wise route of w % 4 != 0) gives the oracle's bytes both ways."""
+    for h, w, C in [(45, 64, 3), (45, 77, 3), (20, 36, 4)]:
+        fhd.fhd_set_row_band(h, w, C, RB)
+        try:
+            assert fhd.fhd_row_band(h, w, C) == RB
+            F, D, B = _rand(h, w, C, seed=RB + w)
+            E = fhd.fhd_permute_encrypt(to_dev(F), d16(D), to_dev(B))
+            assert np.array_equal(host(E), oracle.permute_encrypt(F, D, B)), (h, w, C)
+            Pd = fhd.fhd_permute_decrypt(E, d16(D), to_dev(B))
+            assert np.array_equal(host(Pd), F), (h, w, C)
+        finally:
+            fhd.fhd_set_row_band(h, w, C, 0)
