@@ -137,3 +137,41 @@ def test_withheld_dependency_times_out_and_the_device_recovers():
         assert np.array_equal(host(di[k][2]), F), k
     enc.close()
     dec.close()
+
+
+def test_long_streams_and_mixed_sizes_within_a_stream():
+    """Streams with many frames in one launch, whose frames differ in size (a stream's first frame the
+    largest, so its LHCS_m task must be queued ahead of its later, smaller frames' worker warps), with the
+    maximum of 64 frames: every ciphertext and digest equals the oracle's, and every frame round-trips."""
+    sizes = [(40, 64, 3), (24, 32, 3), (16, 16, 3), (8, 48, 1)]
+    keys = [si.key(1700 + k) for k in range(3)]
+    enc = fhd.Cipher(keys[0], n_workers=6)
+    dec = fhd.Cipher(keys[0], n_workers=6)
+    sids = [enc.open_stream(k) for k in keys]
+    rids = [dec.open_stream(k) for k in keys]
+    ei, di, frames, owner = [], [], [], []
+    for t in range(64):
+        st = 0 if t < 30 else (1 if t < 50 else 2)      # 30, 20 and 14 frames
+        s = sizes[0] if t in (0, 30, 50) else sizes[(t * 7) % 4]
+        F = si.gradient_frame(*s, t=t, seed=17)
+        Fd = to_dev(F)
+        E, R = torch.empty_like(Fd), torch.empty_like(Fd)
+        H = torch.empty(32, dtype=torch.uint8, device=dev())
+        ei.append((sids[st], Fd, E, H))
+        di.append((rids[st], E, R, H))
+        frames.append(F)
+        owner.append(st)
+    enc.round_trip_persistent(dec, ei, di)
+    torch.cuda.synchronize()
+    enc.sync_status()
+    dec.sync_status()
+    refs = [oracle.Stream.from_key(k, n=6) for k in keys]
+    for k, F in enumerate(frames):
+        E_ref, H_ref = refs[owner[k]].encrypt(F)
+        assert np.array_equal(host(ei[k][2]), E_ref), k
+        assert bytes(host(ei[k][3])) == H_ref, k
+        assert np.array_equal(host(di[k][2]), F), k
+    with pytest.raises(fhd.FhdError):       # more than 64 frames in one launch
+        enc.round_trip_persistent(dec, ei + ei[:1], di + di[:1])
+    enc.close()
+    dec.close()
