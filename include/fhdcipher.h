@@ -497,6 +497,38 @@ uint64_t fhd_launch_count(void);
 /* Library version string. */
 const char *fhd_version(void);
 
+/* ---- Checked build (range checks of every computed index) ----
+ * The library can be compiled with -DFHD_BOUNDS_CHECK (libfhdcipher_checked.so beside the default
+ * library).  In that build each global or shared-memory access of a kernel whose index is computed from
+ * the frame geometry, the keystream, the launch descriptor or a task queue is first compared with the
+ * extent of its buffer; an access that fails is counted and skipped (a skipped load reads 0, a skipped
+ * store writes nothing), nothing traps, and the kernel runs to its end.  Results of a call in which a
+ * check failed are void.  cipher_sync_status of a checked build also returns FHD_ERR_STATE when a check
+ * has failed since the last report.  Identical results and no failed check on valid input are what the
+ * checked build's tests assert. */
+
+/* Build options of the loaded library: FHD_BUILD_BOUNDS_CHECK when it is the checked build. */
+#define FHD_BUILD_BOUNDS_CHECK 1u
+uint32_t fhd_build_flags(void);
+
+/* Synchronise the device, then read and clear the bounds records of every kernel of the library:
+ * *count = accesses that failed their range check since the last report; of the first of them, *site (a
+ * code that fhd_bounds_site_name describes), *index and *limit (the checked index and the extent it had
+ * to stay below, in elements of the buffer).  Any out pointer may be NULL.  In the default build every
+ * output is 0 and nothing is synchronised.  Returns FHD_OK or FHD_ERR_CUDA. */
+int fhd_bounds_report(uint32_t *count, uint32_t *site, uint64_t *index, uint64_t *limit);
+
+/* Description of a bounds-check site ("column pass: frame store", ...); "unknown site" otherwise. */
+const char *fhd_bounds_site_name(uint32_t site);
+
+/* Checked build: run the encryption's permutation kernels (row pass, column pass) on a 16 x 64 x 3 frame
+ * whose descriptor declares one row fewer than its buffers hold, so that the checks of the last row's
+ * accesses fail and those accesses are skipped.  Every buffer is allocated at its full size, so no access
+ * leaves its allocation either way.  The bounds records are cleared first; *count and *site (either may
+ * be NULL) are fhd_bounds_report's afterwards.  Runs on `stream` and synchronises it.  Returns
+ * FHD_ERR_STATE in the default build, FHD_ERR_OOM or FHD_ERR_CUDA on failure. */
+int fhd_bounds_selftest(uint32_t *count, uint32_t *site, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

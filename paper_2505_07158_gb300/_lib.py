@@ -40,8 +40,10 @@ EXPORTS = (
     "fhd_stats_correlation", "fhd_stats_local_entropy", "encrypt_frames_sched", "decrypt_frames_sched",
     "fhd_frame_digest_tree", "fhd_fp64_probe", "fhd_set_encrypt_route", "encrypt_frames_persistent",
     "decrypt_frames_persistent", "cipher_round_trip_persistent", "cipher_set_persistent_limits",
-    "cipher_set_worker_cta", "cipher_persistent_trace", "fhd_row_band", "fhd_set_row_band",
+    "cipher_set_worker_cta", "cipher_persistent_trace", "fhd_row_band", "fhd_set_row_band", "fhd_build_flags",
+    "fhd_bounds_report", "fhd_bounds_site_name", "fhd_bounds_selftest",
 )
+FHD_BUILD_BOUNDS_CHECK = 1
 KERNEL_KINDS = ("sha", "master", "keystream", "encrypt", "decrypt")
 
 
@@ -83,13 +85,18 @@ _lock = threading.Lock()
 _lib = None
 
 
+def checked_requested() -> bool:
+    """True when FHD_CHECKED=1 asks for the checked build (range checks of every computed index)."""
+    return os.environ.get("FHD_CHECKED", "0") not in ("", "0")
+
+
 def load(path: str | None = None) -> ctypes.CDLL:
-    """Load (building first if needed) the in-tree library."""
+    """Load (building first if needed) the in-tree library: the checked build when FHD_CHECKED=1."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        lib = ctypes.CDLL(path or _build.build())
+        lib = ctypes.CDLL(path or _build.build(checked=checked_requested()))
         P, u32, u64, dbl, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double, ctypes.c_int
         PP = ctypes.POINTER(ctypes.c_void_p)
         sig = {
@@ -145,6 +152,11 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "cipher_set_persistent_limits": (i32, [P, u64, i32]),
             "cipher_set_worker_cta": (i32, [P, u32]),
             "cipher_persistent_trace": (i32, [P, u32, P]),
+            "fhd_build_flags": (u32, []),
+            "fhd_bounds_report": (i32, [ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.POINTER(u64),
+                                        ctypes.POINTER(u64)]),
+            "fhd_bounds_site_name": (ctypes.c_char_p, [u32]),
+            "fhd_bounds_selftest": (i32, [ctypes.POINTER(u32), ctypes.POINTER(u32), P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -155,7 +167,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
 
 
 def library_path() -> str:
-    return _build.LIB
+    return _build.CHECKED_LIB if checked_requested() else _build.LIB
 
 
 def _check(code: int, handle=None):
@@ -627,6 +639,34 @@ def fhd_frame_scratch_bytes(n_workers: int, height: int, width: int, channels: i
 
 def fhd_launch_count() -> int:
     return int(load().fhd_launch_count())
+
+
+def fhd_build_flags() -> int:
+    """FHD_BUILD_BOUNDS_CHECK when the loaded library is the checked build."""
+    return int(load().fhd_build_flags())
+
+
+def fhd_bounds_report() -> dict:
+    """Read and clear the checked build's bounds records: {"count", "site", "site_name", "index", "limit"}
+    (count 0 in the default build)."""
+    cnt, site, idx, lim = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint64(), ctypes.c_uint64()
+    lib = load()
+    _check(lib.fhd_bounds_report(ctypes.byref(cnt), ctypes.byref(site), ctypes.byref(idx), ctypes.byref(lim)))
+    return {"count": int(cnt.value), "site": int(site.value),
+            "site_name": lib.fhd_bounds_site_name(site.value).decode(), "index": int(idx.value),
+            "limit": int(lim.value)}
+
+
+def fhd_bounds_site_name(site: int) -> str:
+    return load().fhd_bounds_site_name(site).decode()
+
+
+def fhd_bounds_selftest(stream=None) -> tuple[int, int]:
+    """Checked build: the permutation on a frame whose descriptor is one row short of its buffers; returns
+    (failed checks, first site)."""
+    cnt, site = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(load().fhd_bounds_selftest(ctypes.byref(cnt), ctypes.byref(site), _stream_ptr(stream)))
+    return int(cnt.value), int(site.value)
 
 
 def fhd_version() -> str:

@@ -744,9 +744,122 @@ int run_persistent(fhd_cipher *c0, fhd_cipher *c1, uint32_t count, const fhd_fra
     return FHD_OK;
 }
 
+#ifdef FHD_BOUNDS_CHECK
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
+// The bounds records of every translation unit with kernels, read and cleared (the caller has synchronised).
+cudaError_t take_all_bounds(fhd::BoundsRecord &r) {
+    r = fhd::BoundsRecord{};
+    cudaError_t (*const takers[])(fhd::BoundsRecord *) = {fhd::take_bounds_sha, fhd::take_bounds_chaos,
+                                                          fhd::take_bounds_permute, fhd::take_bounds_persist,
+                                                          fhd::take_bounds_stats};
+    for (auto t : takers) {
+        cudaError_t e = t(&r);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+std::string bounds_message(const fhd::BoundsRecord &r) {
+    return std::to_string(r.count) + " range check(s) failed; first: " + fhd::bounds_site_name(r.site) +
+           ", index " + std::to_string(r.index) + " of " + std::to_string(r.limit);
+}
+
 }  // namespace
 
+namespace fhd {
+const char *bounds_site_name(unsigned site) {
+    switch (site) {
+        case kSiteShaMessage: return "digest: sub-frame message outside its frame";
+        case kSiteShaBlock: return "digest: message block past the message";
+        case kSiteShaDigest: return "digest: frame index past the batch";
+        case kSiteMasterIR: return "LHCS_m: iterate past 2n x 4";
+        case kSiteMasterFrame: return "LHCS_m: frame index past the batch";
+        case kSiteWorkerIR: return "worker: initial value past the iterates";
+        case kSiteWorkerD: return "worker: shift-distance byte past C (h + w) entries";
+        case kSiteWorkerB: return "worker: XOR byte past the frame";
+        case kSiteRowLoad: return "row pass: frame load";
+        case kSiteRowShift: return "row pass: row shift load";
+        case kSiteRowSmem: return "row pass: shared-memory band or shift table";
+        case kSiteRowStore: return "row pass: frame store";
+        case kSiteStripShift: return "column pass: column shift load";
+        case kSiteStripLoad: return "column pass: frame or keystream load";
+        case kSiteStripSmem: return "column pass: shared-memory strip";
+        case kSiteStripStore: return "column pass: frame store";
+        case kSiteGatherShift: return "single pass: shift distance or rotation table";
+        case kSiteGatherLoad: return "single pass: frame load";
+        case kSiteGatherSmem: return "single pass: staging buffer or strip";
+        case kSiteGatherStore: return "single pass: keystream load or ciphertext store";
+        case kSitePersistTask: return "persistent launch: task outside the launch";
+        case kSiteStats: return "statistics: frame load past the batch";
+        default: return "unknown site";
+    }
+}
+}  // namespace fhd
+
 extern "C" {
+
+uint32_t fhd_build_flags(void) { return kChecked ? FHD_BUILD_BOUNDS_CHECK : 0u; }
+
+const char *fhd_bounds_site_name(uint32_t site) { return fhd::bounds_site_name(site); }
+
+int fhd_bounds_report(uint32_t *count, uint32_t *site, uint64_t *index, uint64_t *limit) {
+    fhd::BoundsRecord r{};
+    if (kChecked) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = take_all_bounds(r);
+        if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("bounds report: ") + cudaGetErrorString(e));
+    }
+    if (count) *count = r.count;
+    if (site) *site = r.site;
+    if (index) *index = r.index;
+    if (limit) *limit = r.limit;
+    return FHD_OK;
+}
+
+int fhd_bounds_selftest(uint32_t *count, uint32_t *site, void *stream) {
+    if (!kChecked) return fail(nullptr, FHD_ERR_STATE, "not a bounds-checked build");
+    constexpr uint32_t h = 16, w = 64, C = 3;
+    constexpr uint64_t N = (uint64_t)h * w * C;
+    cudaStream_t s = (cudaStream_t)stream;
+    fhd::BoundsRecord r{};
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = take_all_bounds(r);   // start from clear records
+    if (e == cudaSuccess) e = prepare_device();
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("selftest: ") + cudaGetErrorString(e));
+    uint8_t *buf = nullptr;   // F, E, B, G (N bytes each) and D (C (h + w) 16-bit entries), all full size
+    const size_t bytes = 4 * N + 2ull * C * (h + w);
+    if ((e = cudaMalloc(&buf, bytes)) != cudaSuccess) return fail(nullptr, FHD_ERR_OOM, "selftest buffers");
+    static thread_local Batch b;
+    std::memset(&b, 0, sizeof b);
+    b.count = 1;
+    FrameDesc &d = b.f[0];
+    d.src = buf;
+    d.dst = buf + N;
+    d.B = buf + 2 * N;
+    d.G = buf + 3 * N;
+    d.D = reinterpret_cast<uint16_t *>(buf + 4 * N);
+    d.h = h;
+    d.w = w;
+    d.C = C;
+    d.N = N - (uint64_t)w * C;   // the descriptor's extent: one row short of the buffers
+    d.P = fhd::strip_width(h, w, C);
+    b.perm_ctas = fhd::permute_strips(w, d.P);
+    d.RB = fhd::row_band(h, w, C);
+    b.row_ctas = (h + d.RB - 1) / d.RB;
+    e = cudaMemsetAsync(buf, 0x5a, bytes, s);
+    if (e == cudaSuccess) e = fhd::launch_permute(b, true, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = take_all_bounds(r);
+    cudaFree(buf);
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("selftest: ") + cudaGetErrorString(e));
+    if (count) *count = r.count;
+    if (site) *site = r.site;
+    return FHD_OK;
+}
 
 const char *fhd_version(void) { return "fhdcipher 0.1 (sm_103a)"; }
 
@@ -1005,6 +1118,12 @@ int cipher_sync_status(fhd_cipher *c, void *stream) {
     if (e != cudaSuccess) return cuda_fail(c, e, "read status");
     if (st & fhd::kStatusTimeout) return fail(c, FHD_ERR_TIMEOUT, "a bounded device wait timed out");
     if (st) return fail(c, FHD_ERR_STATE, "device status word " + std::to_string(st));
+    if (kChecked) {
+        fhd::BoundsRecord r{};
+        if ((e = cudaDeviceSynchronize()) == cudaSuccess) e = take_all_bounds(r);
+        if (e != cudaSuccess) return cuda_fail(c, e, "read bounds records");
+        if (r.count) return fail(c, FHD_ERR_STATE, bounds_message(r));
+    }
     return FHD_OK;
 }
 

@@ -111,3 +111,5 @@ cudaError_t launch_keystream(const Batch &b, cudaStream_t s, bool dense, uint32_
 }
 
 }  // namespace fhd
+
+FHD_BOUNDS_TAKER(take_bounds_chaos)

@@ -2,6 +2,7 @@
 // and the persistent batch kernel: the lane-packed RK4 steps, the reconstruction, LHCS_m of one stream and
 // one warp of worker pairs.  See chaos.cu for the design.
 #pragma once
+#include "bounds.cuh"
 #include "common.cuh"
 #include "sha256_core.cuh"
 
@@ -164,7 +165,7 @@ __device__ void master_frame(double &s, int lane, const LaneRole &role, const ui
     __syncwarp();
     for (uint32_t t = 0; t < 2 * n; ++t) {
         rk4_step_lanes(s, role, c);
-        if (lane < 4) IR[4 * t + lane] = s;
+        if (lane < 4 && FHD_IN(4 * t + lane, 8ull * n, kSiteMasterIR)) IR[4 * t + lane] = s;
     }
 }
 
@@ -209,8 +210,9 @@ __device__ __forceinline__ WorkerSlice worker_slice(uint64_t LD, uint64_t LB, ui
 
 // Bytes of one step: the pair's XOR of the 6 low mantissa bytes of each
 // variable; this lane writes its half (3 bytes) at stream position pos0 on.
+// dlim and blim are the bytes of D and of B from Dbytes and Bp on (range checks of checked builds).
 __device__ __forceinline__ void emit_bytes(double s, bool active, uint64_t pos0, uint64_t need, uint64_t ndb, int half,
-                                           uint8_t *Dbytes, uint8_t *Bp) {
+                                           uint8_t *Dbytes, uint8_t *Bp, uint64_t dlim, uint64_t blim) {
     const unsigned long long mine = (unsigned long long)__double_as_longlong(s) & 0xffffffffffffull;
     const unsigned long long x = mine ^ __shfl_xor_sync(0xffffffffu, mine, 4);
     if (active && pos0 < need) {
@@ -218,8 +220,11 @@ __device__ __forceinline__ void emit_bytes(double s, bool active, uint64_t pos0,
         for (int bb = 0; bb < 3; ++bb) {
             const uint64_t pos = pos0 + half + bb;
             const uint8_t byte = (uint8_t)(x >> (8 * (half + bb)));
-            if (pos < ndb) Dbytes[pos] = byte;
-            else if (pos < need) Bp[pos - ndb] = byte;
+            if (pos < ndb) {
+                if (FHD_IN(pos, dlim, kSiteWorkerD)) Dbytes[pos] = byte;
+            } else if (pos < need) {
+                if (FHD_IN(pos - ndb, blim, kSiteWorkerB)) Bp[pos - ndb] = byte;
+            }
         }
     }
 }
@@ -240,17 +245,19 @@ __device__ void keystream_warp(const FrameDesc &fd, uint32_t n, const Rk4 &c, ui
     // Uniform trip count: the longest slice of the frame.
     const uint64_t need_max = 2 * ((LD + n - 1) / n) + (LB + n - 1) / n;
     const uint64_t T = (need_max + 23) / 24;
-    const double chain_value = active ? __ldcg(fd.IR + 4 * (2 * p + (ch & 1)) + v) : 0.0;   // written by LHCS_m
+    const uint32_t ir = 4 * (2 * p + (ch & 1)) + v;
+    const double chain_value = active && FHD_IN(ir, 8ull * n, kSiteWorkerIR) ? __ldcg(fd.IR + ir) : 0.0;   // by LHCS_m
     uint8_t *Dbytes = reinterpret_cast<uint8_t *>(fd.D) + 2 * ws.d0;
     uint8_t *Bp = fd.B + ws.b0;
     const uint64_t ndb = 2 * ws.nd;
+    const uint64_t dlim = 2 * LD - 2 * ws.d0, blim = LB - ws.b0;
     const int half = (ch & 1) * 3;
     if (kPairs == kPairsPerWarp) {
         const LaneRole role = lane_role(lane, fd.gamma);
         double s = lane_init(lane, chain_value);
         for (uint64_t t = 0; t < T; ++t) {
             rk4_step_lanes(s, role, c);
-            emit_bytes(s, active, 24 * t + 6 * v, need, ndb, half, Dbytes, Bp);
+            emit_bytes(s, active, 24 * t + 6 * v, need, ndb, half, Dbytes, Bp, dlim, blim);
         }
     } else {
         // The bytes of step t (the state after it) are emitted during step t + 1, and the last step's after
@@ -259,10 +266,10 @@ __device__ void keystream_warp(const FrameDesc &fd, uint32_t n, const Rk4 &c, ui
         double s = chain_value;
         for (uint64_t t = 0; t < T; ++t) {
             rk4_step_lanes8(s, role, c, [&](double prev) {
-                if (t) emit_bytes(prev, active, 24 * (t - 1) + 6 * v, need, ndb, half, Dbytes, Bp);
+                if (t) emit_bytes(prev, active, 24 * (t - 1) + 6 * v, need, ndb, half, Dbytes, Bp, dlim, blim);
             });
         }
-        if (T) emit_bytes(s, active, 24 * (T - 1) + 6 * v, need, ndb, half, Dbytes, Bp);
+        if (T) emit_bytes(s, active, 24 * (T - 1) + 6 * v, need, ndb, half, Dbytes, Bp, dlim, blim);
     }
 }
 
@@ -283,6 +290,7 @@ __device__ void master_stream(const BatchT &b, uint32_t g, StreamState *states, 
     double s = lane_init(lane, lane < 4 ? st->v[lane] : 0.0);
     uint32_t done = 0;
     for (uint32_t k = first; k < last; ++k) {
+        if (!FHD_IN(b.order[k], b.count, kSiteMasterFrame)) break;
         const FrameDesc &fd = b.f[b.order[k]];
         if (!before(b.order[k])) break;   // a dependency of the frame did not arrive (a bounded wait gave up)
         if (lane < 8)   // the frame's digest: folded by the digest stage, or the transmitted one

@@ -121,6 +121,48 @@ enum : unsigned {
     kStatusBounds = 1u << 2,     // a bounds check failed (checked builds)
 };
 
+// Bounds record of a checked build (-DFHD_BOUNDS_CHECK; bounds.cuh): how many accesses failed their range
+// check, and the first one's site, index and extent.  Each translation unit with kernels keeps its own.
+struct BoundsRecord {
+    unsigned count, site;
+    unsigned long long index, limit;
+};
+
+// Sites of the range checks (the buffer and the access that failed).
+enum : unsigned {
+    kSiteShaMessage = 1,     // a sub-frame message outside its frame
+    kSiteShaBlock = 2,       // a message block load past the message
+    kSiteShaDigest = 3,      // a sub-frame digest slot past the frame's n slots, or a frame index past the batch
+    kSiteMasterIR = 10,      // an LHCS_m iterate past the frame's 2n x 4
+    kSiteMasterFrame = 11,   // a stream group's frame index past the batch
+    kSiteWorkerIR = 12,      // a worker chain's initial value past the frame's iterates
+    kSiteWorkerD = 13,       // a shift-distance byte past C (h + w) entries
+    kSiteWorkerB = 14,       // an XOR byte past the frame
+    kSiteRowLoad = 20,       // row pass: frame (F or G) load
+    kSiteRowShift = 21,      // row pass: row shift distance (D) load
+    kSiteRowSmem = 22,       // row pass: shared-memory band or shift table
+    kSiteRowStore = 23,      // row pass: frame (G or output) store
+    kSiteStripShift = 30,    // column pass: column shift distance (D) load
+    kSiteStripLoad = 31,     // column pass: frame (G or E) or B load
+    kSiteStripSmem = 32,     // column pass: shared-memory strip
+    kSiteStripStore = 33,    // column pass: frame store
+    kSiteGatherShift = 40,   // single pass: shift distance or rotation table
+    kSiteGatherLoad = 41,    // single pass: F load
+    kSiteGatherSmem = 42,    // single pass: staging buffer or strip
+    kSiteGatherStore = 43,   // single pass: B load or E store
+    kSitePersistTask = 50,   // persistent launch: a task's frame, side or index outside the launch
+    kSiteStats = 60,         // statistics: a frame load past the batch
+};
+const char *bounds_site_name(unsigned site);
+
+// Read and clear the bounds record of each translation unit with kernels, added into *acc (the first
+// violation kept is the first unit's).  Without FHD_BOUNDS_CHECK they add nothing.
+cudaError_t take_bounds_sha(BoundsRecord *acc);
+cudaError_t take_bounds_chaos(BoundsRecord *acc);
+cudaError_t take_bounds_permute(BoundsRecord *acc);
+cudaError_t take_bounds_persist(BoundsRecord *acc);
+cudaError_t take_bounds_stats(BoundsRecord *acc);
+
 // Launchers (one per kernel family); each returns the launch error.
 cudaError_t launch_sha_subframes(const Batch &b, cudaStream_t s);
 cudaError_t launch_verify(const Batch &b, uint8_t *ok, cudaStream_t s);   // ok[f.slot] per frame

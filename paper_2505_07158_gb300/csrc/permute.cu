@@ -130,7 +130,9 @@ __device__ __forceinline__ void gather_phase1(const FrameDesc &fd, uint32_t j0, 
     uint32_t ab[8];   // strip offset of byte m of source row 0: its rotated row s_v, times RP, plus its column
 #pragma unroll
     for (int m = 0; m < 8; ++m)
-        ab[m] = (unit ? modH.mod(fd.D[3ull * h + (uint64_t)c * w + j0 + 8 * g + m]) : 0) * RP + (8 * g + m) * 3 + c;
+        ab[m] = (unit && FHD_IN((uint64_t)c * w + j0 + 8 * g + m, 3ull * w, kSiteGatherShift)
+                     ? modH.mod(fd.D[3ull * h + (uint64_t)c * w + j0 + 8 * g + m])
+                     : 0) * RP + (8 * g + m) * 3 + c;
     const uint32_t rows_per_it = GS::RW * kGatherWarps;
     const uint32_t iters = (h + rows_per_it - 1) / rows_per_it;
     const uint8_t *src = fd.src;
@@ -143,12 +145,13 @@ __device__ __forceinline__ void gather_phase1(const FrameDesc &fd, uint32_t j0, 
         fs = 32;
         if (lane < GS::NW && i < h) {
             RowRot r;
+            const bool ok = FHD_IN(wc * h + i, 3 * h, kSiteGatherShift);
             if (tab) {
-                const uint32_t v = tab[wc * h + i];
+                const uint32_t v = ok ? tab[wc * h + i] : 0;
                 r.du = v >> 5;
                 r.fs = (v & 31) + 1;
             } else {
-                r = row_rot(fd.D[(uint64_t)wc * h + i], w, modW8);
+                r = row_rot(ok ? fd.D[(uint64_t)wc * h + i] : 0, w, modW8);
             }
             uint32_t us = (j0 >> 2) + r.du;
             us = us >= W4 ? us - W4 : us;
@@ -183,7 +186,8 @@ __device__ __forceinline__ void gather_phase1(const FrameDesc &fd, uint32_t j0, 
                 if (short_row)
                     while (o >= rowB) o -= rowB;
                 // F rows serve several strips: keep them in L2
-                reg[k] = __ldcg(reinterpret_cast<const uint4 *>(src + i * rowB + o));
+                if (FHD_IN((uint64_t)i * rowB + o + 15, fd.N, kSiteGatherLoad))
+                    reg[k] = __ldcg(reinterpret_cast<const uint4 *>(src + i * rowB + o));
             }
         }
     };
@@ -206,7 +210,7 @@ __device__ __forceinline__ void gather_phase1(const FrameDesc &fd, uint32_t j0, 
         const uint32_t uoff = __shfl_sync(0xffffffffu, cur_off, uwi < GS::NW ? uwi : 0);
         const uint32_t ufs = __shfl_sync(0xffffffffu, cur_fs, uwi < GS::NW ? uwi : 0);
         const uint32_t i = (it * kGatherWarps + warp) * GS::RW + ur;
-        if (unit && i < h) {
+        if (unit && i < h && FHD_IN(uwi * GS::NC * 16 + uoff + 24 * g + 35, GS::NCH * 16, kSiteGatherSmem)) {
             const uint32_t *wd = reinterpret_cast<const uint32_t *>(
                 reinterpret_cast<const uint8_t *>(stage + uwi * GS::NC) + uoff + 24 * g);
             const uint32_t x0 = plane_word(wd[0], wd[1], wd[2], s1, s2);
@@ -219,7 +223,7 @@ __device__ __forceinline__ void gather_phase1(const FrameDesc &fd, uint32_t j0, 
             for (int m = 0; m < 8; ++m) {
                 uint32_t a = iRP + ab[m];
                 a = a >= hRP ? a - hRP : a;
-                S[a] = (uint8_t)((m < 4 ? q0 : q1) >> (8 * (m & 3)));
+                if (FHD_IN(a, hRP, kSiteGatherSmem)) S[a] = (uint8_t)((m < 4 ? q0 : q1) >> (8 * (m & 3)));
             }
         }
     }
@@ -232,6 +236,7 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_encrypt_kernel(const
     const FrameDesc &fd = b.f[find_frame<false>(b, cta)];
     const uint32_t h = fd.h, w = fd.w, P = fd.P;
     const uint32_t j0 = (cta - fd.cta0) * P;
+    if (!FHD_IN(j0, w, kSiteGatherSmem)) return;   // a strip past the frame (the whole CTA)
     const uint32_t Pe = min(P, w - j0);
     const uint32_t RP = 3 * P, QC = 3 * Pe, rowB = 3 * w;
     const uint32_t t = threadIdx.x;
@@ -262,7 +267,8 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_encrypt_kernel(const
 #pragma unroll
         for (int k = 0; k < kRowsV; ++k) {
             const uint32_t i = ib + k * RT;
-            if (i < h) {
+            if (i < h && FHD_IN((size_t)i * RP + 16 * tv + 15, (size_t)h * RP, kSiteGatherSmem) &&
+                FHD_IN((uint64_t)i * rowB + base + 15, fd.N, kSiteGatherStore)) {
                 v[k] = *reinterpret_cast<const uint4 *>(S + (size_t)i * RP + 16 * tv);
                 k4[k] = __ldcs(reinterpret_cast<const uint4 *>(fd.B + (uint64_t)i * rowB + base));
             }
@@ -270,7 +276,7 @@ __global__ void __launch_bounds__(kGatherThreads, 2) gather_encrypt_kernel(const
 #pragma unroll
         for (int k = 0; k < kRowsV; ++k) {
             const uint32_t i = ib + k * RT;
-            if (i < h) {
+            if (i < h && FHD_IN((uint64_t)i * rowB + base + 15, fd.N, kSiteGatherStore)) {
                 uint4 o = v[k];
                 o.x ^= k4[k].x; o.y ^= k4[k].y; o.z ^= k4[k].z; o.w ^= k4[k].w;
                 __stcs(reinterpret_cast<uint4 *>(fd.dst + (uint64_t)i * rowB + base), o);
@@ -433,3 +439,5 @@ cudaError_t launch_permute(const Batch &b, bool encrypt, cudaStream_t s) {
 }
 
 }  // namespace fhd
+
+FHD_BOUNDS_TAKER(take_bounds_permute)

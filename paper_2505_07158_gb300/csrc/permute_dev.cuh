@@ -3,6 +3,7 @@
 // pass over a band of rows, each run by a group of threads that meets at a caller-given barrier.  See
 // permute.cu for the design.
 #pragma once
+#include "bounds.cuh"
 #include "common.cuh"
 
 namespace fhd {
@@ -68,6 +69,7 @@ __device__ void strip_pass(const FrameDesc &fd, uint32_t strip, uint8_t *smem, u
     const uint16_t *Dv = fd.D + (uint64_t)C * h;
     const FastMod modH(h);
     uint8_t *S = smem;
+    if (!FHD_IN(j0, w, kSiteStripSmem)) return;   // a strip past the frame (the same for the whole group)
 
     // ---- phase 1: loads of the strip rows, bytes scattered to their rotated rows.  With 4-byte-aligned
     // rows a lane owns one 32-bit word of the strip row (the lanes of a warp hold consecutive words), so
@@ -83,7 +85,8 @@ __device__ void strip_pass(const FrameDesc &fd, uint32_t strip, uint8_t *smem, u
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const uint32_t q = 4 * j + k, jj = q / C, c = q - jj * C;
-                const uint32_t t = modH.mod(pass_ld<kL2>(Dv + (uint64_t)c * w + j0 + jj));
+                const uint64_t dv = (uint64_t)c * w + j0 + jj;
+                const uint32_t t = FHD_IN(dv, (uint64_t)C * w, kSiteStripShift) ? modH.mod(pass_ld<kL2>(Dv + dv)) : 0;
                 ht[k] = kEnc ? t : h - t;
             }
             const uint8_t *sp = src + base + 4 * j;
@@ -93,7 +96,7 @@ __device__ void strip_pass(const FrameDesc &fd, uint32_t strip, uint8_t *smem, u
 #pragma unroll
                 for (int k = 0; k < kRowsW; ++k) {
                     const uint32_t i = ib + k * RT;
-                    if (i < h) {
+                    if (i < h && FHD_IN(base + 4 * j + (uint64_t)i * rowB + 3, fd.N, kSiteStripLoad)) {
                         e[k] = pass_ld<kL2>(reinterpret_cast<const unsigned int *>(sp + (uint64_t)i * rowB));
                         if (!kEnc) e[k] ^= pass_ld<kL2>(reinterpret_cast<const unsigned int *>(bp + (uint64_t)i * rowB));
                     }
@@ -106,7 +109,8 @@ __device__ void strip_pass(const FrameDesc &fd, uint32_t strip, uint8_t *smem, u
                         for (int bb = 0; bb < 4; ++bb) {
                             uint32_t d = i + ht[bb];
                             d = d >= h ? d - h : d;
-                            S[(size_t)d * RP + 4 * j + bb] = (uint8_t)(e[k] >> (8 * bb));
+                            if (FHD_IN((size_t)d * RP + 4 * j + bb, (size_t)h * RP, kSiteStripSmem))
+                                S[(size_t)d * RP + 4 * j + bb] = (uint8_t)(e[k] >> (8 * bb));
                         }
                     }
                 }
@@ -117,15 +121,19 @@ __device__ void strip_pass(const FrameDesc &fd, uint32_t strip, uint8_t *smem, u
         if (tid < QC * RT) {
             const uint32_t q = tid % QC, tr = tid / QC;
             const uint32_t jj = q / C, c = q - jj * C;
-            const uint32_t t = modH.mod(pass_ld<kL2>(Dv + (uint64_t)c * w + j0 + jj));
+            const uint64_t dv = (uint64_t)c * w + j0 + jj;
+            const uint32_t t = FHD_IN(dv, (uint64_t)C * w, kSiteStripShift) ? modH.mod(pass_ld<kL2>(Dv + dv)) : 0;
             const uint32_t ht = kEnc ? t : h - t;
             for (uint32_t i = tr; i < h; i += RT) {
                 const uint64_t o = (uint64_t)i * rowB + base + q;
-                uint8_t e = pass_ld<kL2>(src + o);
-                if (!kEnc) e ^= pass_ld<kL2>(fd.B + o);
+                uint8_t e = 0;
+                if (FHD_IN(o, fd.N, kSiteStripLoad)) {
+                    e = pass_ld<kL2>(src + o);
+                    if (!kEnc) e ^= pass_ld<kL2>(fd.B + o);
+                }
                 uint32_t d = i + ht;
                 d = d >= h ? d - h : d;
-                S[(size_t)d * RP + q] = e;
+                if (FHD_IN((size_t)d * RP + q, (size_t)h * RP, kSiteStripSmem)) S[(size_t)d * RP + q] = e;
             }
         }
     }
@@ -142,7 +150,8 @@ __device__ void strip_pass(const FrameDesc &fd, uint32_t strip, uint8_t *smem, u
 #pragma unroll
             for (int k = 0; k < kRowsV; ++k) {
                 const uint32_t i = ib + k * RT;
-                if (i < h) {
+                if (i < h && FHD_IN((size_t)i * RP + 16 * tv + 15, (size_t)h * RP, kSiteStripSmem) &&
+                    FHD_IN((uint64_t)i * rowB + base + 16 * tv + 15, fd.N, kSiteStripLoad)) {
                     g[k] = *reinterpret_cast<const uint4 *>(S + (size_t)i * RP + 16 * tv);
                     if (kEnc) k4[k] = pass_ld<kL2>(reinterpret_cast<const uint4 *>(fd.B + (uint64_t)i * rowB + base + 16 * tv));
                 }
@@ -150,7 +159,7 @@ __device__ void strip_pass(const FrameDesc &fd, uint32_t strip, uint8_t *smem, u
 #pragma unroll
             for (int k = 0; k < kRowsV; ++k) {
                 const uint32_t i = ib + k * RT;
-                if (i < h) {
+                if (i < h && FHD_IN((uint64_t)i * rowB + base + 16 * tv + 15, fd.N, kSiteStripStore)) {
                     uint4 v = g[k];
                     if (kEnc) { v.x ^= k4[k].x; v.y ^= k4[k].y; v.z ^= k4[k].z; v.w ^= k4[k].w; }
                     uint4 *dstp = reinterpret_cast<uint4 *>(out + (uint64_t)i * rowB + base + 16 * tv);
@@ -161,6 +170,8 @@ __device__ void strip_pass(const FrameDesc &fd, uint32_t strip, uint8_t *smem, u
     } else if (vec == 4) {
         for (uint32_t i = tr; i < h; i += RT) {
             const uint64_t o = (uint64_t)i * rowB + base + 4 * tv;
+            if (!FHD_IN((size_t)i * RP + 4 * tv + 3, (size_t)h * RP, kSiteStripSmem) || !FHD_IN(o + 3, fd.N, kSiteStripStore))
+                continue;
             uint32_t g = *reinterpret_cast<const uint32_t *>(S + (size_t)i * RP + 4 * tv);
             if (kEnc) g ^= pass_ld<kL2>(reinterpret_cast<const uint32_t *>(fd.B + o));
             *reinterpret_cast<uint32_t *>(out + o) = g;
@@ -168,6 +179,7 @@ __device__ void strip_pass(const FrameDesc &fd, uint32_t strip, uint8_t *smem, u
     } else {
         for (uint32_t i = tr; i < h; i += RT) {
             const uint64_t o = (uint64_t)i * rowB + base + tv;
+            if (!FHD_IN((size_t)i * RP + tv, (size_t)h * RP, kSiteStripSmem) || !FHD_IN(o, fd.N, kSiteStripStore)) continue;
             uint8_t g = S[(size_t)i * RP + tv];
             if (kEnc) g ^= pass_ld<kL2>(fd.B + o);
             out[o] = g;
@@ -199,6 +211,8 @@ __device__ void row_pass(const FrameDesc &fd, uint32_t band, uint8_t *smem, uint
     uint8_t *Out = smem + (size_t)RB * pitch;                    // RB rows
     uint32_t *sh = reinterpret_cast<uint32_t *>(smem + 2 * (size_t)RB * pitch);   // row shifts [r * C + c]
     const FastMod modW8(8 * w);
+    [[maybe_unused]] const size_t band_bytes = (size_t)RB * pitch;   // extent of In and of Out
+    if (!FHD_IN(i0, h, kSiteRowSmem)) return;   // a band past the frame (the same for the whole group)
 
     // ---- load the band (rows are contiguous in global memory)
     const bool v16 = rowB % 16 == 0 && aligned(src, 16) && aligned(dst, 16);
@@ -206,18 +220,24 @@ __device__ void row_pass(const FrameDesc &fd, uint32_t band, uint8_t *smem, uint
         const uint32_t nvr = rowB / 16;
         for (uint32_t k = tid; k < nr * nvr; k += nthr) {
             const uint32_t r = k / nvr, v = k - r * nvr;
-            *reinterpret_cast<uint4 *>(In + (size_t)r * pitch + 16 * v) =
-                pass_ld<kL2>(reinterpret_cast<const uint4 *>(src + (uint64_t)r * rowB + 16 * v));
+            if (FHD_IN((size_t)r * pitch + 16 * v + 15, band_bytes, kSiteRowSmem) &&
+                FHD_IN((uint64_t)(i0 + r) * rowB + 16 * v + 15, fd.N, kSiteRowLoad))
+                *reinterpret_cast<uint4 *>(In + (size_t)r * pitch + 16 * v) =
+                    pass_ld<kL2>(reinterpret_cast<const uint4 *>(src + (uint64_t)r * rowB + 16 * v));
         }
     } else {
         for (uint32_t k = tid; k < nr * rowB; k += nthr) {
             const uint32_t r = k / rowB, q = k - r * rowB;
-            In[(size_t)r * pitch + q] = pass_ld<kL2>(src + (uint64_t)r * rowB + q);
+            if (FHD_IN((size_t)r * pitch + q, band_bytes, kSiteRowSmem) &&
+                FHD_IN((uint64_t)(i0 + r) * rowB + q, fd.N, kSiteRowLoad))
+                In[(size_t)r * pitch + q] = pass_ld<kL2>(src + (uint64_t)r * rowB + q);
         }
     }
     for (uint32_t k = tid; k < nr * C; k += nthr) {
         const uint32_t r = k / C, c = k - r * C;
-        sh[k] = modW8.mod(pass_ld<kL2>(fd.D + (uint64_t)c * h + i0 + r));
+        const uint64_t di = (uint64_t)c * h + i0 + r;
+        if (FHD_IN(k, (uint64_t)RB * C, kSiteRowSmem))
+            sh[k] = FHD_IN(di, (uint64_t)C * h, kSiteRowShift) ? modW8.mod(pass_ld<kL2>(fd.D + di)) : 0;
     }
     sync();
 
@@ -251,7 +271,8 @@ __device__ void row_pass(const FrameDesc &fd, uint32_t band, uint8_t *smem, uint
                 for (int c = 0; c < 3; ++c) {
                     uint32_t u = g + du[c];
                     u = u >= W4 ? u - W4 : u;
-                    const uint32_t u1 = u + 1 == W4 ? 0 : u + 1;
+                    uint32_t u1 = u + 1 == W4 ? 0 : u + 1;
+                    if (!FHD_IN(u, W4, kSiteRowSmem) || !FHD_IN(u1, W4, kSiteRowSmem)) u = u1 = 0;
                     const uint32_t a0 = row[3 * u], a1 = row[3 * u + 1], a2 = row[3 * u + 2];
                     const uint32_t b0 = row[3 * u1], b1 = row[3 * u1 + 1], b2 = row[3 * u1 + 2];
                     uint32_t lo, hi;
@@ -277,8 +298,10 @@ __device__ void row_pass(const FrameDesc &fd, uint32_t band, uint8_t *smem, uint
         const uint32_t nvr = rowB / 16;
         for (uint32_t r = 0; r < nr; ++r)
             for (uint32_t v = tid; v < nvr; v += nthr)
-                *reinterpret_cast<uint4 *>(dst + (uint64_t)r * rowB + 16 * v) =
-                    *reinterpret_cast<const uint4 *>(Outp + (size_t)r * pitch + 16 * v);
+                if (FHD_IN((size_t)r * pitch + 16 * v + 15, band_bytes, kSiteRowSmem) &&
+                    FHD_IN((uint64_t)(i0 + r) * rowB + 16 * v + 15, fd.N, kSiteRowStore))
+                    *reinterpret_cast<uint4 *>(dst + (uint64_t)r * rowB + 16 * v) =
+                        *reinterpret_cast<const uint4 *>(Outp + (size_t)r * pitch + 16 * v);
         return;
     }
 
@@ -297,6 +320,7 @@ __device__ void row_pass(const FrameDesc &fd, uint32_t band, uint8_t *smem, uint
             int p0 = kEnc ? (int)j - (int)a - 1 : (int)(j + a);
             if (p0 < 0) p0 += (int)w;
             if (p0 >= (int)w) p0 -= (int)w;
+            if (!FHD_IN(p0, w, kSiteRowSmem)) p0 = 0;
             uint32_t A0, A1, A2, A3, A4;
             if ((uint32_t)p0 + 4 < w) {
                 const uint8_t *p = row + (uint32_t)p0 * C;
@@ -324,13 +348,17 @@ __device__ void row_pass(const FrameDesc &fd, uint32_t band, uint8_t *smem, uint
         const uint32_t nvr = rowB / 16;
         for (uint32_t k = tid; k < nr * nvr; k += nthr) {
             const uint32_t r = k / nvr, v = k - r * nvr;
-            *reinterpret_cast<uint4 *>(dst + (uint64_t)r * rowB + 16 * v) =
-                *reinterpret_cast<const uint4 *>(Out + (size_t)r * pitch + 16 * v);
+            if (FHD_IN((size_t)r * pitch + 16 * v + 15, band_bytes, kSiteRowSmem) &&
+                FHD_IN((uint64_t)(i0 + r) * rowB + 16 * v + 15, fd.N, kSiteRowStore))
+                *reinterpret_cast<uint4 *>(dst + (uint64_t)r * rowB + 16 * v) =
+                    *reinterpret_cast<const uint4 *>(Out + (size_t)r * pitch + 16 * v);
         }
     } else {
         for (uint32_t k = tid; k < nr * rowB; k += nthr) {
             const uint32_t r = k / rowB, q = k - r * rowB;
-            dst[(uint64_t)r * rowB + q] = Out[(size_t)r * pitch + q];
+            if (FHD_IN((size_t)r * pitch + q, band_bytes, kSiteRowSmem) &&
+                FHD_IN((uint64_t)(i0 + r) * rowB + q, fd.N, kSiteRowStore))
+                dst[(uint64_t)r * rowB + q] = Out[(size_t)r * pitch + q];
         }
     }
 }

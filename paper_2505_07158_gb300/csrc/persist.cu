@@ -106,13 +106,17 @@ __device__ __noinline__ void digest_task(const PLaunch &L, uint32_t task, uint32
     const uint32_t n = S.n;
     sha_pipeline(
         [&](uint32_t m, const uint8_t *&p, uint64_t &len, uint8_t *&out) {
+            if (!FHD_IN(m / n, S.count, kSiteShaDigest) || !FHD_IN(L.prio[m / n], S.count, kSitePersistTask))
+                return false;
             const FrameDesc &fd = S.f[L.prio[m / n]];
             const uint32_t i = m % n;
             const uint64_t lo = (uint64_t)(((unsigned __int128)fd.N * i) / n);
             const uint64_t hi = (uint64_t)(((unsigned __int128)fd.N * (i + 1)) / n);
+            if (!FHD_IN(hi, fd.N + 1, kSiteShaMessage)) return false;
             p = fd.src + lo;
             len = hi - lo;
             out = fd.part + 32ull * i;
+            return true;
         },
         S.count * n, task, rtid, kBarSha, sm);
 }
@@ -138,6 +142,7 @@ __device__ void digest_worker(const PLaunch &L, ShaSmem &sm, unsigned *slot) {
             for (uint32_t r = m0 / n; r * n < m1; ++r) {
                 const uint32_t lo = max(m0, r * n), hi = min(m1, (r + 1) * n);
                 const uint32_t f = L.prio[r];
+                if (!FHD_IN(f, S.count, kSitePersistTask)) continue;
                 const unsigned old = atomicAdd(&L.cnt->sha_msgs[f], hi - lo);
                 if (old + (hi - lo) != n) continue;
                 __threadfence();
@@ -196,7 +201,10 @@ __device__ void chain_worker(const PLaunch &L, uint8_t *H) {
         // then per frame (smallest first) its worker warps, the sides interleaved
         if (task < L.chain_masters_total) {
             const uint32_t r = segment(L.chain_begin, L.s[0].count, task);
-            const uint32_t f = L.mprio[r], side = task - L.chain_begin[r], g = L.chain_group[f];
+            const uint32_t f = L.mprio[r], side = task - L.chain_begin[r];
+            if (!FHD_IN(f, L.s[0].count, kSitePersistTask) || !FHD_IN(side, L.sides, kSitePersistTask)) continue;
+            const uint32_t g = L.chain_group[f];
+            if (!FHD_IN(g, L.s[side].groups, kSitePersistTask)) continue;
             const PSide &S = L.s[side];
             master_stream(
                 S, g, S.states, S.status, H, lane,
@@ -212,6 +220,9 @@ __device__ void chain_worker(const PLaunch &L, uint8_t *H) {
         } else {
             const uint32_t per = L.sides * L.wpf, t2 = task - L.chain_masters_total, r = t2 / per;
             const uint32_t f = L.mprio[r], k = t2 - r * per, side = k / L.wpf, pg = k - side * L.wpf;
+            if (!FHD_IN(r, L.s[0].count, kSitePersistTask) || !FHD_IN(f, L.s[0].count, kSitePersistTask) ||
+                !FHD_IN(side, L.sides, kSitePersistTask))
+                continue;
             const PSide &S = L.s[side];
             if (wait(&L.cnt->master_done[side][f], 1u))
                 keystream_task(S.f[f], S.n, Rk4{S.hstep, S.hhalf, S.hsixth}, pg, lane);
@@ -281,6 +292,9 @@ __device__ void mem_worker(const PLaunch &L, uint8_t *smem, unsigned *slot) {
         sync();
         if (t >= L.mem_tasks) return;
         const uint32_t kind = code & 3, side = (code >> 2) & 1;
+        if (!FHD_IN(f, L.s[0].count, kSitePersistTask) || !FHD_IN(side, L.sides, kSitePersistTask) ||
+            !FHD_IN(idx, kind == 0 || kind == 3 ? L.s[side].bands[f] : L.s[side].strips[f], kSitePersistTask))
+            continue;
         const FrameDesc &fd = L.s[side].f[f];
         if (code & 8) mem_task(kind, fd, idx, smem, mtid);
         __threadfence();
@@ -362,3 +376,5 @@ cudaError_t launch_persistent(const PLaunch &L, size_t mem_smem, cudaStream_t s)
 }
 
 }  // namespace fhd
+
+FHD_BOUNDS_TAKER(take_bounds_persist)

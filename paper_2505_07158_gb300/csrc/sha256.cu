@@ -29,13 +29,16 @@ __global__ void __launch_bounds__(64) sha_subframes_kernel(const __grid_constant
     const uint32_t n = b.n;
     sha_pipeline(
         [&](uint32_t m, const uint8_t *&p, uint64_t &len, uint8_t *&out) {
+            if (!FHD_IN(m / n, b.count, kSiteShaDigest)) return false;
             const FrameDesc &fd = b.f[m / n];
             const uint32_t i = m % n;
             const uint64_t lo = (uint64_t)(((unsigned __int128)fd.N * i) / n);
             const uint64_t hi = (uint64_t)(((unsigned __int128)fd.N * (i + 1)) / n);
+            if (!FHD_IN(hi, fd.N + 1, kSiteShaMessage)) return false;
             p = fd.src + lo;
             len = hi - lo;
             out = fd.part + 32ull * i;
+            return true;
         },
         b.count * n, blockIdx.x, threadIdx.x, 1, sm);
 }
@@ -49,9 +52,11 @@ __global__ void __launch_bounds__(64) sha_plain_kernel(const uint8_t *data, uint
             const uint32_t k = m / n, i = m % n;
             const uint64_t lo = (uint64_t)(((unsigned __int128)nbytes * i) / n);
             const uint64_t hi = (uint64_t)(((unsigned __int128)nbytes * (i + 1)) / n);
+            if (!FHD_IN(k, count, kSiteShaDigest) || !FHD_IN(hi, nbytes + 1, kSiteShaMessage)) return false;
             p = data + k * nbytes + lo;
             len = hi - lo;
             out = part + 32ull * m;
+            return true;
         },
         count * n, blockIdx.x, threadIdx.x, 1, sm);
 }
@@ -63,13 +68,16 @@ __global__ void __launch_bounds__(64) sha_dst_kernel(const __grid_constant__ Bat
     const uint32_t n = b.n;
     sha_pipeline(
         [&](uint32_t m, const uint8_t *&p, uint64_t &len, uint8_t *&out) {
+            if (!FHD_IN(m / n, b.count, kSiteShaDigest)) return false;
             const FrameDesc &fd = b.f[m / n];
             const uint32_t i = m % n;
             const uint64_t lo = (uint64_t)(((unsigned __int128)fd.N * i) / n);
             const uint64_t hi = (uint64_t)(((unsigned __int128)fd.N * (i + 1)) / n);
+            if (!FHD_IN(hi, fd.N + 1, kSiteShaMessage)) return false;
             p = fd.dst + lo;
             len = hi - lo;
             out = fd.part + 32ull * i;
+            return true;
         },
         b.count * n, blockIdx.x, threadIdx.x, 1, sm);
 }
@@ -230,3 +238,5 @@ cudaError_t launch_fold(const uint8_t *part, uint32_t n, uint32_t count, uint8_t
 }
 
 }  // namespace fhd
+
+FHD_BOUNDS_TAKER(take_bounds_sha)

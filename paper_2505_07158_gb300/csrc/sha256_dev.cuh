@@ -1,6 +1,7 @@
 // Device code of the sub-frame SHA-256 (FIPS 180-4) shared by the digest kernels and the persistent batch
 // kernel: the producer/consumer message pipeline and the tree digest.  See sha256.cu for the design.
 #pragma once
+#include "bounds.cuh"
 #include "common.cuh"
 #include "sha256_core.cuh"
 
@@ -44,6 +45,11 @@ __device__ __forceinline__ void message_block(const uint8_t *p, uint64_t len, ui
                                               const uint4 cur[4], uint32_t w[16]) {
     const uint64_t full = len >> 6;
     if (b < full) {
+        if (!FHD_IN(64 * b + 63, len, kSiteShaBlock)) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) w[k] = 0;
+            return;
+        }
         if (aligned16) {
             block_words(cur, w);
         } else {
@@ -101,7 +107,8 @@ struct ShaSmem {
 
 // 32 messages per pipeline: of its 64 threads (rtid 0..63), warp 0 compresses and warp 1 produces W + K.
 // Pipeline `unit` takes messages 32 unit .. 32 unit + 31 of the nmsg messages; message m is located by
-// locate(m, p, len, out) and its digest goes to out (32 bytes).  `bar` is the hardware barrier id the
+// locate(m, p, len, out) and its digest goes to out (32 bytes); locate returns false for a message that
+// failed a range check (checked builds), which is then skipped.  `bar` is the hardware barrier id the
 // pipeline's two warps use.
 template <class Locate>
 __device__ void sha_pipeline(Locate locate, uint32_t nmsg, uint32_t unit, uint32_t rtid, uint32_t bar, ShaSmem &sm) {
@@ -109,11 +116,11 @@ __device__ void sha_pipeline(Locate locate, uint32_t nmsg, uint32_t unit, uint32
     const int lane = rtid & 31;
     const bool producer = rtid >= 32;
     const uint32_t m = unit * kMsgPerCta + lane;
-    const bool active = m < nmsg;
+    bool active = m < nmsg;
     const uint8_t *p = nullptr;
     uint64_t len = 0;
     uint8_t *out = nullptr;
-    if (active) locate(m, p, len, out);
+    if (active) active = locate(m, p, len, out);
     const uint64_t nb = active ? padded_blocks(len) : 0;
     const uint64_t NB = __reduce_max_sync(0xffffffffu, (unsigned)nb);   // < 2^32 blocks per message
     if (producer) {
@@ -124,7 +131,7 @@ __device__ void sha_pipeline(Locate locate, uint32_t nmsg, uint32_t unit, uint32
         const bool al = (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
         const uint64_t full = len >> 6;
         auto issue = [&](uint64_t blk) {
-            if (active && al && blk < full) {
+            if (active && al && blk < full && FHD_IN(64 * blk + 63, len, kSiteShaBlock)) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) cp_async16(&ring[blk % kRing][q][lane], p + 64 * blk + 16 * q);
             }

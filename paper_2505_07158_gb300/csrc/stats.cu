@@ -14,6 +14,7 @@
 // time with the SIMD byte instructions, are merged with one global atomic per
 // counter and CTA, and a per-(frame, channel) warp finishes the statistic.  The correlation and local-entropy
 // statistics read only the sampled pairs and blocks (a few kB per frame).
+#include "bounds.cuh"
 #include "common.cuh"
 
 namespace fhd {
@@ -49,6 +50,7 @@ __global__ void __launch_bounds__(kStatThreads) hist_kernel(const uint8_t *frame
     const bool vec = (reinterpret_cast<uintptr_t>(frames + b0) & 15) == 0 && (b1 - b0) % G == 0;
     if (vec) {
         for (uint64_t k = b0 + G * (uint64_t)threadIdx.x; k < b1; k += G * (uint64_t)blockDim.x) {
+            if (!FHD_IN(k + G - 1, total, kSiteStats)) break;
             uint4 v[C];
 #pragma unroll
             for (int m = 0; m < C; ++m) v[m] = __ldcs(reinterpret_cast<const uint4 *>(frames + k) + m);
@@ -135,6 +137,7 @@ __global__ void __launch_bounds__(kStatThreads) npcr_kernel(const uint8_t *a, co
                      (b1 - b0) % G == 0;
     if (vec) {
         for (uint64_t k = b0 + G * (uint64_t)threadIdx.x; k < b1; k += G * (uint64_t)blockDim.x) {
+            if (!FHD_IN(k + G - 1, total, kSiteStats)) break;
             uint4 va[C], vb[C];
 #pragma unroll
             for (int m = 0; m < C; ++m) {
@@ -209,6 +212,7 @@ __global__ void __launch_bounds__(kStatThreads) corr_kernel(const uint8_t *frame
             atomicOr(status, 1u);
             continue;
         }
+        if (!FHD_IN(((uint64_t)(i + di) * w + j + dj) * C + C - 1, (uint64_t)h * w * C, kSiteStats)) continue;
         const uint8_t *px = F + ((uint64_t)i * w + j) * C;
         const uint8_t *py = F + ((uint64_t)(i + di) * w + j + dj) * C;
 #pragma unroll
@@ -265,7 +269,9 @@ __global__ void __launch_bounds__(kStatThreads) block_entropy_kernel(const uint8
     if (inside) {
         for (uint32_t i = 0; i < bs; ++i) {
             const uint8_t *row = F + ((uint64_t)(r0 + i) * w + c0) * C;
-            for (uint32_t t = threadIdx.x; t < bs * C; t += blockDim.x) atomicAdd(&hist[t % C][row[t]], 1u);
+            for (uint32_t t = threadIdx.x; t < bs * C; t += blockDim.x)
+                if (FHD_IN(((uint64_t)(r0 + i) * w + c0) * C + t, (uint64_t)h * w * C, kSiteStats))
+                    atomicAdd(&hist[t % C][row[t]], 1u);
         }
     } else if (threadIdx.x == 0) {
         atomicOr(status, 1u);
@@ -375,3 +381,5 @@ cudaError_t launch_stats_local_entropy(const uint8_t *frames, uint32_t count, ui
 }
 
 }  // namespace fhd
+
+FHD_BOUNDS_TAKER(take_bounds_stats)

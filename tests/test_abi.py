@@ -38,6 +38,35 @@ def test_every_declared_symbol_is_exported(lib):
         assert getattr(lib, name) is not None
 
 
+def test_checked_build_exports_the_same_symbols():
+    """The checked build (-DFHD_BOUNDS_CHECK) is the same library with range checks: every declared symbol,
+    and a build flag that says which build it is (the default library's says 0)."""
+    import paper_2505_07158_gb300 as fhd
+    from paper_2505_07158_gb300 import build as b
+    path = b.build(checked=True)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(line.split()[-1] for line in out.splitlines() if line.strip())
+    for name in declared_functions():
+        assert name in exported, name
+    checked = ctypes.CDLL(path)
+    checked.fhd_build_flags.restype = ctypes.c_uint32
+    assert checked.fhd_build_flags() == fhd.FHD_BUILD_BOUNDS_CHECK
+    if not fhd.checked_requested():
+        assert fhd.fhd_build_flags() == 0
+
+
+def test_bounds_calls_without_a_device(lib):
+    """Host-side behaviour of the bounds calls: site names, and the default build's report (all zero, no
+    device call) and self-test (refused: not a checked build)."""
+    import paper_2505_07158_gb300 as fhd
+    assert fhd.fhd_bounds_site_name(33) == "column pass: frame store"
+    assert fhd.fhd_bounds_site_name(9999) == "unknown site"
+    if fhd.fhd_build_flags() == 0:
+        assert fhd.fhd_bounds_report() == {"count": 0, "site": 0, "site_name": "unknown site", "index": 0,
+                                           "limit": 0}
+        assert lib.fhd_bounds_selftest(None, None, None) == fhd.FHD_ERR_STATE
+
+
 def test_host_side_argument_checks(lib):
     import paper_2505_07158_gb300 as fhd
     out = ctypes.c_void_p()
