@@ -400,23 +400,32 @@ def run_ours(args):
             self.digests_ready, self.cipher_ready = torch.cuda.Event(), torch.cuda.Event()
             self.enc_master, self.dec_master, self.rx_done = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
             self.dec_done, self.enc_ks, self.dec_ks = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
+            self.h2d_done = torch.cuda.Event()
             self.used = False
             self.e2e_used = False
             self.host_out = torch.empty_like(host).pin_memory()
             self.host_dig = torch.empty((FRAMES, 32), dtype=torch.uint8).pin_memory()
 
     slots = [Slot() for _ in range(max(1, args.inflight))]
+    # The end-to-end copies run on two streams of their own, one per direction, so that a copy waiting for
+    # its slot to come free never sits in a compute stream: a clip's host-to-device copy waits for the
+    # slot's previous copy-out, its sender for that copy, and its copy-out for its receiver.
+    h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
     WW = args.worker_window if 0 < args.worker_window < len(slots) else 0
     KEEP = max(2, WW)
     last = [None] * KEEP     # slots of the previous clips, oldest first: the chaining state advances clip after clip
 
     def round_trip(sl, e2e=False):
         prev, prev2 = last[-1], last[-2]
-        if sl.used:
-            sl.tx.wait_event(sl.rx_done)
         if e2e:
-            with torch.cuda.stream(sl.tx):
+            if sl.used:
+                h2d.wait_event(sl.rx_done)
+            with torch.cuda.stream(h2d):
                 sl.src_all.copy_(host, non_blocking=True)
+            sl.h2d_done.record(h2d)
+            sl.tx.wait_event(sl.h2d_done)
+        elif sl.used:
+            sl.tx.wait_event(sl.rx_done)
         # The digest stage (integer work) of this clip runs at once, during the previous clip's keystreams
         # (binary64 work).  This clip's LHCS_m waits for the chaining state and, by --gate, for:
         #   permute:   the previous clip's ciphertext and decrypted frames (all of its work);
@@ -455,11 +464,14 @@ def run_ours(args):
                            data_events=[sl.cipher_ready], keystream_event=sl.dec_ks, worker_wait_events=dwk)
         sl.dec_done.record(sl.rx)             # before the copy-out: gates the next clip's receiver
         if e2e:
-            with torch.cuda.stream(sl.rx):
+            d2h.wait_event(sl.dec_done)
+            with torch.cuda.stream(d2h):
                 sl.host_out.copy_(sl.dec_all, non_blocking=True)
                 sl.host_dig.copy_(sl.digs, non_blocking=True)
             sl.e2e_used = True
-        sl.rx_done.record(sl.rx)
+            sl.rx_done.record(d2h)
+        else:
+            sl.rx_done.record(sl.rx)
         sl.used = True
         last.append(sl)
         del last[:-KEEP]
