@@ -51,6 +51,144 @@ __device__ __forceinline__ uint32_t strip_vec(uint64_t rowB, uint32_t P, uint32_
     return 1;
 }
 
+// 4 x 4 byte transpose: byte m of word r becomes byte r of word m.
+__device__ __forceinline__ void transpose4x4(uint32_t &a, uint32_t &b, uint32_t &c, uint32_t &d) {
+    const uint32_t t0 = __byte_perm(a, b, 0x5140), t1 = __byte_perm(a, b, 0x7362);
+    const uint32_t t2 = __byte_perm(c, d, 0x5140), t3 = __byte_perm(c, d, 0x7362);
+    a = __byte_perm(t0, t2, 0x5410);
+    b = __byte_perm(t0, t2, 0x7632);
+    c = __byte_perm(t1, t3, 0x5410);
+    d = __byte_perm(t1, t3, 0x7632);
+}
+
+// Column-word layout of a strip (the column pass's shared memory when h % 4 == 0).  A word holds four
+// consecutive rows of one byte column (row 4k + r in byte r).  The strip's QC byte columns form NL = QC / 4
+// column quads; the word of row quad p and column q = 4 lam + m sits at p * 4NL + m NL + lam.  A thread owns
+// one column quad lam and row quads p = p0, p0 + nq, ...: LT threads per row quad (NL, rounded up), so that the
+// threads of a warp take one or two row quads and the NL (or NL + 16) words they touch at a time lie in
+// distinct banks: with LT = 16 the pitch 4NL must be 16 mod 32.
+struct ColWords {
+    uint32_t NL, LT;
+};
+__device__ __forceinline__ ColWords col_words(uint32_t QC) {
+    const uint32_t NL = QC >> 2;
+    return {NL, NL <= 16 && (NL & 7) == 4 ? 16u : (NL + 31) & ~31u};
+}
+
+// Column pass over a strip in the column-word layout: for each column q of the strip, out[d][q] =
+// X[(d - s'_q) mod h][q] with s'_q = s_v (encrypt) or h - s_v (decrypt); X = G (encrypt) or E ^ B (decrypt),
+// and the output is XORed with B when encrypting.  With s'_q = 4 a + b:
+// * phase 1: the thread loads four rows of its four columns (one 32-bit word per row), transposes them into
+//   four column words and stores column q's word of row quad k at row quad (k + a) mod h/4: the rotation by
+//   whole row quads;
+// * phase 2: output row quad t of column q is bytes 4 - b .. 7 - b of the column's words at row quads t - 1
+//   and t (one byte permute: the rest of the rotation), transposed back into four row words.
+// Every shared access is one 32-bit word per thread in distinct banks; every global access is a 32-bit word
+// per thread, consecutive across the threads of a row quad.
+template <bool kEnc, bool kL2, class Sync>
+__device__ void strip_pass_cw(const FrameDesc &fd, uint32_t j0, uint32_t QC, ColWords cw, uint8_t *smem, uint32_t tid,
+                              uint32_t nthr, Sync sync) {
+    // row quads per thread and batch: 16 (8 in the persistent kernel, whose task bodies share 128 registers)
+    // independent 32-bit loads in flight
+    constexpr int kU = kL2 ? 2 : 4;
+    const uint32_t h = fd.h, w = fd.w, C = fd.C, H4 = h >> 2, NL = cw.NL, QP = QC;
+    const uint64_t rowB = (uint64_t)w * C, base = (uint64_t)j0 * C;
+    const uint64_t rw = rowB >> 2;   // 32-bit words per frame row
+    const uint8_t *src = kEnc ? fd.G : fd.src;
+    uint8_t *out = kEnc ? fd.dst : fd.G;
+    uint32_t *S = reinterpret_cast<uint32_t *>(smem);
+    [[maybe_unused]] const size_t words = (size_t)H4 * QP;
+    const uint32_t lam = tid % cw.LT, p0 = tid / cw.LT, nq = nthr / cw.LT;
+    const bool live = lam < NL;
+    // per column m of the thread's quad: whole row quads of the rotation (16 bits each) and the rest (2 bits)
+    uint32_t a01 = 0, a23 = 0, bs = 0;
+    const uint32_t *sp = reinterpret_cast<const uint32_t *>(src + base) + lam;
+    const uint32_t *bp = reinterpret_cast<const uint32_t *>(fd.B + base) + lam;
+    if (live) {
+        const FastMod modH(h);
+        const uint16_t *Dv = fd.D + (uint64_t)C * h;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const uint32_t q = 4 * lam + m, jj = q / C, c = q - jj * C;
+            const uint64_t dv = (uint64_t)c * w + j0 + jj;
+            const uint32_t t = FHD_IN(dv, (uint64_t)C * w, kSiteStripShift) ? modH.mod(pass_ld<kL2>(Dv + dv)) : 0;
+            const uint32_t sp2 = kEnc ? t : (t ? h - t : 0);
+            if (m < 2) a01 |= (sp2 >> 2) << (16 * m);
+            else a23 |= (sp2 >> 2) << (16 * (m - 2));
+            bs |= (sp2 & 3) << (2 * m);
+        }
+        for (uint32_t k0 = p0; k0 < H4; k0 += kU * nq) {
+            uint32_t v[kU][4];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const uint32_t k = k0 + u * nq;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const uint64_t o = (uint64_t)(4 * k + r) * rw;
+                    v[u][r] = 0;
+                    if (k < H4 && FHD_IN(base + 4 * (o + lam) + 3, fd.N, kSiteStripLoad)) {
+                        v[u][r] = pass_ld<kL2>(sp + o);
+                        if (!kEnc) v[u][r] ^= pass_ld<kL2>(bp + o);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const uint32_t k = k0 + u * nq;
+                if (k >= H4) break;
+                transpose4x4(v[u][0], v[u][1], v[u][2], v[u][3]);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    uint32_t p = k + (((m < 2 ? a01 : a23) >> (16 * (m & 1))) & 0xffffu);
+                    p = p >= H4 ? p - H4 : p;
+                    const size_t i = (size_t)p * QP + m * NL + lam;
+                    if (FHD_IN(i, words, kSiteStripSmem)) S[i] = v[u][m];
+                }
+            }
+        }
+    }
+    sync();
+    if (!live) return;
+    uint32_t *op = reinterpret_cast<uint32_t *>(out + base) + lam;
+    for (uint32_t t0 = p0; t0 < H4; t0 += kU * nq) {
+        uint32_t kb[kU][4];   // B words of the batch's output rows (encrypt), loaded before any store
+        if (kEnc) {
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const uint32_t t = t0 + u * nq;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const uint64_t o = (uint64_t)(4 * t + r) * rw;
+                    kb[u][r] = t < H4 && FHD_IN(base + 4 * (o + lam) + 3, fd.N, kSiteStripLoad) ? pass_ld<kL2>(bp + o) : 0;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const uint32_t t = t0 + u * nq;
+            if (t >= H4) break;
+            const uint32_t tm = t ? t - 1 : H4 - 1;
+            uint32_t v[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const size_t i0 = (size_t)tm * QP + m * NL + lam, i1 = (size_t)t * QP + m * NL + lam;
+                const uint32_t sel = 0x7654u - ((bs >> (2 * m)) & 3) * 0x1111u;
+                v[m] = FHD_IN(i0, words, kSiteStripSmem) && FHD_IN(i1, words, kSiteStripSmem)
+                           ? __byte_perm(S[i0], S[i1], sel)
+                           : 0;
+            }
+            transpose4x4(v[0], v[1], v[2], v[3]);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const uint64_t o = (uint64_t)(4 * t + r) * rw;
+                if (!FHD_IN(base + 4 * (o + lam) + 3, fd.N, kSiteStripStore)) continue;
+                if (kEnc) __stcs(op + o, v[r] ^ kb[u][r]);
+                else op[o] = v[r];
+            }
+        }
+    }
+}
+
 // Column pass.  Encrypt: S[(i + s_v) mod h][q] = G[i][q]; E = S ^ B.
 // Decrypt: S[(i - s_v) mod h][q] = (E ^ B)[i][q]; G = S.
 // Column pass over strip `strip` of frame fd by the nthr threads (tid = 0..nthr-1) of a group that meets at
@@ -70,6 +208,16 @@ __device__ void strip_pass(const FrameDesc &fd, uint32_t strip, uint8_t *smem, u
     const FastMod modH(h);
     uint8_t *S = smem;
     if (!FHD_IN(j0, w, kSiteStripSmem)) return;   // a strip past the frame (the same for the whole group)
+    {
+        // the column-word route: rows of whole row quads, 32-bit aligned rows and pointers, and a strip whose
+        // column-word pitch is its row length (no padding: it fits the strip's shared memory)
+        const ColWords cw = col_words(QC);
+        if ((h & 3) == 0 && (QC & 3) == 0 && rowB % 4 == 0 && base % 4 == 0 && nthr % cw.LT == 0 &&
+            (cw.LT != 16 || (QC & 31) == 16) && aligned(src, 4) && aligned(out, 4) && aligned(fd.B, 4)) {
+            strip_pass_cw<kEnc, kL2>(fd, j0, QC, cw, smem, tid, nthr, sync);
+            return;
+        }
+    }
 
     // ---- phase 1: loads of the strip rows, bytes scattered to their rotated rows.  With 4-byte-aligned
     // rows a lane owns one 32-bit word of the strip row (the lanes of a warp hold consecutive words), so
