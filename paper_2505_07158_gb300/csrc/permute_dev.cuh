@@ -335,6 +335,80 @@ __device__ void strip_pass(const FrameDesc &fd, uint32_t strip, uint8_t *smem, u
     }
 }
 
+// Plane word of channel c (pixels 4j .. 4j+3) from the three interleaved words 3j .. 3j+2 of an RGB row.
+__device__ __forceinline__ uint32_t rgb_plane_word(uint32_t w0, uint32_t w1, uint32_t w2, int c) {
+    if (c == 0) return __byte_perm(__byte_perm(w0, w1, 0x0630), w2, 0x5210);
+    if (c == 1) return __byte_perm(__byte_perm(w0, w1, 0x0741), w2, 0x6210);
+    return __byte_perm(__byte_perm(w0, w1, 0x0052), w2, 0x7410);
+}
+
+// Row pass of interleaved RGB rows with w % 16 == 0 and 16-byte aligned rows, staged as channel planes: each
+// 48-byte group of a source row (16 pixels, three 16-byte loads) is deinterleaved once, while it is staged,
+// into four plane words per channel (shared memory: row r, plane c at r * pitch + c * w).  A thread then
+// builds one output 4-pixel group: per channel the two plane words that hold its source bytes (two 32-bit
+// shared loads, consecutive across the threads), one funnel shift, and the three channels' words
+// interleaved back into the three output words, stored straight to the frame.
+template <bool kEnc, bool kL2, class Sync>
+__device__ void row_pass_planar(const FrameDesc &fd, uint32_t i0, uint32_t nr, const uint8_t *src, uint8_t *dst,
+                                uint8_t *In, uint32_t *sh, uint32_t tid, uint32_t nthr, Sync sync) {
+    const uint32_t h = fd.h, w = fd.w, RB = fd.RB, rowB = 3 * w, pitch = rowB, W4 = w >> 2, W16 = w >> 4;
+    [[maybe_unused]] const size_t band_bytes = (size_t)RB * pitch;
+    const FastMod modW8(8 * w);
+    for (uint32_t k = tid; k < nr * W16; k += nthr) {
+        const uint32_t r = k / W16, g = k - r * W16;
+        if (!FHD_IN((uint64_t)(i0 + r) * rowB + 48 * g + 47, fd.N, kSiteRowLoad) ||
+            !FHD_IN((size_t)r * pitch + 2 * w + 16 * g + 15, band_bytes, kSiteRowSmem))
+            continue;
+        const uint4 *sp = reinterpret_cast<const uint4 *>(src + (uint64_t)r * rowB + 48 * g);
+        const uint4 x0 = pass_ld<kL2>(sp), x1 = pass_ld<kL2>(sp + 1), x2 = pass_ld<kL2>(sp + 2);
+        const uint32_t wd[12] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w, x2.x, x2.y, x2.z, x2.w};
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            *reinterpret_cast<uint4 *>(In + (size_t)r * pitch + (size_t)c * w + 16 * g) =
+                make_uint4(rgb_plane_word(wd[0], wd[1], wd[2], c), rgb_plane_word(wd[3], wd[4], wd[5], c),
+                           rgb_plane_word(wd[6], wd[7], wd[8], c), rgb_plane_word(wd[9], wd[10], wd[11], c));
+    }
+    for (uint32_t k = tid; k < nr * 3; k += nthr) {
+        const uint32_t r = k / 3, c = k - r * 3;
+        const uint64_t di = (uint64_t)c * h + i0 + r;
+        if (FHD_IN(k, (uint64_t)RB * 3, kSiteRowSmem))
+            sh[k] = FHD_IN(di, 3ull * h, kSiteRowShift) ? modW8.mod(pass_ld<kL2>(fd.D + di)) : 0;
+    }
+    sync();
+    for (uint32_t r = 0; r < nr; ++r) {
+        uint32_t du[3], fs[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const uint32_t sc = sh[r * 3 + c];
+            const uint32_t a = sc >> 3, rr = sc & 7;
+            // first source pixel of output pixel 0: -a-1 (encrypt) or a (decrypt), mod w
+            int s0 = kEnc ? -(int)a - 1 : (int)a;
+            if (s0 < 0) s0 += (int)w;
+            du[c] = (uint32_t)s0 >> 2;
+            const uint32_t o = (uint32_t)s0 & 3;
+            fs[c] = kEnc ? 8 * o + 8 - rr : 8 * o + rr;
+        }
+        const uint32_t *plane = reinterpret_cast<const uint32_t *>(In + (size_t)r * pitch);
+        uint32_t *orow = reinterpret_cast<uint32_t *>(dst + (uint64_t)r * rowB);
+        for (uint32_t g = tid; g < W4; g += nthr) {
+            uint32_t q[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                uint32_t u = g + du[c];
+                u = u >= W4 ? u - W4 : u;
+                uint32_t u1 = u + 1 == W4 ? 0 : u + 1;
+                if (!FHD_IN(u, W4, kSiteRowSmem) || !FHD_IN(u1, W4, kSiteRowSmem)) u = u1 = 0;
+                q[c] = __funnelshift_rc(plane[c * W4 + u], plane[c * W4 + u1], fs[c]);
+            }
+            if (!FHD_IN((uint64_t)(i0 + r) * rowB + 12 * g + 11, fd.N, kSiteRowStore)) continue;
+            uint32_t *wp = orow + 3 * g;
+            wp[0] = __byte_perm(__byte_perm(q[0], q[1], 0x1040), q[2], 0x3410);
+            wp[1] = __byte_perm(__byte_perm(q[1], q[0], 0x2601), q[2], 0x3250);
+            wp[2] = __byte_perm(__byte_perm(q[2], q[0], 0x3072), q[1], 0x3710);
+        }
+    }
+}
+
 // Row pass over a band of RB whole rows.  Encrypt: G = left rotation of each
 // channel row of F by s_h bits.  Decrypt: output = right rotation of each
 // channel row of G by s_h bits.
@@ -364,6 +438,10 @@ __device__ void row_pass(const FrameDesc &fd, uint32_t band, uint8_t *smem, uint
 
     // ---- load the band (rows are contiguous in global memory)
     const bool v16 = rowB % 16 == 0 && aligned(src, 16) && aligned(dst, 16);
+    if (C == 3 && (w & 15) == 0 && v16) {
+        row_pass_planar<kEnc, kL2>(fd, i0, nr, src, dst, In, sh, tid, nthr, sync);
+        return;
+    }
     if (v16) {
         const uint32_t nvr = rowB / 16;
         for (uint32_t k = tid; k < nr * nvr; k += nthr) {
