@@ -389,7 +389,10 @@ int fhd_set_encrypt_route(int route);
  * on a stream that is being captured into a CUDA graph stay on that stream.
  * cipher_set_partition(c, 0) turns it off for this handle; enabling fails
  * with FHD_ERR_CUDA (and leaves it off) where partitioning is unavailable.
- * cipher_get_partition reports the SM counts in use (0, 0 when off). */
+ * cipher_set_partition(c, 2) splits three ways: LHCS_m, the digest stage
+ * (sub-frame SHA-256 and fold, Algorithm 1) on a second small partition, and
+ * the rest; other modes are FHD_ERR_INVALID_ARG.  cipher_get_partition reports
+ * the SM counts of the LHCS_m partition and of the rest (0, 0 when off). */
 int cipher_set_partition(fhd_cipher *c, int enable);
 int cipher_get_partition(fhd_cipher *c, uint32_t *chain_sms, uint32_t *bulk_sms);
 

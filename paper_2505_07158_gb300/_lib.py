@@ -420,9 +420,11 @@ class Cipher:
                                         ctypes.byref(count)), self._h)
         return [(KERNEL_KINDS[kinds[i]], t0[i], t1[i]) for i in range(min(n, count.value))]
 
-    def set_partition(self, enable: bool):
-        """Run LHCS_m on its own small SM partition (green contexts) or not."""
-        _check(load().cipher_set_partition(self._handle(), 1 if enable else 0), self._h)
+    def set_partition(self, enable):
+        """Run LHCS_m on its own small SM partition (green contexts; True or 1), LHCS_m and the digest stage
+        each on their own (2), or neither (False or 0)."""
+        mode = int(enable) if not isinstance(enable, bool) else (1 if enable else 0)
+        _check(load().cipher_set_partition(self._handle(), mode), self._h)
 
     def set_layout(self, layout: str):
         """Worker warp layout: "latency" (six chains per warp) or "throughput" (eight)."""

@@ -36,15 +36,18 @@ struct fhd_cipher {
     // streams: `chain` in the small partition (LHCS_m) and `bulk` in the rest
     // (digests, workers, permutation), and joins back; ev = fork, digests,
     // master, join.
+    // With the three-way partition (mode 2) the digest stage runs on `digest3` in a partition of its own,
+    // LHCS_m on `chain3` and the rest on `bulk3`; ev[4] orders LHCS_m after the bulk stream's work so far.
     struct Scratch {
         cudaStream_t stream;
         uint8_t *ptr;
         size_t cap;
         cudaStream_t chain = nullptr, bulk = nullptr;
-        cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+        cudaStream_t chain3 = nullptr, digest3 = nullptr, bulk3 = nullptr;
+        cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     };
     std::vector<Scratch> scratch;
-    bool partition = false;
+    int partition = 0;   // 0 off, 1 LHCS_m on its own SMs, 2 LHCS_m and the digest stage each on their own
     int layout = FHD_LAYOUT_LATENCY;
     uint32_t worker_cta = 1;   // worker warps per CTA of the keystream kernel
     uint32_t digest_mode = FHD_DIGEST_XOR;
@@ -194,6 +197,10 @@ struct DevicePartition {
     CUgreenCtx chain = nullptr, bulk = nullptr;
     unsigned chain_sms = 0, bulk_sms = 0;
     std::string why;   // the step that failed, when !ok
+    // The three-way split (cipher_set_partition(c, 2)): LHCS_m, the digest stage, and the rest.
+    bool tried3 = false, ok3 = false;
+    CUgreenCtx chain3 = nullptr, digest3 = nullptr, bulk3 = nullptr;
+    unsigned chain3_sms = 0, digest3_sms = 0, bulk3_sms = 0;
 };
 
 std::mutex g_part_mu;
@@ -264,8 +271,68 @@ const DevicePartition *device_partition(int dev) {
     return p.ok ? &p : nullptr;
 }
 
-// The internal streams and events of caller stream `sc` (created on first use).
+// The three-way partition of device `dev` (kChainSms for LHCS_m, kChainSms for the digest stage, the rest),
+// created on first use; nullptr where the device or driver cannot partition.
+const DevicePartition *device_partition3(int dev) {
+    if (!device_partition(dev)) return nullptr;
+    std::lock_guard<std::mutex> lk(g_part_mu);
+    DevicePartition &p = g_part[dev];
+    if (!p.tried3) {
+        p.tried3 = true;
+        // One split into two groups of kChainSms and the remainder (a remainder cannot be split again).
+        CUdevice cd;
+        CUdevResource all{}, g2[2] = {}, r2{};
+        CUdevResourceDesc da = nullptr, dd = nullptr, db = nullptr;
+        unsigned n2 = 2;
+        auto ok = [&](CUresult rr, const char *what) {
+            if (rr != CUDA_SUCCESS) p.why = std::string(what) + " failed with CUresult " + std::to_string((int)rr);
+            return rr == CUDA_SUCCESS;
+        };
+        CUdevResource &a = g2[0], &d = g2[1];
+        if (ok(g_drv.deviceGet(&cd, dev), "cuDeviceGet") &&
+            ok(g_drv.getDevResource(cd, &all, CU_DEV_RESOURCE_TYPE_SM), "cuDeviceGetDevResource") &&
+            ok(g_drv.smSplit(g2, &n2, &all, &r2, 0, kChainSms), "cuDevSmResourceSplitByCount") &&
+            ok(n2 == 2 ? CUDA_SUCCESS : CUDA_ERROR_INVALID_VALUE, "two SM groups") &&
+            ok(g_drv.genDesc(&da, &a, 1), "cuDevResourceGenerateDesc") &&
+            ok(g_drv.genDesc(&dd, &d, 1), "cuDevResourceGenerateDesc") &&
+            ok(g_drv.genDesc(&db, &r2, 1), "cuDevResourceGenerateDesc") &&
+            ok(g_drv.greenCreate(&p.chain3, da, cd, CU_GREEN_CTX_DEFAULT_STREAM), "cuGreenCtxCreate") &&
+            ok(g_drv.greenCreate(&p.digest3, dd, cd, CU_GREEN_CTX_DEFAULT_STREAM), "cuGreenCtxCreate") &&
+            ok(g_drv.greenCreate(&p.bulk3, db, cd, CU_GREEN_CTX_DEFAULT_STREAM), "cuGreenCtxCreate")) {
+            p.ok3 = true;
+            p.chain3_sms = a.sm.smCount;
+            p.digest3_sms = d.sm.smCount;
+            p.bulk3_sms = r2.sm.smCount;
+        }
+    }
+    return p.ok3 ? &p : nullptr;
+}
+
+// The internal streams and events of caller stream `sc` for the handle's partition mode (created on first
+// use).
 cudaError_t partition_streams(fhd_cipher *c, fhd_cipher::Scratch &sc) {
+    if (!sc.ev[0]) {
+        for (auto &e : sc.ev) {
+            cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+            if (r != cudaSuccess) return r;
+        }
+    }
+    if (c->partition == 2) {
+        if (sc.chain3) return cudaSuccess;
+        const DevicePartition *p = device_partition3(c->device);
+        if (!p) return cudaErrorNotSupported;
+        CUstream s3[3] = {nullptr, nullptr, nullptr};
+        CUgreenCtx g3[3] = {p->chain3, p->digest3, p->bulk3};
+        for (int k = 0; k < 3; ++k)
+            if (g_drv.greenStream(&s3[k], g3[k], CU_STREAM_NON_BLOCKING, 0) != CUDA_SUCCESS) {
+                for (int j = 0; j < k; ++j) g_drv.streamDestroy(s3[j]);
+                return cudaErrorNotSupported;
+            }
+        sc.chain3 = (cudaStream_t)s3[0];
+        sc.digest3 = (cudaStream_t)s3[1];
+        sc.bulk3 = (cudaStream_t)s3[2];
+        return cudaSuccess;
+    }
     if (sc.chain) return cudaSuccess;
     const DevicePartition *p = device_partition(c->device);
     if (!p) return cudaErrorNotSupported;
@@ -274,10 +341,6 @@ cudaError_t partition_streams(fhd_cipher *c, fhd_cipher::Scratch &sc) {
     if (g_drv.greenStream(&b, p->bulk, CU_STREAM_NON_BLOCKING, 0) != CUDA_SUCCESS) {
         g_drv.streamDestroy(a);
         return cudaErrorNotSupported;
-    }
-    for (auto &e : sc.ev) {
-        cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
-        if (r != cudaSuccess) return r;
     }
     sc.chain = (cudaStream_t)a;
     sc.bulk = (cudaStream_t)b;
@@ -427,7 +490,7 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
     if (e != cudaSuccess) return cuda_fail(c, e, "prepare");
     static thread_local Batch b;   // ~12 KB: kept off the stack
     bool part = false;
-    cudaStream_t sc = s, sb = s;
+    cudaStream_t sc = s, sb = s, sd = s;   // LHCS_m, the rest, the digest stage
     cudaEvent_t *ev = nullptr;
     for (uint32_t base = 0; base < count; base += fhd::kMaxBatch) {
         uint32_t m = count - base < (uint32_t)fhd::kMaxBatch ? count - base : (uint32_t)fhd::kMaxBatch;
@@ -456,11 +519,14 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
             fhd_cipher::Scratch *slot = scratch_of(c, s);
             part = c->partition && slot && !capturing(s) && partition_streams(c, *slot) == cudaSuccess;
             if (part) {
-                sc = slot->chain;
-                sb = slot->bulk;
+                const bool three = c->partition == 2;
+                sc = three ? slot->chain3 : slot->chain;
+                sb = three ? slot->bulk3 : slot->bulk;
+                sd = three ? slot->digest3 : sb;
                 ev = slot->ev;
                 if ((e = cudaEventRecord(ev[0], s)) != cudaSuccess || (e = cudaStreamWaitEvent(sb, ev[0], 0)) != cudaSuccess ||
-                    (e = cudaStreamWaitEvent(sc, ev[0], 0)) != cudaSuccess)
+                    (e = cudaStreamWaitEvent(sc, ev[0], 0)) != cudaSuccess ||
+                    (three && (e = cudaStreamWaitEvent(sd, ev[0], 0)) != cudaSuccess))
                     return cuda_fail(c, e, "fork");
             }
         }
@@ -506,21 +572,24 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
         }
         b.group_begin[b.groups] = (uint16_t)pos;
         if (encrypt) {
-            if ((e = timed(c, FHD_K_SHA, sb, [&] {
-                     cudaError_t r = fhd::launch_sha_subframes(b, sb);
+            if ((e = timed(c, FHD_K_SHA, sd, [&] {
+                     cudaError_t r = fhd::launch_sha_subframes(b, sd);
                      if (r != cudaSuccess) return r;
-                     return b.digest_mode == FHD_DIGEST_TREE ? fhd::launch_tree_batch(b, sb)
-                                                             : fhd::launch_fold_batch(b, sb);
+                     return b.digest_mode == FHD_DIGEST_TREE ? fhd::launch_tree_batch(b, sd)
+                                                             : fhd::launch_fold_batch(b, sd);
                  })) != cudaSuccess)
                 return cuda_fail(c, e, "sha launch");
             if (digests_done && !b.digest_masked && base + m >= count &&
-                (e = cudaEventRecord(digests_done, sb)) != cudaSuccess)
+                (e = cudaEventRecord(digests_done, sd)) != cudaSuccess)
                 return cuda_fail(c, e, "record digest event");
         }
         // LHCS_m of this group of frames after the bulk stream's work so far: this group's digests,
         // and the previous group's workers, which read the iterates this LHCS_m overwrites.
         if (part && ((e = cudaEventRecord(ev[1], sb)) != cudaSuccess || (e = cudaStreamWaitEvent(sc, ev[1], 0)) != cudaSuccess))
             return cuda_fail(c, e, "bulk to chain stream");
+        if (part && sd != sb &&
+            ((e = cudaEventRecord(ev[4], sd)) != cudaSuccess || (e = cudaStreamWaitEvent(sc, ev[4], 0)) != cudaSuccess))
+            return cuda_fail(c, e, "digest to chain stream");
         if (base == 0)
             for (uint32_t k = 0; k < hk.n_key_waits; ++k)
                 if (hk.key_waits[k] && (e = cudaStreamWaitEvent(sc, (cudaEvent_t)hk.key_waits[k], 0)) != cudaSuccess)
@@ -1193,9 +1262,10 @@ int fhd_fp64_probe(uint32_t warps_per_subpartition, uint32_t iters, double *sink
 
 int cipher_set_partition(fhd_cipher *c, int enable) {
     if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
-    if (!enable) { c->partition = false; return FHD_OK; }
-    if (!device_partition(c->device)) {
-        c->partition = false;
+    if (enable < 0 || enable > 2) return fail(c, FHD_ERR_INVALID_ARG, "partition mode must be 0, 1 or 2");
+    if (!enable) { c->partition = 0; return FHD_OK; }
+    if (!(enable == 2 ? device_partition3(c->device) : device_partition(c->device))) {
+        c->partition = 0;
         std::string why;
         {
             std::lock_guard<std::mutex> lk(g_part_mu);
@@ -1203,7 +1273,7 @@ int cipher_set_partition(fhd_cipher *c, int enable) {
         }
         return fail(c, FHD_ERR_CUDA, "the device or driver cannot partition its SMs (green contexts): " + why);
     }
-    c->partition = true;
+    c->partition = enable;
     return FHD_OK;
 }
 
@@ -1309,6 +1379,12 @@ int cipher_set_layout(fhd_cipher *c, int layout) {
 
 int cipher_get_partition(fhd_cipher *c, uint32_t *chain_sms, uint32_t *bulk_sms) {
     if (!c || !chain_sms || !bulk_sms) return fail(c, FHD_ERR_INVALID_ARG, "null argument");
+    if (c->partition == 2) {
+        const DevicePartition *p = device_partition3(c->device);
+        *chain_sms = p ? p->chain3_sms : 0;
+        *bulk_sms = p ? p->bulk3_sms : 0;
+        return FHD_OK;
+    }
     const DevicePartition *p = c->partition ? device_partition(c->device) : nullptr;
     *chain_sms = p ? p->chain_sms : 0;
     *bulk_sms = p ? p->bulk_sms : 0;
@@ -1326,6 +1402,9 @@ void cipher_destroy(fhd_cipher *c) {
             if (e) cudaEventDestroy(e);
         if (sc.chain) g_drv.streamDestroy((CUstream)sc.chain);
         if (sc.bulk) g_drv.streamDestroy((CUstream)sc.bulk);
+        if (sc.chain3) g_drv.streamDestroy((CUstream)sc.chain3);
+        if (sc.digest3) g_drv.streamDestroy((CUstream)sc.digest3);
+        if (sc.bulk3) g_drv.streamDestroy((CUstream)sc.bulk3);
     }
     cudaFree(c->d_states);
     cudaFree(c->d_status);

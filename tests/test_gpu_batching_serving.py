@@ -262,22 +262,29 @@ def test_launch_count_per_call():
 
 
 def test_sm_partition_matches_single_stream():
-    """The SM partition (LHCS_m on its own SMs, the rest on the others) changes where kernels run,
-    not what they compute: a mixed batch encrypted with it on and off is byte-identical, and both
-    match the oracle."""
+    """The SM partition (LHCS_m on its own SMs, the rest on the others; or three ways, the digest stage on
+    SMs of its own too) changes where kernels run, not what they compute: a mixed batch encrypted in every
+    mode is byte-identical, and all match the oracle."""
     shapes = [(60, 100, 3), (32, 48, 1), (96, 128, 3)]
     key = si.key(630)
     frames = [to_dev(si.gradient_frame(*s, t=t, seed=631)) for t, s in enumerate(shapes)]
     outs = []
-    for on in (True, False):
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for mode in (1, 0, 2):   # LHCS_m on its own SMs; no partition; LHCS_m and the digest stage on their own
         c = fhd.Cipher(key)
-        if not on:
-            c.set_partition(False)
+        try:
+            c.set_partition(mode)
+        except fhd.FhdError as exc:   # a device or driver without green contexts: that mode is not run
+            assert exc.code == fhd.FHD_ERR_CUDA and mode, exc
+            outs.append(None)
+            continue
         sid = c.open_stream()
         chain, bulk = c.partition()
-        if on and chain:
-            assert bulk > chain and (chain + bulk) == torch.cuda.get_device_properties(0).multi_processor_count
-        if not on:
+        if mode == 1 and chain:
+            assert bulk > chain and (chain + bulk) == sms
+        if mode == 2 and chain:
+            assert bulk > chain and chain + bulk < sms     # the digest stage's SMs are in neither
+        if mode == 0:
             assert (chain, bulk) == (0, 0)
         E = [torch.empty_like(f) for f in frames]
         H = torch.empty((len(frames), 32), dtype=torch.uint8, device=dev())
@@ -285,13 +292,19 @@ def test_sm_partition_matches_single_stream():
         c.encrypt_frames([(sid, frames[k], E[k], H[k]) for k in range(len(frames))], stream=s)
         torch.cuda.synchronize()
         outs.append(([host(e) for e in E], host(H)))
-    for k in range(len(frames)):
-        assert np.array_equal(outs[0][0][k], outs[1][0][k]), k
-    assert np.array_equal(outs[0][1], outs[1][1])
+    base = outs[1]   # no partition
+    for other in (0, 2):
+        if outs[other] is None:
+            continue
+        for k in range(len(frames)):
+            assert np.array_equal(base[0][k], outs[other][0][k]), (other, k)
+        assert np.array_equal(base[1], outs[other][1])
+    with pytest.raises(fhd.FhdError):
+        fhd.Cipher(key).set_partition(3)
     ref = oracle.Stream.from_key(key)
     for k in range(len(frames)):
         E_ref, H_ref = ref.encrypt(host(frames[k]))
-        assert np.array_equal(outs[0][0][k], E_ref), k
+        assert np.array_equal(base[0][k], E_ref), k
 
 
 def test_more_than_one_descriptor_group():
