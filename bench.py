@@ -91,6 +91,9 @@ def parse():
     ap.add_argument("--inflight", type=int, default=None,
                     help="clips in flight on separate buffers: later clips' digest stage and LHCS_m overlap earlier "
                          "clips' keystreams (default: the tuned table's, else 5)")
+    ap.add_argument("--int-mix", type=int, default=None, choices=range(9), metavar="0..8",
+                    help="worker warps per 8 (throughput layout) that step on the integer pipes beside the "
+                         "binary64 ones (default: the tuned table's, else 0)")
     ap.add_argument("--worker-window", type=int, default=None,
                     help="clip k's workers (both sides) wait for the workers of clip k - W, so about W clips' "
                          "workers share the FP64 pipes while later clips' digests and LHCS_m run ahead "
@@ -361,7 +364,7 @@ def run_ours(args):
     pipe = autotune.pipeline_defaults() or {}
     split_source = {}
     for name, attr, default in (("layout", "layout", "throughput"), ("inflight", "inflight", 5),
-                                ("worker_window", "worker_window", 3)):
+                                ("worker_window", "worker_window", 3), ("int_mix", "int_mix", 0)):
         if getattr(args, attr) is None:
             setattr(args, attr, pipe.get(name, default))
             split_source[name] = "tuned table" if name in pipe else "built-in default"
@@ -382,6 +385,8 @@ def run_ours(args):
     dec.set_layout(args.layout)
     enc.set_worker_cta(args.worker_cta)
     dec.set_worker_cta(args.worker_cta)
+    enc.set_int_mix(args.int_mix)
+    dec.set_int_mix(args.int_mix)
     sid, rid = enc.open_stream(), dec.open_stream()
     stream = torch.cuda.current_stream()
 
@@ -728,6 +733,7 @@ def run_ours(args):
                                    "decrypt_frames on the receiver's (its chaotic stage waits for the digests, its "
                                    "inverse permutation for the ciphertext)",
                        "clips_in_flight": INF, "next_clip_gate": args.gate, "worker_window": WW,
+                       "int_mix_per8": args.int_mix,
                        "worker_layout": args.layout, "worker_warps_per_cta": args.worker_cta,
                        "encrypt_route": args.encrypt_route,
                        "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),

@@ -413,6 +413,20 @@ int cipher_set_layout(fhd_cipher *c, int layout);
  * same for every value; FHD_ERR_INVALID_ARG for another value. */
 int cipher_set_worker_cta(fhd_cipher *c, uint32_t warps);
 
+/* Worker warps of the eight-chain layout (FHD_LAYOUT_THROUGHPUT), per 8
+ * consecutive warps, that run their RK4 steps (Sec. II-B, Algorithm 2) on the
+ * integer pipes instead of the binary64 pipe: every multiply and add done in
+ * integer arithmetic, rounded to nearest even exactly as IEEE 754 binary64
+ * prescribes, with the binary64 instruction for the operands that path does
+ * not cover (a step with such an operand is done again with binary64
+ * instructions).  The two kinds of pipe work side by side on a GB300
+ * sub-partition, but an integer-pipe step takes ~3,300 warp instructions and
+ * about four times as long as a binary64 one, and a worker launch lasts as long
+ * as its slowest warp: with the clip pipeline every mix measured slower than 0.
+ * 0 (the default) to 8; results are bit-identical for every value;
+ * FHD_ERR_INVALID_ARG above 8. */
+int cipher_set_int_mix(fhd_cipher *c, uint32_t per8);
+
 
 /* ---- Frame statistics of the paper's evaluation (Sec. III and IV-B) ----
  * Batched over `count` frames stored contiguously in device memory as
@@ -493,6 +507,17 @@ int cipher_profile_spans(fhd_cipher *c, void *origin, uint32_t cap, int32_t *kin
  * double per SM that the kernel may write.  Bad arguments return
  * FHD_ERR_INVALID_ARG and enqueue nothing. */
 int fhd_fp64_probe(uint32_t warps_per_subpartition, uint32_t iters, double *sink, uint64_t *lane_ops, void *stream);
+
+/* Check of the integer-pipe binary64 multiply and add that cipher_set_int_mix
+ * uses, against the binary64 instructions, on `pairs` (1 .. 2^40) operand
+ * pairs from a counter-based generator seeded by `seed` (any bit patterns, the
+ * chaotic range, near cancellation, the alignment boundary of the sum, few
+ * significand bits for exact products and ties, zeros and subnormals).
+ * counts (host, 4 entries) receives: mismatched products, mismatched sums
+ * (bit for bit; the target is 0 and 0), and the products and sums that the
+ * integer fast path took.  Synchronises `stream`.  FHD_ERR_INVALID_ARG for a
+ * null counts or pairs out of range; FHD_ERR_OOM; FHD_ERR_CUDA. */
+int fhd_binary64_check(uint64_t pairs, uint64_t seed, uint64_t *counts, void *stream);
 
 /* Number of kernels this library has launched in this process. */
 uint64_t fhd_launch_count(void);

@@ -41,7 +41,7 @@ EXPORTS = (
     "fhd_frame_digest_tree", "fhd_fp64_probe", "fhd_set_encrypt_route", "encrypt_frames_persistent",
     "decrypt_frames_persistent", "cipher_round_trip_persistent", "cipher_set_persistent_limits",
     "cipher_set_worker_cta", "cipher_persistent_trace", "fhd_row_band", "fhd_set_row_band", "fhd_build_flags",
-    "fhd_bounds_report", "fhd_bounds_site_name", "fhd_bounds_selftest",
+    "fhd_bounds_report", "fhd_bounds_site_name", "fhd_bounds_selftest", "cipher_set_int_mix", "fhd_binary64_check",
 )
 FHD_BUILD_BOUNDS_CHECK = 1
 KERNEL_KINDS = ("sha", "master", "keystream", "encrypt", "decrypt")
@@ -153,6 +153,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "cipher_set_worker_cta": (i32, [P, u32]),
             "cipher_persistent_trace": (i32, [P, u32, P]),
             "fhd_build_flags": (u32, []),
+            "cipher_set_int_mix": (i32, [P, u32]),
+            "fhd_binary64_check": (i32, [u64, u64, P, P]),
             "fhd_bounds_report": (i32, [ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.POINTER(u64),
                                         ctypes.POINTER(u64)]),
             "fhd_bounds_site_name": (ctypes.c_char_p, [u32]),
@@ -434,6 +436,10 @@ class Cipher:
         """Worker warps per CTA of the worker kernel (1, 2, 4 or 8); same results for every value."""
         _check(load().cipher_set_worker_cta(self._handle(), int(warps)), self._h)
 
+    def set_int_mix(self, per8: int):
+        """Eight-chain worker warps per 8 that step on the integer pipes (0..8); same results for every value."""
+        _check(load().cipher_set_int_mix(self._handle(), int(per8)), self._h)
+
     def partition(self) -> tuple:
         """(SMs of the LHCS_m partition, SMs of the rest); (0, 0) when off."""
         a, b = ctypes.c_uint32(), ctypes.c_uint32()
@@ -641,6 +647,14 @@ def fhd_frame_scratch_bytes(n_workers: int, height: int, width: int, channels: i
 
 def fhd_launch_count() -> int:
     return int(load().fhd_launch_count())
+
+
+def fhd_binary64_check(pairs: int, seed: int = 1, stream=None) -> dict:
+    """Integer-pipe binary64 multiply and add against the binary64 instructions on `pairs` generated operand
+    pairs: {"bad_mul", "bad_add", "fast_mul", "fast_add"}."""
+    out = (ctypes.c_uint64 * 4)()
+    _check(load().fhd_binary64_check(pairs, seed, out, _stream_ptr(stream)))
+    return {"bad_mul": int(out[0]), "bad_add": int(out[1]), "fast_mul": int(out[2]), "fast_add": int(out[3])}
 
 
 def fhd_build_flags() -> int:

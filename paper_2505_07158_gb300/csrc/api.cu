@@ -50,6 +50,7 @@ struct fhd_cipher {
     int partition = 0;   // 0 off, 1 LHCS_m on its own SMs, 2 LHCS_m and the digest stage each on their own
     int layout = FHD_LAYOUT_LATENCY;
     uint32_t worker_cta = 1;   // worker warps per CTA of the keystream kernel
+    uint32_t int_mix = 0;      // eight-chain worker warps per 8 on the integer pipes
     uint32_t digest_mode = FHD_DIGEST_XOR;
     uint32_t transport = FHD_TRANSPORT_PLAIN;
     cudaStream_t last_stream = nullptr;
@@ -500,6 +501,7 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
         b.digest_mode = c->digest_mode;
         b.digest_masked = c->transport == FHD_TRANSPORT_MASKED;
         b.encrypt = encrypt;
+        b.int_mix = c->layout == FHD_LAYOUT_THROUGHPUT ? c->int_mix : 0;
         b.hstep = c->h;
         b.hhalf = c->h / 2.0;
         b.hsixth = c->h / 6.0;
@@ -1260,6 +1262,24 @@ int fhd_fp64_probe(uint32_t warps_per_subpartition, uint32_t iters, double *sink
     return FHD_OK;
 }
 
+int fhd_binary64_check(uint64_t pairs, uint64_t seed, uint64_t *counts, void *stream) {
+    if (!counts) return fail(nullptr, FHD_ERR_INVALID_ARG, "null counts");
+    if (pairs < 1 || pairs > (1ull << 40)) return fail(nullptr, FHD_ERR_INVALID_ARG, "pairs must be 1..2^40");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long *d = nullptr;
+    cudaError_t e = cudaMallocAsync(&d, 4 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+    unsigned long long h[4] = {0, 0, 0, 0};
+    e = cudaMemsetAsync(d, 0, sizeof h, s);
+    if (e == cudaSuccess) e = fhd::launch_binary64_check(pairs, seed, d, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(d, s);
+    if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("binary64 check: ") + cudaGetErrorString(e));
+    for (int k = 0; k < 4; ++k) counts[k] = h[k];
+    return FHD_OK;
+}
+
 int cipher_set_partition(fhd_cipher *c, int enable) {
     if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
     if (enable < 0 || enable > 2) return fail(c, FHD_ERR_INVALID_ARG, "partition mode must be 0, 1 or 2");
@@ -1359,6 +1379,13 @@ int fhd_stats_local_entropy(const uint8_t *frames, uint32_t count, uint32_t heig
     cudaFreeAsync(ent, s);
     if (!status) cudaFreeAsync(st, s);
     if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("local entropy launch: ") + cudaGetErrorString(e));
+    return FHD_OK;
+}
+
+int cipher_set_int_mix(fhd_cipher *c, uint32_t per8) {
+    if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
+    if (per8 > 8) return fail(c, FHD_ERR_INVALID_ARG, "per8 must be 0..8");
+    c->int_mix = per8;
     return FHD_OK;
 }
 

@@ -69,13 +69,23 @@ __global__ void __launch_bounds__(32) master_raw_kernel(double *state5, const ui
 // K2b: one warp per kPairs worker pairs of one frame (three with the six-chain step, four with the
 // eight-chain step); a CTA carries blockDim.x / 32 consecutive such warps (warps of one CTA are spread over
 // the SM's sub-partitions).
-template <int kPairs>
+// kMix (eight-chain step only): b.int_mix of every 8 consecutive warps step on the integer pipes instead of
+// the binary64 pipe (the same bytes: rk4_step_lanes8_int).  A separate instantiation, so that the binary64-only
+// kernel keeps its own register allocation.
+template <int kPairs, bool kMix = false>
 __global__ void __launch_bounds__(256) keystream_kernel(const __grid_constant__ Batch b) {
     const uint32_t wpf = (b.n + kPairs - 1) / kPairs;
     const uint32_t task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const uint32_t f = task / wpf, pg = task % wpf;
     if (f >= b.count) return;
-    keystream_warp<kPairs>(b.f[f], b.n, Rk4{b.hstep, b.hhalf, b.hsixth}, pg, threadIdx.x & 31);
+    const Rk4 c{b.hstep, b.hhalf, b.hsixth};
+    if constexpr (kMix) {
+        if ((task & 7) < b.int_mix) {
+            keystream_warp<kPairs, true>(b.f[f], b.n, c, pg, threadIdx.x & 31);
+            return;
+        }
+    }
+    keystream_warp<kPairs>(b.f[f], b.n, c, pg, threadIdx.x & 31);
 }
 
 }  // namespace
@@ -100,7 +110,10 @@ cudaError_t launch_keystream(const Batch &b, cudaStream_t s, bool dense, uint32_
     const uint32_t k = warps_per_cta ? warps_per_cta : 1;
     if (dense) {
         const uint32_t warps = b.count * ((b.n + 3) / 4);
-        keystream_kernel<4><<<(warps + k - 1) / k, 32 * k, 0, s>>>(b);
+        if (b.int_mix)
+            keystream_kernel<4, true><<<(warps + k - 1) / k, 32 * k, 0, s>>>(b);
+        else
+            keystream_kernel<4><<<(warps + k - 1) / k, 32 * k, 0, s>>>(b);
         note_launch();
         return cudaGetLastError();
     }

@@ -2,6 +2,7 @@
 // and the persistent batch kernel: the lane-packed RK4 steps, the reconstruction, LHCS_m of one stream and
 // one warp of worker pairs.  See chaos.cu for the design.
 #pragma once
+#include "binary64_int.cuh"
 #include "bounds.cuh"
 #include "common.cuh"
 #include "sha256_core.cuh"
@@ -135,6 +136,68 @@ __device__ __forceinline__ void rk4_step_lanes8(double &s, const LaneRole8 &r, c
     }
 }
 
+// Integer-pipe operations of one lane without a vote: the fast path's result and, in `sp`, whether the
+// lane needs the binary64 instruction instead.
+__device__ __forceinline__ double lane_mul(double a, double b, bool &sp) {
+    bool x;
+    const uint64_t r = b64_mul((uint64_t)__double_as_longlong(a), (uint64_t)__double_as_longlong(b), x);
+    sp = sp || x;
+    return __longlong_as_double((long long)r);
+}
+__device__ __forceinline__ double lane_add(double a, double b, bool &sp) {
+    bool x;
+    const uint64_t r = b64_add((uint64_t)__double_as_longlong(a), (uint64_t)__double_as_longlong(b), x);
+    sp = sp || x;
+    return __longlong_as_double((long long)r);
+}
+// 2 k, exactly: one more in the exponent field while the double stays normal and finite.
+__device__ __forceinline__ double lane_twice(double k, bool &sp) {
+    const uint64_t K = (uint64_t)__double_as_longlong(k);
+    sp = sp || ((uint32_t)(K >> 52) & 0x7ff) - 1 >= 0x7fd;
+    return __longlong_as_double((long long)(K + (1ull << 52)));
+}
+
+// The eight-chain step with every rounded operation on the integer pipes (binary64_int.cuh): bit-identical
+// to rk4_step_lanes8.  Each fused multiply-add of that step is split into its multiply and its add, which
+// rounds the same way because in every use one of the two is exact: a factor of +-1 (Pb = 1, B2 = +-1,
+// kS = +-1), a factor 2 (the combination), or an addend of -0.  The products by kS = +-1 are sign flips and
+// the addends -0 after a rounded product are dropped (x + (-0) = x for every x the product can be, +0
+// included).  The operations take no vote: a lane whose operands leave the integer fast path marks the
+// step, and a marked step is done again, from its starting state, by rk4_step_lanes8 (one vote per step;
+// the step's stream bytes, those of the state before it, are emitted once).
+template <class F>
+__device__ __forceinline__ void rk4_step_lanes8_int(double &s, const LaneRole8 &r, const Rk4 &c, F &&after_fetch) {
+    const long long kneg = r.kS < 0.0 ? (long long)kSign : 0;
+    const double s0 = s;
+    bool sp = false;
+    double tin = s, acc = 0.0;
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+        const double a = __shfl_sync(0xffffffffu, tin, r.s1);
+        const double b = __shfl_sync(0xffffffffu, tin, r.s2);
+        const double d = __shfl_sync(0xffffffffu, tin, r.s3);
+        if (st == 0) after_fetch(tin);
+        const double Pc = r.vx ? tin : 0.0;
+        const double Qb = r.vx ? 1.0 : d;
+        const double P2 = r.vy ? tin : 0.0;
+        const double p = lane_add(lane_mul(a, r.Pb, sp), -Pc, sp);
+        const double q = lane_mul(b, Qb, sp);
+        const double p2 = lane_add(lane_mul(p, r.B2, sp), -P2, sp);
+        const double k = lane_add(__longlong_as_double(__double_as_longlong(q) ^ kneg), p2, sp);
+        if (st < 3) {
+            tin = lane_add(s, lane_mul(st == 2 ? c.h : c.hh, k, sp), sp);
+            acc = st == 0 ? k : lane_add(acc, lane_twice(k, sp), sp);
+        } else {
+            acc = lane_add(acc, k, sp);
+            s = lane_add(s, lane_mul(c.h6, acc, sp), sp);
+        }
+    }
+    if (__any_sync(0xffffffffu, sp)) {
+        s = s0;
+        rk4_step_lanes8(s, r, c, [](double) {});
+    }
+}
+
 // Sec. II-A, Fig. 1a: reconstruct one initial condition from 8 digest bytes
 // (two for the integer part mod u, six for the 48-bit fraction), v by
 // magnitude; non-finite or |v| >= 2^52 contributes 0 and 0.
@@ -232,7 +295,7 @@ __device__ __forceinline__ void emit_bytes(double s, bool active, uint64_t pos0,
 // Worker pairs pg * kPairs .. pg * kPairs + kPairs - 1 of frame fd (Algorithm 2), run by one warp (lane = its
 // lane): lane 4c + v holds variable v of chain c, chains 2q and 2q + 1 are pair q, so the partner of a lane
 // is lane ^ 4.  Every warp of the frame runs the frame's uniform trip count (its longest slice).
-template <int kPairs>
+template <int kPairs, bool kInt = false>
 __device__ void keystream_warp(const FrameDesc &fd, uint32_t n, const Rk4 &c, uint32_t pg, int lane) {
     const int v = lane & 3, ch = lane >> 2;
     const uint32_t p = pg * kPairs + (ch >> 1);
@@ -265,9 +328,11 @@ __device__ void keystream_warp(const FrameDesc &fd, uint32_t n, const Rk4 &c, ui
         const LaneRole8 role = lane_role8(lane, fd.gamma);
         double s = chain_value;
         for (uint64_t t = 0; t < T; ++t) {
-            rk4_step_lanes8(s, role, c, [&](double prev) {
+            auto emit = [&](double prev) {
                 if (t) emit_bytes(prev, active, 24 * (t - 1) + 6 * v, need, ndb, half, Dbytes, Bp, dlim, blim);
-            });
+            };
+            if constexpr (kInt) rk4_step_lanes8_int(s, role, c, emit);
+            else rk4_step_lanes8(s, role, c, emit);
         }
         if (T) emit_bytes(s, active, 24 * (T - 1) + 6 * v, need, ndb, half, Dbytes, Bp, dlim, blim);
     }

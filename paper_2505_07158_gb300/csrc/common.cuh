@@ -40,6 +40,7 @@ struct Batch {
     uint32_t digest_mode;     // FHD_DIGEST_XOR (the paper's fold) or FHD_DIGEST_TREE
     uint32_t digest_masked;   // transmitted digest is H xor M (FHD_TRANSPORT_MASKED)
     uint32_t encrypt;         // 1: this batch encrypts (LHCS_m masks the digest), 0: decrypts (unmasks)
+    uint32_t int_mix;         // eight-chain worker warps per 8 that step on the integer pipes (0..8)
     double hstep, hhalf, hsixth;   // RK4 step h, h/2 and h/6 (rounded once, on the host)
     uint32_t u[4];            // reconstruction bounds
     uint16_t order[kMaxBatch];          // frame indices grouped by stream, in call order
@@ -206,6 +207,10 @@ cudaError_t permute_prepare();   // opt in to large dynamic shared memory
 // lane-operations the launch executes.
 cudaError_t launch_fp64_probe(uint32_t warps_per_subpartition, uint32_t iters, double *sink, uint64_t *lane_ops,
                               cudaStream_t s);
+// Integer-pipe binary64 check (probe.cu): `pairs` operand pairs from a counter-based generator, products and
+// sums compared bit for bit with the binary64 instructions; counts[0..3] (device) += mismatched products,
+// mismatched sums, products and sums taken by the integer fast path.
+cudaError_t launch_binary64_check(uint64_t pairs, uint64_t seed, unsigned long long *counts, cudaStream_t s);
 int set_strip_override(uint32_t h, uint32_t w, uint32_t C, uint32_t P);
 int set_row_band_override(uint32_t h, uint32_t w, uint32_t C, uint32_t RB);
 int set_encrypt_route(int route);   // FHD_ROUTE_TWO_PASS or FHD_ROUTE_SINGLE_PASS; -1 on a bad value

@@ -55,6 +55,15 @@ def test_checked_build_exports_the_same_symbols():
         assert fhd.fhd_build_flags() == 0
 
 
+def test_int_mix_and_binary64_check_arguments(lib):
+    import paper_2505_07158_gb300 as fhd
+    assert lib.cipher_set_int_mix(None, 1) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.fhd_binary64_check(16, 1, None, None) == fhd.FHD_ERR_INVALID_ARG
+    out = (ctypes.c_uint64 * 4)()
+    assert lib.fhd_binary64_check(0, 1, out, None) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.fhd_binary64_check((1 << 40) + 1, 1, out, None) == fhd.FHD_ERR_INVALID_ARG
+
+
 def test_bounds_calls_without_a_device(lib):
     """Host-side behaviour of the bounds calls: site names, and the default build's report (all zero, no
     device call) and self-test (refused: not a checked build)."""

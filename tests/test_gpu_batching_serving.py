@@ -362,3 +362,54 @@ def test_worker_layouts_match_oracle(layout, cta):
             assert torch.equal(R[k], frames[k])
     with pytest.raises(KeyError):
         c.set_layout("fast")
+
+
+
+@pytest.mark.parametrize("mix", [1, 3, 8])
+def test_integer_worker_mix_matches_oracle(mix):
+    """Worker warps stepping on the integer pipes (cipher_set_int_mix: mix of every 8 warps of the
+    eight-chain layout) produce the oracle's bytes, mixed with binary64 warps in one launch or alone, for
+    worker counts that fill and do not fill the last warp, at 1, 4 and 8 warps per CTA."""
+    shapes = [(40, 56, 3), (24, 40, 1)]
+    for n, cta in ((5, 1), (32, 4), (12, 8)):
+        key = si.key(670 + n + mix)
+        frames = [to_dev(si.uniform_frame(*s, seed=671 + n + k)) for k, s in enumerate(shapes)]
+        c, d = fhd.Cipher(key, n_workers=n), fhd.Cipher(key, n_workers=n)
+        for x in (c, d):
+            x.set_layout("throughput")
+            x.set_worker_cta(cta)
+            x.set_int_mix(mix)
+        sid, rid = c.open_stream(), d.open_stream()
+        E = [torch.empty_like(f) for f in frames]
+        R = [torch.empty_like(f) for f in frames]
+        H = torch.empty((len(frames), 32), dtype=torch.uint8, device=dev())
+        for t in range(2):   # two frames per stream: the chaining state after integer-pipe workers
+            c.encrypt_frames([(sid, frames[k], E[k], H[k]) for k in range(len(frames))])
+            d.decrypt_frames([(rid, E[k], R[k], H[k]) for k in range(len(frames))])
+            torch.cuda.synchronize()
+            if t == 0:
+                ref = oracle.Stream.from_key(key, n=n)
+            for k in range(len(frames)):
+                E_ref, H_ref = ref.encrypt(host(frames[k]))
+                assert np.array_equal(host(E[k]), E_ref), (mix, n, t, k)
+                assert bytes(host(H[k])) == H_ref
+                assert torch.equal(R[k], frames[k])
+    with pytest.raises(fhd.FhdError):
+        c.set_int_mix(9)
+
+
+def test_integer_worker_mix_full_1080p_frame():
+    """One 1080p frame (n = 32: 8 worker warps of 8 chains, about 8,100 RK4 steps each) with every worker
+    warp on the integer pipes, and with half of them: the oracle's ciphertext and digest."""
+    key = si.key(690)
+    F = si.gradient_frame(1080, 1920, 3, t=0, seed=691)
+    E_ref, H_ref = oracle.Stream.from_key(key).encrypt(F)
+    for mix in (8, 4):
+        c = fhd.Cipher(key)
+        c.set_layout("throughput")
+        c.set_int_mix(mix)
+        sid = c.open_stream()
+        E, H = c.encrypt(sid, to_dev(F))
+        torch.cuda.synchronize()
+        assert bytes(host(H)) == H_ref, mix
+        assert np.array_equal(host(E), E_ref), mix
