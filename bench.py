@@ -50,11 +50,12 @@ HBM_PEAK_FALLBACK = 6800.0
 # per SM (an earlier probe with one warp per sub-partition), x 152 SMs x 2.07 GHz maximum SM clock.
 FP64_PEAK_TOPS_FALLBACK = 1.684 * 152 * 2.07e9 / 1e12
 RK4_FP64_OPS = 104      # per chain step: 4 x 13 (Eq. 1) + 3 x 8 (stages) + 4 x 7 (combination)
-# DRAM bytes (read + write) per 1080p frame of one launch, from ncu captures of the hot kernels on a 4-frame
-# clip, one kernel per capture (scaled by frames; cold caches, writes still in L2 at kernel end not
-# counted); None where the kernel changed after its capture.
-TRAFFIC_PER_FRAME = {"keystream": (29952 + 0) / 4, "encrypt": (24923136 + 42752 + 49837056 + 1724160) / 4,
-                     "decrypt": (49890048 + 1330176 + 24923392 + 3072) / 4, "sha": None, "master": None}
+# DRAM bytes (read + write) per 1080p frame of one launch, from ncu captures (cold caches, writes still in L2
+# at kernel end not counted): the worker kernel on a 4-frame clip, the four permutation passes on the 30-frame
+# clip (row + column pass of each direction, divided by 30); None where no capture of the current kernel exists.
+TRAFFIC_PER_FRAME = {"keystream": (29952 + 0) / 4,
+                     "encrypt": (186890496 + 130175232 + 374881536 + 156594944) / 30,
+                     "decrypt": (411278336 + 127123200 + 186961664 + 125687808) / 30, "sha": None, "master": None}
 
 
 def parse():
