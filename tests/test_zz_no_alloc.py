@@ -2,8 +2,8 @@
 allocate device memory (a real-time capture/encode loop, where an allocator
 call can block or synchronise the device and stall work in flight, or a host
 framework that reserves all device memory up front).  It must give exactly
-the digests of the allocating entry point fhd_frame_digest, call after call,
-although every call reuses the same fixed device array.
+the digests of the allocating entry point fhd_frame_digest and of the oracle,
+call after call, although every call reuses the same fixed device array.
 
 This file is collected last on purpose, so that a run stopping at the first
 failure has already run every other test; it passes on its own too."""
@@ -12,6 +12,8 @@ import ctypes
 import numpy as np
 import pytest
 import torch
+
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -40,6 +42,9 @@ def test_noalloc_digest_equals_allocating_digest_two_calls_in_a_row():
         ref = fhd.fhd_frame_digest(data, n=n, count=count)
         torch.cuda.synchronize()
         assert torch.equal(out, ref)
+        host = data.cpu().numpy()
+        for k in range(count):   # and the oracle's digest of each buffer (Sec. II-A)
+            assert bytes(out[k].cpu().numpy()) == oracle.frame_digest(host[k * nbytes:(k + 1) * nbytes], n=n), k
 
 
 def test_noalloc_rejects_requests_beyond_the_fixed_array():
