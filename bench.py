@@ -92,6 +92,9 @@ def parse():
     ap.add_argument("--inflight", type=int, default=None,
                     help="clips in flight on separate buffers: later clips' digest stage and LHCS_m overlap earlier "
                          "clips' keystreams (default: the tuned table's, else 5)")
+    ap.add_argument("--worker-smem", type=int, default=None,
+                    help="dynamic shared memory per worker CTA, a cap on worker CTAs per SM (default: the tuned "
+                         "table's, else 0: none)")
     ap.add_argument("--int-mix", type=int, default=None, choices=range(9), metavar="0..8",
                     help="worker warps per 8 (throughput layout) that step on the integer pipes beside the "
                          "binary64 ones (default: the tuned table's, else 0)")
@@ -365,7 +368,8 @@ def run_ours(args):
     pipe = autotune.pipeline_defaults() or {}
     split_source = {}
     for name, attr, default in (("layout", "layout", "throughput"), ("inflight", "inflight", 5),
-                                ("worker_window", "worker_window", 3), ("int_mix", "int_mix", 0)):
+                                ("worker_window", "worker_window", 3), ("int_mix", "int_mix", 0),
+                                ("worker_smem", "worker_smem", 0)):
         if getattr(args, attr) is None:
             setattr(args, attr, pipe.get(name, default))
             split_source[name] = "tuned table" if name in pipe else "built-in default"
@@ -388,6 +392,8 @@ def run_ours(args):
     dec.set_worker_cta(args.worker_cta)
     enc.set_int_mix(args.int_mix)
     dec.set_int_mix(args.int_mix)
+    enc.set_worker_smem(args.worker_smem)
+    dec.set_worker_smem(args.worker_smem)
     sid, rid = enc.open_stream(), dec.open_stream()
     stream = torch.cuda.current_stream()
 
@@ -734,7 +740,7 @@ def run_ours(args):
                                    "decrypt_frames on the receiver's (its chaotic stage waits for the digests, its "
                                    "inverse permutation for the ciphertext)",
                        "clips_in_flight": INF, "next_clip_gate": args.gate, "worker_window": WW,
-                       "int_mix_per8": args.int_mix,
+                       "int_mix_per8": args.int_mix, "worker_smem_bytes": args.worker_smem,
                        "worker_layout": args.layout, "worker_warps_per_cta": args.worker_cta,
                        "encrypt_route": args.encrypt_route,
                        "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),
@@ -1174,8 +1180,20 @@ def run_tune(args):
         print(f"pipeline {layout} inflight={inflight} window={window}: {v}", flush=True)
     best = max((k for k in results if results[k]), key=lambda k: results[k])
     layout, inflight, window = best.split("/")
+    # then the cap on worker CTAs per SM (dynamic shared memory per worker CTA) at the best split
+    smem_results = {}
+    for smem in (0, 24000, 28000, 32000, 38000):
+        cmd = [sys.executable, os.path.abspath(__file__), "--no-extras", "--no-cpu-baseline", "--no-probe",
+               "--steps", "15", "--repeats", "3", "--layout", layout, "--inflight", inflight,
+               "--worker-window", window, "--worker-smem", str(smem)]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+        smem_results[str(smem)] = json.loads(lines[-1])["value"] if r.returncode == 0 and lines else None
+        print(f"pipeline {best} worker_smem={smem}: {smem_results[str(smem)]}", flush=True)
+    best_smem = max((k for k in smem_results if smem_results[k]), key=lambda k: smem_results[k])
     pipeline = {"layout": layout, "inflight": int(inflight), "worker_window": int(window),
-                "frames_per_s": results[best], "candidates": results,
+                "worker_smem": int(best_smem), "worker_smem_candidates": smem_results,
+                "frames_per_s": max(results[best], smem_results[best_smem] or 0), "candidates": results,
                 "how": "bench.py headline, 15 steps, median of 3 timed regions per candidate, one process each"}
     table = {gpu: {"shapes": entries, "pipeline": pipeline}}
     with open(args.tune, "w") as f:

@@ -427,6 +427,12 @@ int cipher_set_worker_cta(fhd_cipher *c, uint32_t warps);
  * FHD_ERR_INVALID_ARG above 8. */
 int cipher_set_int_mix(fhd_cipher *c, uint32_t per8);
 
+/* Dynamic shared memory each CTA of the worker kernel requests (0, the
+ * default, to 232448 bytes).  The kernel does not use it: it caps how many
+ * worker CTAs an SM holds at once (a placement control).  Results are the
+ * same for every value; FHD_ERR_INVALID_ARG above 232448. */
+int cipher_set_worker_smem(fhd_cipher *c, uint32_t bytes);
+
 
 /* ---- Frame statistics of the paper's evaluation (Sec. III and IV-B) ----
  * Batched over `count` frames stored contiguously in device memory as

@@ -42,6 +42,7 @@ EXPORTS = (
     "decrypt_frames_persistent", "cipher_round_trip_persistent", "cipher_set_persistent_limits",
     "cipher_set_worker_cta", "cipher_persistent_trace", "fhd_row_band", "fhd_set_row_band", "fhd_build_flags",
     "fhd_bounds_report", "fhd_bounds_site_name", "fhd_bounds_selftest", "cipher_set_int_mix", "fhd_binary64_check",
+    "cipher_set_worker_smem",
 )
 FHD_BUILD_BOUNDS_CHECK = 1
 KERNEL_KINDS = ("sha", "master", "keystream", "encrypt", "decrypt")
@@ -154,6 +155,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "cipher_persistent_trace": (i32, [P, u32, P]),
             "fhd_build_flags": (u32, []),
             "cipher_set_int_mix": (i32, [P, u32]),
+            "cipher_set_worker_smem": (i32, [P, u32]),
             "fhd_binary64_check": (i32, [u64, u64, P, P]),
             "fhd_bounds_report": (i32, [ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.POINTER(u64),
                                         ctypes.POINTER(u64)]),
@@ -435,6 +437,10 @@ class Cipher:
     def set_worker_cta(self, warps: int):
         """Worker warps per CTA of the worker kernel (1, 2, 4 or 8); same results for every value."""
         _check(load().cipher_set_worker_cta(self._handle(), int(warps)), self._h)
+
+    def set_worker_smem(self, nbytes: int):
+        """Dynamic shared memory per worker CTA (a cap on worker CTAs per SM); same results for every value."""
+        _check(load().cipher_set_worker_smem(self._handle(), int(nbytes)), self._h)
 
     def set_int_mix(self, per8: int):
         """Eight-chain worker warps per 8 that step on the integer pipes (0..8); same results for every value."""

@@ -51,6 +51,7 @@ struct fhd_cipher {
     int layout = FHD_LAYOUT_LATENCY;
     uint32_t worker_cta = 1;   // worker warps per CTA of the keystream kernel
     uint32_t int_mix = 0;      // eight-chain worker warps per 8 on the integer pipes
+    uint32_t worker_smem = 0;  // dynamic shared memory per worker CTA (caps worker CTAs per SM)
     uint32_t digest_mode = FHD_DIGEST_XOR;
     uint32_t transport = FHD_TRANSPORT_PLAIN;
     cudaStream_t last_stream = nullptr;
@@ -610,7 +611,7 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
             for (uint32_t k = 0; k < hk.n_worker_waits; ++k)
                 if (hk.worker_waits[k] && (e = cudaStreamWaitEvent(sb, (cudaEvent_t)hk.worker_waits[k], 0)) != cudaSuccess)
                     return cuda_fail(c, e, "wait worker event");
-        if ((e = timed(c, FHD_K_KEYSTREAM, sb, [&] { return fhd::launch_keystream(b, sb, c->layout == FHD_LAYOUT_THROUGHPUT, c->worker_cta); })) != cudaSuccess)
+        if ((e = timed(c, FHD_K_KEYSTREAM, sb, [&] { return fhd::launch_keystream(b, sb, c->layout == FHD_LAYOUT_THROUGHPUT, c->worker_cta, c->worker_smem); })) != cudaSuccess)
             return cuda_fail(c, e, "keystream launch");
         if (keystream_done && base + m >= count && (e = cudaEventRecord(keystream_done, sb)) != cudaSuccess)
             return cuda_fail(c, e, "record keystream event");
@@ -1379,6 +1380,13 @@ int fhd_stats_local_entropy(const uint8_t *frames, uint32_t count, uint32_t heig
     cudaFreeAsync(ent, s);
     if (!status) cudaFreeAsync(st, s);
     if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("local entropy launch: ") + cudaGetErrorString(e));
+    return FHD_OK;
+}
+
+int cipher_set_worker_smem(fhd_cipher *c, uint32_t bytes) {
+    if (!c) return fail(nullptr, FHD_ERR_INVALID_ARG, "null cipher");
+    if (bytes > 232448) return fail(c, FHD_ERR_INVALID_ARG, "bytes must be at most 232448");
+    c->worker_smem = bytes;
     return FHD_OK;
 }
 

@@ -105,20 +105,28 @@ cudaError_t launch_master_raw(double *state5, const uint8_t *H, uint32_t n, doub
     return cudaGetLastError();
 }
 
-cudaError_t launch_keystream(const Batch &b, cudaStream_t s, bool dense, uint32_t warps_per_cta) {
+cudaError_t launch_keystream(const Batch &b, cudaStream_t s, bool dense, uint32_t warps_per_cta, uint32_t smem) {
     if (!b.count) return cudaSuccess;
     const uint32_t k = warps_per_cta ? warps_per_cta : 1;
+    if (smem > 48 * 1024) {
+        const void *fns[3] = {(const void *)keystream_kernel<4>, (const void *)keystream_kernel<4, true>,
+                              (const void *)keystream_kernel<kPairsPerWarp>};
+        for (const void *f : fns) {
+            cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+    }
     if (dense) {
         const uint32_t warps = b.count * ((b.n + 3) / 4);
         if (b.int_mix)
-            keystream_kernel<4, true><<<(warps + k - 1) / k, 32 * k, 0, s>>>(b);
+            keystream_kernel<4, true><<<(warps + k - 1) / k, 32 * k, smem, s>>>(b);
         else
-            keystream_kernel<4><<<(warps + k - 1) / k, 32 * k, 0, s>>>(b);
+            keystream_kernel<4><<<(warps + k - 1) / k, 32 * k, smem, s>>>(b);
         note_launch();
         return cudaGetLastError();
     }
     const uint32_t warps = b.count * ((b.n + kPairsPerWarp - 1) / kPairsPerWarp);
-    keystream_kernel<kPairsPerWarp><<<(warps + k - 1) / k, 32 * k, 0, s>>>(b);
+    keystream_kernel<kPairsPerWarp><<<(warps + k - 1) / k, 32 * k, smem, s>>>(b);
     note_launch();
     return cudaGetLastError();
 }

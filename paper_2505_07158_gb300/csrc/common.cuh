@@ -192,7 +192,10 @@ uint32_t noalloc_max_digests();
 cudaError_t launch_master(const Batch &b, StreamState *states, unsigned *status, cudaStream_t s);
 cudaError_t launch_master_raw(double *state5, const uint8_t *H, uint32_t n, double hstep, const uint32_t u[4],
                               double *IR, unsigned *status, cudaStream_t s);
-cudaError_t launch_keystream(const Batch &b, cudaStream_t s, bool dense = false, uint32_t warps_per_cta = 1);
+// smem: dynamic shared memory each worker CTA requests (unused by the kernel: it caps the worker CTAs an SM
+// holds at once).
+cudaError_t launch_keystream(const Batch &b, cudaStream_t s, bool dense = false, uint32_t warps_per_cta = 1,
+                             uint32_t smem = 0);
 cudaError_t launch_permute(const Batch &b, bool encrypt, cudaStream_t s);
 
 // Geometry of the permutation passes: strip width (column pass) and rows per

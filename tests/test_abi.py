@@ -58,6 +58,7 @@ def test_checked_build_exports_the_same_symbols():
 def test_int_mix_and_binary64_check_arguments(lib):
     import paper_2505_07158_gb300 as fhd
     assert lib.cipher_set_int_mix(None, 1) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.cipher_set_worker_smem(None, 0) == fhd.FHD_ERR_INVALID_ARG
     assert lib.fhd_binary64_check(16, 1, None, None) == fhd.FHD_ERR_INVALID_ARG
     out = (ctypes.c_uint64 * 4)()
     assert lib.fhd_binary64_check(0, 1, out, None) == fhd.FHD_ERR_INVALID_ARG

@@ -398,6 +398,30 @@ def test_integer_worker_mix_matches_oracle(mix):
         c.set_int_mix(9)
 
 
+@pytest.mark.parametrize("smem", [28000, 60000])
+def test_worker_smem_cap_matches_oracle(smem):
+    """A cap on worker CTAs per SM (dynamic shared memory each worker CTA requests, above the default
+    48 KB limit too) changes placement only: the oracle's bytes, both layouts."""
+    key = si.key(695)
+    frames = [to_dev(si.uniform_frame(40, 56, 3, seed=696)), to_dev(si.uniform_frame(24, 40, 1, seed=697))]
+    ref = oracle.Stream.from_key(key, n=12)
+    E_ref = [ref.encrypt(host(f)) for f in frames]
+    for layout in ("latency", "throughput"):
+        c = fhd.Cipher(key, n_workers=12)
+        c.set_layout(layout)
+        c.set_worker_smem(smem)
+        sid = c.open_stream()
+        E = [torch.empty_like(f) for f in frames]
+        H = torch.empty((len(frames), 32), dtype=torch.uint8, device=dev())
+        c.encrypt_frames([(sid, frames[k], E[k], H[k]) for k in range(len(frames))])
+        torch.cuda.synchronize()
+        for k in range(len(frames)):
+            assert np.array_equal(host(E[k]), E_ref[k][0]), (layout, k)
+            assert bytes(host(H[k])) == E_ref[k][1]
+    with pytest.raises(fhd.FhdError):
+        c.set_worker_smem(232449)
+
+
 def test_integer_worker_mix_full_1080p_frame():
     """One 1080p frame (n = 32: 8 worker warps of 8 chains, about 8,100 RK4 steps each) with every worker
     warp on the integer pipes, and with half of them: the oracle's ciphertext and digest."""
