@@ -425,8 +425,10 @@ def run_ours(args):
 
     slots = [Slot() for _ in range(max(1, args.inflight))]
     # The end-to-end copies run on two streams of their own, one per direction, so that a copy waiting for
-    # its slot to come free never sits in a compute stream: a clip's host-to-device copy waits for the
-    # slot's previous copy-out, its sender for that copy, and its copy-out for its receiver.
+    # its slot to come free never sits in a compute stream.  A clip's host-to-device copy waits only for the
+    # slot's previous encryption to have read its frames, so it runs a round trip ahead; the sender waits
+    # for that copy and for the slot's previous receiver and copy-out (the ciphertext, digest and output
+    # buffers are reused); the copy-out waits for the receiver.
     h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
     WW = args.worker_window if 0 < args.worker_window < len(slots) else 0
     KEEP = max(2, WW)
@@ -436,12 +438,12 @@ def run_ours(args):
         prev, prev2 = last[-1], last[-2]
         if e2e:
             if sl.used:
-                h2d.wait_event(sl.rx_done)
+                h2d.wait_event(sl.cipher_ready)
             with torch.cuda.stream(h2d):
                 sl.src_all.copy_(host, non_blocking=True)
             sl.h2d_done.record(h2d)
             sl.tx.wait_event(sl.h2d_done)
-        elif sl.used:
+        if sl.used:
             sl.tx.wait_event(sl.rx_done)
         # The digest stage (integer work) of this clip runs at once, during the previous clip's keystreams
         # (binary64 work).  This clip's LHCS_m waits for the chaining state and, by --gate, for:
