@@ -590,12 +590,13 @@ def run_ours(args):
         _, e2e_dev_ms, e2e_wall = timed_steps(args.steps, INF, e2e=True)
         e2e_reps.append((replicas.max_over_ranks(max(e2e_dev_ms, 1000 * e2e_wall) / args.steps, device=dev),
                          e2e_dev_ms / args.steps, 1000 * e2e_wall / args.steps))
+    e2e_values = [world * FRAMES / (r[0] / 1000.0) for r in e2e_reps]   # in the order the regions ran
     e2e_reps.sort()
     e2e_ms, e2e_dev, e2e_wall_ms = e2e_reps[len(e2e_reps) // 2]
     e2e_parts = {"device_ms_per_step": e2e_dev, "wall_ms_per_step": e2e_wall_ms,
                  "repeats": {"n": len(e2e_reps), "value": "median",
                              "min": world * FRAMES / (e2e_reps[-1][0] / 1000.0),
-                             "max": world * FRAMES / (e2e_reps[0][0] / 1000.0)}}
+                             "max": world * FRAMES / (e2e_reps[0][0] / 1000.0), "values": e2e_values}}
     e2e_ok = all(torch.equal(sl.host_out, host) for sl in slots if sl.e2e_used)
 
     # ---- plain path: one call per frame (the paper's per-frame loop), one CUDA stream
