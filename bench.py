@@ -752,6 +752,7 @@ def run_ours(args):
                        "frames_per_step": FRAMES * world, "l2": "inputs larger than L2 (~560 MB live per step)",
                        "parallelism": f"replicas x{world} (independent streams)",
                        "strip_width": tuned[f"{HGT}x{WID}x{CH}"]["P"], "row_band": tuned[f"{HGT}x{WID}x{CH}"]["RB"],
+                       "permute_cta_threads": list(fhd.fhd_cta_threads(HGT, WID, CH)),
                        "tile_source": tuned[f"{HGT}x{WID}x{CH}"]["source"], "work_split_source": split_source},
             "verified_round_trip": bool(verified) and bool(e2e_ok) and bool(alone_ok),
             "kernels_alone_ms": {k: v[0] / v[1] for k, v in alone.items() if v[1]},

@@ -362,6 +362,18 @@ int fhd_set_strip_width(uint32_t height, uint32_t width, uint32_t channels, uint
 uint32_t fhd_row_band(uint32_t height, uint32_t width, uint32_t channels);
 int fhd_set_row_band(uint32_t height, uint32_t width, uint32_t channels, uint32_t RB);
 
+
+/* Threads per CTA of the permutation passes for frames of one shape (autotuner
+ * hook): the column pass 256 or 512 (default 512, two CTAs per SM; 256 runs four
+ * per SM), the row pass 128 or 256 (default 256, six CTAs per SM; 128 runs
+ * twelve); 0 keeps the default.  A batch takes the choice of its largest frame's
+ * shape.  Results are the same for every value.  FHD_ERR_INVALID_ARG for another
+ * value or a bad shape, FHD_ERR_TOO_LARGE when the override table (64 shapes) is
+ * full.  fhd_cta_threads reports the choice in effect. */
+int fhd_set_cta_threads(uint32_t height, uint32_t width, uint32_t channels, uint32_t strip_threads,
+                        uint32_t row_threads);
+int fhd_cta_threads(uint32_t height, uint32_t width, uint32_t channels, uint32_t *strip_threads,
+                    uint32_t *row_threads);
 /* Route of the encryption's confusion + XOR (Sec. II-C), bit-identical either
  * way, process-wide.  FHD_ROUTE_TWO_PASS (default): a row pass (row
  * rotations, whole rows staged in shared memory) writes the row-rotated frame

@@ -42,7 +42,7 @@ EXPORTS = (
     "decrypt_frames_persistent", "cipher_round_trip_persistent", "cipher_set_persistent_limits",
     "cipher_set_worker_cta", "cipher_persistent_trace", "fhd_row_band", "fhd_set_row_band", "fhd_build_flags",
     "fhd_bounds_report", "fhd_bounds_site_name", "fhd_bounds_selftest", "cipher_set_int_mix", "fhd_binary64_check",
-    "cipher_set_worker_smem",
+    "cipher_set_worker_smem", "fhd_set_cta_threads", "fhd_cta_threads",
 )
 FHD_BUILD_BOUNDS_CHECK = 1
 KERNEL_KINDS = ("sha", "master", "keystream", "encrypt", "decrypt")
@@ -124,6 +124,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "fhd_set_strip_width": (i32, [u32, u32, u32, u32]),
             "fhd_row_band": (u32, [u32, u32, u32]),
             "fhd_set_row_band": (i32, [u32, u32, u32, u32]),
+            "fhd_set_cta_threads": (i32, [u32, u32, u32, u32, u32]),
+            "fhd_cta_threads": (i32, [u32, u32, u32, ctypes.POINTER(u32), ctypes.POINTER(u32)]),
             "fhd_version": (ctypes.c_char_p, []),
             "cipher_profile": (i32, [P, i32]),
             "cipher_profile_read": (i32, [P, P, P]),
@@ -645,6 +647,19 @@ def fhd_row_band(height: int, width: int, channels: int) -> int:
 
 def fhd_set_row_band(height: int, width: int, channels: int, RB: int):
     _check(load().fhd_set_row_band(height, width, channels, RB))
+
+
+def fhd_set_cta_threads(height: int, width: int, channels: int, strip_threads: int = 0, row_threads: int = 0):
+    """Threads per CTA of the permutation passes for one frame shape (column pass 256/512, row pass 128/256;
+    0 keeps the default)."""
+    _check(load().fhd_set_cta_threads(height, width, channels, strip_threads, row_threads))
+
+
+def fhd_cta_threads(height: int, width: int, channels: int) -> tuple:
+    """(column-pass, row-pass) threads per CTA in effect for a frame shape."""
+    a, b = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(load().fhd_cta_threads(height, width, channels, ctypes.byref(a), ctypes.byref(b)))
+    return int(a.value), int(b.value)
 
 
 def fhd_frame_scratch_bytes(n_workers: int, height: int, width: int, channels: int) -> int:

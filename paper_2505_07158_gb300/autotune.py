@@ -6,11 +6,13 @@ Per frame shape (height, width, channels) it chooses, by timing:
   memory.  Wide strips amortise the per-row work; narrow ones let two or more CTAs share an SM and hide
   memory latency.  Every power-of-two P whose strip fits is timed.
 * RB, the rows per CTA of the row pass (bands of whole rows staged in shared memory), at the chosen P.
+* ST and RT, the threads per CTA of the column pass (256 or 512) and of the row pass (128 or 256), at the
+  chosen P and RB.
 
 Each candidate is timed as the batched encrypt + decrypt permutation launches per frame of a batch of up to
 30 frames (CUDA events the library records on the launch stream, median of several runs); the fastest is
-installed with ``fhd_set_strip_width`` / ``fhd_set_row_band``.  Outputs are bit-identical for every
-choice (the GPU tests check this).
+installed with ``fhd_set_strip_width`` / ``fhd_set_row_band`` / ``fhd_set_cta_threads``.  Outputs are
+bit-identical for every choice (the GPU tests check this).
 
 The clip pipeline's work split (worker warp layout, clips in flight, worker window) is tuned by
 ``bench.py --tune``, which times the headline under each setting and stores the best here.
@@ -78,9 +80,10 @@ def _shapes_of(table: dict, gpu: str) -> dict:
     return table.get(gpu, {}).get("shapes", {})
 
 
-def time_shape(h: int, w: int, C: int, P: int, RB: int = 0, reps: int = 3, frames: int = 8) -> float:
-    """Milliseconds per frame of the batched encrypt + decrypt permutation launches at strip width P and
-    row band RB (0: the built-in band).
+def time_shape(h: int, w: int, C: int, P: int, RB: int = 0, reps: int = 3, frames: int = 8, ST: int = 0,
+               RT: int = 0) -> float:
+    """Milliseconds per frame of the batched encrypt + decrypt permutation launches at strip width P, row
+    band RB (0: the built-in band) and threads per CTA ST, RT of the two passes (0: the defaults).
 
     The frames go through encrypt_frames / decrypt_frames exactly as in production; only the permutation
     launches are timed (CUDA events the library records on the launch stream).  A large worker count keeps
@@ -98,6 +101,7 @@ def time_shape(h: int, w: int, C: int, P: int, RB: int = 0, reps: int = 3, frame
     Hd = [torch.empty(32, dtype=torch.uint8, device=dev) for _ in F]
     _lib.fhd_set_strip_width(h, w, C, P)
     _lib.fhd_set_row_band(h, w, C, RB)
+    _lib.fhd_set_cta_threads(h, w, C, ST, RT)
     try:
         def once():
             enc.encrypt_frames([(sid, F[k], E[k], Hd[k]) for k in range(frames)])
@@ -112,11 +116,13 @@ def time_shape(h: int, w: int, C: int, P: int, RB: int = 0, reps: int = 3, frame
             ts.append(t / frames)
         torch.cuda.synchronize()
         if not all(torch.equal(R[k], F[k]) for k in range(frames)):
-            raise RuntimeError(f"strip width {P}, row band {RB} failed the round trip for {h}x{w}x{C}")
+            raise RuntimeError(f"strip width {P}, row band {RB}, CTA threads {ST}/{RT} failed the round trip "
+                               f"for {h}x{w}x{C}")
         return statistics.median(ts)
     finally:
         _lib.fhd_set_strip_width(h, w, C, 0)
         _lib.fhd_set_row_band(h, w, C, 0)
+        _lib.fhd_set_cta_threads(h, w, C, 0, 0)
         enc.close()
         dec.close()
 
@@ -128,26 +134,34 @@ def batch_frames(h: int, w: int, C: int) -> int:
     return max(4, min(30, int(1.5e9 // (h * w * C))))
 
 
+CTA_CANDIDATES = ((512, 256), (256, 256), (512, 128))
+
+
 def tune_shape(h: int, w: int, C: int, reps: int = 7) -> dict:
-    """Time every strip width, then every row band at the best width: {"P", "RB", "ms", "rb_ms"}."""
+    """Time every strip width, then every row band at the best width, then the CTA shapes of the two passes:
+    {"P", "RB", "ST", "RT", "ms", "rb_ms", "cta_ms"}."""
     n = batch_frames(h, w, C)
     times = {P: time_shape(h, w, C, P, 0, reps, frames=n) for P in candidates(h, w, C)}
     best = min(times, key=times.get)
     rb_times = {RB: time_shape(h, w, C, best, RB, reps, frames=n) for RB in row_band_candidates(h, w, C)}
     rb = min(rb_times, key=rb_times.get) if rb_times else 0
-    return {"P": best, "RB": rb, "ms": {str(p): t for p, t in times.items()},
-            "rb_ms": {str(r): t for r, t in rb_times.items()}}
+    cta_times = {(st, rt): time_shape(h, w, C, best, rb, reps, frames=n, ST=st, RT=rt) for st, rt in CTA_CANDIDATES}
+    st, rt = min(cta_times, key=cta_times.get)
+    return {"P": best, "RB": rb, "ST": st, "RT": rt, "ms": {str(p): t for p, t in times.items()},
+            "rb_ms": {str(r): t for r, t in rb_times.items()},
+            "cta_ms": {f"{a}/{b}": t for (a, b), t in cta_times.items()}}
 
 
 def _install(h, w, C, entry):
     _lib.fhd_set_strip_width(h, w, C, int(entry.get("P", 0)))
     _lib.fhd_set_row_band(h, w, C, int(entry.get("RB", 0)))
+    _lib.fhd_set_cta_threads(h, w, C, int(entry.get("ST", 0)), int(entry.get("RT", 0)))
 
 
 def tune(shapes, cache_path: str = DEFAULT_CACHE, force: bool = False, committed: str = COMMITTED) -> dict:
     """Install the tile shapes of every shape: from the committed table for this GPU, else this machine's
     cache, else by timing (recorded in the cache).  force=True times every shape again.  Returns
-    {shape key: {"P", "RB", "source"}}."""
+    {shape key: {"P", "RB", "ST", "RT", "source"}} (0: the library's default)."""
     gpu = _gpu_name()
     fixed = {} if force else _shapes_of(load_cache(committed), gpu)
     cache = load_cache(cache_path)
@@ -158,14 +172,15 @@ def tune(shapes, cache_path: str = DEFAULT_CACHE, force: bool = False, committed
         k = _key(h, w, C)
         if k in fixed:
             entry, src = fixed[k], "committed"
-        elif not force and k in table and "RB" in table[k]:
+        elif not force and k in table and "ST" in table[k]:
             entry, src = table[k], "cache"
         else:
             entry, src = tune_shape(h, w, C), "timed"
             table[k] = entry
             changed = True
         _install(h, w, C, entry)
-        out[k] = {"P": int(entry["P"]), "RB": int(entry.get("RB", 0)), "source": src}
+        out[k] = {"P": int(entry["P"]), "RB": int(entry.get("RB", 0)), "ST": int(entry.get("ST", 0)),
+                  "RT": int(entry.get("RT", 0)), "source": src}
     if changed:
         save_cache(cache, cache_path)
     return out

@@ -1602,6 +1602,23 @@ uint32_t fhd_row_band(uint32_t height, uint32_t width, uint32_t channels) {
     return fhd::row_band(height, width, channels);
 }
 
+int fhd_set_cta_threads(uint32_t height, uint32_t width, uint32_t channels, uint32_t strip_threads,
+                        uint32_t row_threads) {
+    if (!height || !width || !channels || channels > 4 || (strip_threads && strip_threads != 256 && strip_threads != 512) ||
+        (row_threads && row_threads != 128 && row_threads != 256))
+        return fail(nullptr, FHD_ERR_INVALID_ARG, "bad CTA threads override");
+    return fhd::set_cta_threads_override(height, width, channels, strip_threads, row_threads) == 0
+               ? FHD_OK
+               : fail(nullptr, FHD_ERR_TOO_LARGE, "override table full");
+}
+
+int fhd_cta_threads(uint32_t height, uint32_t width, uint32_t channels, uint32_t *strip_threads, uint32_t *row_threads) {
+    if (!strip_threads || !row_threads) return fail(nullptr, FHD_ERR_INVALID_ARG, "null argument");
+    if (!height || !width || !channels || channels > 4) return fail(nullptr, FHD_ERR_INVALID_ARG, "bad frame shape");
+    fhd::cta_threads(height, width, channels, strip_threads, row_threads);
+    return FHD_OK;
+}
+
 int fhd_set_row_band(uint32_t height, uint32_t width, uint32_t channels, uint32_t RB) {
     if (!height || !width || !channels || channels > 4 || RB > 64)
         return fail(nullptr, FHD_ERR_INVALID_ARG, "bad row band override");

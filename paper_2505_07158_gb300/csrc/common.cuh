@@ -216,6 +216,9 @@ cudaError_t launch_fp64_probe(uint32_t warps_per_subpartition, uint32_t iters, d
 cudaError_t launch_binary64_check(uint64_t pairs, uint64_t seed, unsigned long long *counts, cudaStream_t s);
 int set_strip_override(uint32_t h, uint32_t w, uint32_t C, uint32_t P);
 int set_row_band_override(uint32_t h, uint32_t w, uint32_t C, uint32_t RB);
+// Threads per CTA of the column pass (256 or 512) and the row pass (128 or 256) for a frame shape; 0: default.
+int set_cta_threads_override(uint32_t h, uint32_t w, uint32_t C, uint32_t st, uint32_t rt);
+void cta_threads(uint32_t h, uint32_t w, uint32_t C, uint32_t *st, uint32_t *rt);
 int set_encrypt_route(int route);   // FHD_ROUTE_TWO_PASS or FHD_ROUTE_SINGLE_PASS; -1 on a bad value
 
 }  // namespace fhd

@@ -30,11 +30,16 @@
 namespace fhd {
 namespace {
 
-// CTA shapes, measured on the 30-frame 1080p clip (encrypt / decrypt permutation per call): column pass 512
-// threads, two CTAs per SM (0.269 / 0.259 ms; 256 threads at four per SM: 0.326 / 0.368); row pass 256
-// threads held to six CTAs per SM, 40 registers (0.265 / 0.257 ms; eight per SM spill at 32 registers).
+// CTA shapes.  Column pass: 512 threads at two CTAs per SM (the default) or 256 at four; row pass: 256
+// threads held to six CTAs per SM (40 registers) or 128 at twelve.  The autotuner picks per frame shape
+// (fhd_set_cta_threads); on the 30-frame 1080p clip the defaults measured 0.269 / 0.259 ms per encrypt /
+// decrypt permutation call, 256-thread column-pass CTAs 0.326 / 0.368.
 constexpr int kStripThreads = 512;
 constexpr int kRowThreads = 256;
+template <int kT>
+constexpr int strip_ctas_per_sm() { return kT == 512 ? 2 : 4; }
+template <int kT>
+constexpr int row_ctas_per_sm() { return kT == 256 ? 6 : 12; }
 template <bool kRow>
 __device__ __forceinline__ uint32_t find_frame(const Batch &b, uint32_t cta) {
     uint32_t lo = 0, hi = b.count;
@@ -45,16 +50,18 @@ __device__ __forceinline__ uint32_t find_frame(const Batch &b, uint32_t cta) {
     return lo;
 }
 
-template <bool kEnc>
-__global__ void __launch_bounds__(kStripThreads, 2) strip_kernel(const __grid_constant__ Batch b, uint32_t cta_base) {
+template <bool kEnc, int kT = kStripThreads>
+__global__ void __launch_bounds__(kT, strip_ctas_per_sm<kT>()) strip_kernel(const __grid_constant__ Batch b,
+                                                                            uint32_t cta_base) {
     extern __shared__ __align__(16) uint8_t smem[];
     const uint32_t cta = cta_base + blockIdx.x;
     const FrameDesc &fd = b.f[find_frame<false>(b, cta)];
     strip_pass<kEnc>(fd, cta - fd.cta0, smem, threadIdx.x, blockDim.x, [] { __syncthreads(); });
 }
 
-template <bool kEnc>
-__global__ void __launch_bounds__(kRowThreads, 6) row_kernel(const __grid_constant__ Batch b, uint32_t cta_base) {
+template <bool kEnc, int kT = kRowThreads>
+__global__ void __launch_bounds__(kT, row_ctas_per_sm<kT>()) row_kernel(const __grid_constant__ Batch b,
+                                                                        uint32_t cta_base) {
     extern __shared__ __align__(16) uint8_t smem[];
     const uint32_t cta = cta_base + blockIdx.x;
     const FrameDesc &fd = b.f[find_frame<true>(b, cta)];
@@ -305,6 +312,8 @@ uint32_t permute_strips(uint32_t w, uint32_t P) { return (w + P - 1) / P; }
 static uint32_t g_override_key[64][3];
 static uint32_t g_override_P[64];
 static uint32_t g_override_RB[64];
+static uint32_t g_override_ST[64];   // column-pass threads per CTA (0: kStripThreads)
+static uint32_t g_override_RT[64];   // row-pass threads per CTA (0: kRowThreads)
 static int g_overrides = 0;
 
 static int override_slot(uint32_t h, uint32_t w, uint32_t C) {
@@ -315,7 +324,26 @@ static int override_slot(uint32_t h, uint32_t w, uint32_t C) {
     g_override_key[g_overrides][1] = w;
     g_override_key[g_overrides][2] = C;
     g_override_P[g_overrides] = g_override_RB[g_overrides] = 0;
+    g_override_ST[g_overrides] = g_override_RT[g_overrides] = 0;
     return g_overrides++;
+}
+
+int set_cta_threads_override(uint32_t h, uint32_t w, uint32_t C, uint32_t st, uint32_t rt) {
+    const int k = override_slot(h, w, C);
+    if (k < 0) return -1;
+    g_override_ST[k] = st;
+    g_override_RT[k] = rt;
+    return 0;
+}
+
+void cta_threads(uint32_t h, uint32_t w, uint32_t C, uint32_t *st, uint32_t *rt) {
+    *st = kStripThreads;
+    *rt = kRowThreads;
+    for (int k = 0; k < g_overrides; ++k)
+        if (g_override_key[k][0] == h && g_override_key[k][1] == w && g_override_key[k][2] == C) {
+            if (g_override_ST[k]) *st = g_override_ST[k];
+            if (g_override_RT[k]) *rt = g_override_RT[k];
+        }
 }
 
 int set_strip_override(uint32_t h, uint32_t w, uint32_t C, uint32_t P) {
@@ -360,8 +388,10 @@ uint32_t strip_width(uint32_t h, uint32_t w, uint32_t C) {
 }
 
 cudaError_t permute_prepare() {
-    const void *fns[5] = {(const void *)strip_kernel<true>, (const void *)strip_kernel<false>,
+    const void *fns[9] = {(const void *)strip_kernel<true>, (const void *)strip_kernel<false>,
+                          (const void *)strip_kernel<true, 256>, (const void *)strip_kernel<false, 256>,
                           (const void *)row_kernel<true>, (const void *)row_kernel<false>,
+                          (const void *)row_kernel<true, 128>, (const void *)row_kernel<false, 128>,
                           (const void *)gather_encrypt_kernel};
     for (const void *f : fns) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
@@ -425,20 +455,40 @@ cudaError_t launch_permute(const Batch &b, bool encrypt, cudaStream_t s) {
             return cudaGetLastError();
         }
     }
+    // CTA shapes of the batch: those of its largest frame's shape
+    uint32_t big = 0;
+    for (uint32_t k = 1; k < b.count; ++k)
+        if (b.f[k].N > b.f[big].N) big = k;
+    uint32_t st, rt;
+    cta_threads(b.f[big].h, b.f[big].w, b.f[big].C, &st, &rt);
+    auto rows = [&](bool enc) {
+        if (rt == 128) {
+            if (enc) row_kernel<true, 128><<<b.row_ctas, 128, rsm, s>>>(b, 0);
+            else row_kernel<false, 128><<<b.row_ctas, 128, rsm, s>>>(b, 0);
+        } else {
+            if (enc) row_kernel<true><<<b.row_ctas, kRowThreads, rsm, s>>>(b, 0);
+            else row_kernel<false><<<b.row_ctas, kRowThreads, rsm, s>>>(b, 0);
+        }
+        note_launch();
+        return cudaGetLastError();
+    };
+    auto strips = [&](bool enc) {
+        if (st == 256) {
+            if (enc) strip_kernel<true, 256><<<b.perm_ctas, 256, ssm, s>>>(b, 0);
+            else strip_kernel<false, 256><<<b.perm_ctas, 256, ssm, s>>>(b, 0);
+        } else {
+            if (enc) strip_kernel<true><<<b.perm_ctas, kStripThreads, ssm, s>>>(b, 0);
+            else strip_kernel<false><<<b.perm_ctas, kStripThreads, ssm, s>>>(b, 0);
+        }
+        note_launch();
+        return cudaGetLastError();
+    };
     if (encrypt) {
-        row_kernel<true><<<b.row_ctas, kRowThreads, rsm, s>>>(b, 0);
-        note_launch();
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        strip_kernel<true><<<b.perm_ctas, kStripThreads, ssm, s>>>(b, 0);
-        note_launch();
-    } else {
-        strip_kernel<false><<<b.perm_ctas, kStripThreads, ssm, s>>>(b, 0);
-        note_launch();
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        row_kernel<false><<<b.row_ctas, kRowThreads, rsm, s>>>(b, 0);
-        note_launch();
+        if ((e = rows(true)) != cudaSuccess) return e;
+        return strips(true);
     }
-    return cudaGetLastError();
+    if ((e = strips(false)) != cudaSuccess) return e;
+    return rows(false);
 }
 
 }  // namespace fhd

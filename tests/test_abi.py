@@ -55,6 +55,18 @@ def test_checked_build_exports_the_same_symbols():
         assert fhd.fhd_build_flags() == 0
 
 
+def test_cta_threads_overrides_on_the_host(lib):
+    import paper_2505_07158_gb300 as fhd
+    assert fhd.fhd_cta_threads(1080, 1920, 3) == (512, 256)
+    assert lib.fhd_set_cta_threads(1080, 1920, 3, 300, 0) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.fhd_set_cta_threads(1080, 1920, 3, 0, 64) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.fhd_set_cta_threads(0, 1920, 3, 256, 128) == fhd.FHD_ERR_INVALID_ARG
+    fhd.fhd_set_cta_threads(37, 41, 3, 256, 0)
+    assert fhd.fhd_cta_threads(37, 41, 3) == (256, 256)
+    fhd.fhd_set_cta_threads(37, 41, 3, 0, 0)
+    assert fhd.fhd_cta_threads(37, 41, 3) == (512, 256)
+
+
 def test_int_mix_and_binary64_check_arguments(lib):
     import paper_2505_07158_gb300 as fhd
     assert lib.cipher_set_int_mix(None, 1) == fhd.FHD_ERR_INVALID_ARG

@@ -364,3 +364,21 @@ def test_permute_row_band_overrides(RB):
             assert np.array_equal(host(Pd), F), (h, w, C)
         finally:
             fhd.fhd_set_row_band(h, w, C, 0)
+
+
+@pytest.mark.parametrize("st,rt", [(256, 128), (256, 256), (512, 128)])
+def test_permute_cta_thread_overrides(st, rt):
+    """Every CTA shape the autotuner may install for the two passes gives the oracle's bytes both ways: the
+    column-word route (h % 4 == 0), the byte-scatter route (h % 4 != 0) and the byte-wise row route
+    (w % 4 != 0), full and tail strips, at 1080p too."""
+    for h, w, C in [(44, 64, 3), (45, 77, 3), (20, 36, 4), (48, 100, 1), (1080, 1920, 3)]:
+        fhd.fhd_set_cta_threads(h, w, C, st, rt)
+        try:
+            assert fhd.fhd_cta_threads(h, w, C) == (st, rt)
+            F, D, B = _rand(h, w, C, seed=st + rt + w)
+            E = fhd.fhd_permute_encrypt(to_dev(F), d16(D), to_dev(B))
+            assert np.array_equal(host(E), oracle.permute_encrypt(F, D, B)), (h, w, C)
+            Pd = fhd.fhd_permute_decrypt(E, d16(D), to_dev(B))
+            assert np.array_equal(host(Pd), F), (h, w, C)
+        finally:
+            fhd.fhd_set_cta_threads(h, w, C, 0, 0)
