@@ -61,7 +61,7 @@ TRAFFIC_PER_FRAME = {"keystream": (29952 + 0) / 4,
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=120)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -79,6 +79,8 @@ def parse():
                     help="comma list of the other workloads to run: " + ",".join(EXTRAS))
     ap.add_argument("--encrypt-route", default="two_pass", choices=["two_pass", "single_pass"],
                     help="route of the encryption's confusion + XOR in the headline")
+    ap.add_argument("--keystream-route", default="trajectory", choices=["trajectory", "pairs"],
+                    help="route of the keystream: one LHCS_m trajectory per frame (default) or the n worker pairs")
     ap.add_argument("--gate", default="chain", choices=["permute", "keystream", "chain", "window"],
                     help="what the next clip's LHCS_m waits for besides the chaining state (see round_trip)")
     ap.add_argument("--partition", action="store_true",
@@ -229,6 +231,17 @@ def worker_steps(h, w, C, n):
     return 2 * total
 
 
+def traj_steps(h, w, C, n):
+    """RK4 steps of one frame's trajectory in the one-trajectory keystream route: records R (the bound the
+    library sizes them by) need the states up to s_{R+2}, and s_1 .. s_2n are LHCS_m's iterates."""
+    LD, LB = C * (h + w), h * w * C
+    R = (48 * (n - 1) + 2 * -(-LD // n) + -(-LB // n) + 23) // 24
+    return R + 2 - 2 * n
+
+
+RK4_FP64_INSTR = 27     # binary64 instructions one warp issues per RK4 step of its chains (six-chain layout)
+
+
 def sha_blocks(N, n):
     blocks = 0
     for i in range(n):
@@ -376,6 +389,7 @@ def run_ours(args):
         else:
             split_source[name] = "flag"
     fhd.fhd_set_encrypt_route(args.encrypt_route)
+    fhd.fhd_set_keystream_route(args.keystream_route)
     clip = si.clip(FRAMES, HGT, WID, CH, seed=rank)
     host = torch.from_numpy(clip).pin_memory()
     key = si.key(rank)
@@ -700,9 +714,39 @@ def run_ours(args):
                 "timing": "one launch with nothing else running (in the timed run it overlaps the keystreams)",
                 "ms_per_launch_alone": ms, "ms_per_launch_in_timed_run": kern[k]["avg_launch_ms"]}
 
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    def traj_roof(k):
+        # One chain per frame, strictly sequential: the launch lasts its longest chain, whose warp issues 27
+        # binary64 instructions per step back to back on one sub-partition's binary64 pipe.  achieved = the
+        # binary64 lane-operations that warp issues per second (steps x 27 x 32 / launch time alone), peak =
+        # one sub-partition's share of the measured binary64 peak: frac is how close the chain runs to the
+        # pipe's own rate.  The whole GPU's binary64 fraction (algorithmic ops of all launches over the union
+        # of their spans) is reported beside it.
+        steps = traj_steps(HGT, WID, CH, N_WORKERS)
+        ms = alone[k][0] / alone[k][1]
+        sp_peak = fp64_peak * 1e12 / (sms * 4) / 1e9
+        ach = steps * RK4_FP64_INSTR * 32 / (ms / 1000.0) / 1e9
+        n_l = kern[k]["launches_per_step"] * args.steps
+        gpu_ach = n_l * steps * per_step_frames * RK4_FP64_OPS / (busy_ms(k) / 1000.0) / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": sp_peak, "unit": "Gop/s (binary64 lane-ops, one sub-partition)",
+                "frac": ach / sp_peak, "traffic": None,
+                "peak_source": fp64_source + f", divided by {sms} SMs x 4 sub-partitions",
+                "per_launch_units": f"{per_step_frames} frames x one trajectory of {steps} RK4 steps "
+                                    f"({RK4_FP64_INSTR} binary64 warp instructions each) + the D/B emission",
+                "timing": "one launch (trajectory + emission) with nothing else running",
+                "ms_per_launch_alone": ms, "ms_per_launch_in_timed_run": kern[k]["avg_launch_ms"],
+                "step_cycles_alone": (ms / 1000.0) * (clocks_mhz or 0) * 1e6 / steps if clocks_mhz else None,
+                "gpu_binary64_frac": gpu_ach / fp64_peak,
+                "gpu_binary64_note": f"{steps} steps x {RK4_FP64_OPS} ops per frame, all launches over the union "
+                                     "of their spans, against the whole GPU's measured peak: the route needs "
+                                     "one chain per frame, so the pipes stay mostly idle"}
+
     roofs = {}
+    clocks_mhz = clk.summary().get("sm_mhz")
     if "keystream" in kern:
-        roofs["keystream"] = fp64_roof("keystream", chain_steps)
+        roofs["keystream"] = (traj_roof("keystream") if args.keystream_route == "trajectory"
+                              else fp64_roof("keystream", chain_steps))
     if "master" in kern:
         roofs["master"] = fp64_roof("master", master_steps)
         roofs["master"]["achieved_per_launch_alone"] = (master_steps * RK4_FP64_OPS /
@@ -745,7 +789,7 @@ def run_ours(args):
                        "clips_in_flight": INF, "next_clip_gate": args.gate, "worker_window": WW,
                        "int_mix_per8": args.int_mix, "worker_smem_bytes": args.worker_smem,
                        "worker_layout": args.layout, "worker_warps_per_cta": args.worker_cta,
-                       "encrypt_route": args.encrypt_route,
+                       "encrypt_route": args.encrypt_route, "keystream_route": args.keystream_route,
                        "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),
                        "sm_partition": {"lhcs_m_sms": enc.partition()[0], "other_sms": enc.partition()[1],
                                         "digest_stage_own_sms": bool(args.digest_partition and not args.no_partition)},

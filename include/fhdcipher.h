@@ -342,6 +342,17 @@ int fhd_master(double *state, const uint8_t *H, const fhd_params *params, double
 int fhd_keystream(const double *IR, double gamma, const fhd_params *params, uint32_t height,
                   uint32_t width, uint32_t channels, uint16_t *D, uint8_t *B, void *stream);
 
+/* The same D and B by the one-trajectory route (fhd_set_keystream_route), for
+ * an IR that holds LHCS_m's 2n iterates as fhd_master writes them (row t the
+ * state after step t+1 of one trajectory of Eq. (1) with this gamma and step):
+ * the route reads IR[0] .. IR[2n-1] as that trajectory and continues it from
+ * IR[2n-1].  For such an IR the result equals fhd_keystream's; for iterates
+ * of no single trajectory it does not (use fhd_keystream).  Takes
+ * 24 ceil((48 (n-1) + 2 ceil(C (h+w)/n) + ceil(h w C/n)) / 24) + 64 bytes of
+ * scratch from cudaMallocAsync on `stream` for the call. */
+int fhd_keystream_trajectory(const double *IR, double gamma, const fhd_params *params, uint32_t height,
+                             uint32_t width, uint32_t channels, uint16_t *D, uint8_t *B, void *stream);
+
 /* Sec. II-C, Algos 3-7 fused: dst = XOR(B, vertical shift(horizontal bit
  * shift(src))) with the distances in D, one frame, device pointers. */
 int fhd_permute_encrypt(const uint8_t *src, uint8_t *dst, uint32_t height, uint32_t width,
@@ -388,6 +399,26 @@ int fhd_cta_threads(uint32_t height, uint32_t width, uint32_t channels, uint32_t
  * Returns FHD_ERR_INVALID_ARG for another value. */
 enum { FHD_ROUTE_TWO_PASS = 0, FHD_ROUTE_SINGLE_PASS = 1 };
 int fhd_set_encrypt_route(int route);
+
+/* Route of the keystream (Sec. II-B, Algorithm 2: D and B from the iterates
+ * IR), bit-identical either way, process-wide; taken by encrypt_frames and
+ * decrypt_frames and their variants, where IR is always LHCS_m's (the
+ * persistent launches always run the worker pairs; fhd_keystream, which takes
+ * any IR, too).
+ * FHD_KS_ROUTE_TRAJECTORY (default): worker pair i starts from IR[2i] and
+ * IR[2i+1] and iterates the same map with the same step as LHCS_m, so both of
+ * its systems are the frame's LHCS_m trajectory continued, and worker i's
+ * byte stream is worker 0's from 48 i bytes on.  The route computes that one
+ * trajectory per frame -- about N/(24 n) + 2n states, each once, instead of
+ * 2n chains of about N/(24 n) steps -- into 24-byte records (the XOR of the
+ * stream bytes of consecutive states), then copies each worker's window of
+ * the records into its slices of D and B.  Its time per frame is the
+ * trajectory's sequential latency, the same as one worker chain's.
+ * FHD_KS_ROUTE_PAIRS: the n worker pairs as 2n chains (the warp layout of
+ * cipher_set_layout).  Returns the previous route, or FHD_ERR_INVALID_ARG for
+ * another value. */
+enum { FHD_KS_ROUTE_PAIRS = 0, FHD_KS_ROUTE_TRAJECTORY = 1 };
+int fhd_set_keystream_route(int route);
 
 /* ---- Instrumentation (not part of the cipher). ---- */
 

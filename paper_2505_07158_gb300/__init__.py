@@ -11,6 +11,6 @@ from ._lib import (  # noqa: F401
     FHD_ERR_TOO_LARGE, FHD_OK, FHD_STATE_BYTES, Cipher, FhdError, fhd_frame_digest, fhd_keystream, fhd_master,
     fhd_frame_scratch_bytes, fhd_launch_count, fhd_permute_decrypt, fhd_permute_encrypt, KERNEL_KINDS, fhd_set_strip_width, fhd_strip_width, fhd_row_band, fhd_set_row_band, fhd_version, library_path,
     load, fhd_stats_histogram, fhd_stats_npcr_uaci, fhd_stats_correlation, fhd_stats_local_entropy, fhd_fp64_probe,
-    fhd_set_encrypt_route, fhd_build_flags, fhd_bounds_report, fhd_bounds_site_name, fhd_bounds_selftest,
+    fhd_set_encrypt_route, fhd_set_keystream_route, fhd_build_flags, fhd_bounds_report, fhd_bounds_site_name, fhd_bounds_selftest,
     FHD_BUILD_BOUNDS_CHECK, checked_requested, fhd_binary64_check, fhd_set_cta_threads, fhd_cta_threads,
 )

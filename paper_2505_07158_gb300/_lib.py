@@ -42,7 +42,8 @@ EXPORTS = (
     "decrypt_frames_persistent", "cipher_round_trip_persistent", "cipher_set_persistent_limits",
     "cipher_set_worker_cta", "cipher_persistent_trace", "fhd_row_band", "fhd_set_row_band", "fhd_build_flags",
     "fhd_bounds_report", "fhd_bounds_site_name", "fhd_bounds_selftest", "cipher_set_int_mix", "fhd_binary64_check",
-    "cipher_set_worker_smem", "fhd_set_cta_threads", "fhd_cta_threads",
+    "cipher_set_worker_smem", "fhd_set_cta_threads", "fhd_cta_threads", "fhd_set_keystream_route",
+    "fhd_keystream_trajectory",
 )
 FHD_BUILD_BOUNDS_CHECK = 1
 KERNEL_KINDS = ("sha", "master", "keystream", "encrypt", "decrypt")
@@ -118,6 +119,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "fhd_frame_digest_tree": (i32, [P, u64, u32, u32, P, P]),
             "fhd_master": (i32, [P, P, P, P, P]),
             "fhd_keystream": (i32, [P, dbl, P, u32, u32, u32, P, P, P]),
+            "fhd_keystream_trajectory": (i32, [P, dbl, P, u32, u32, u32, P, P, P]),
             "fhd_permute_encrypt": (i32, [P, P, u32, u32, u32, P, P, P]),
             "fhd_permute_decrypt": (i32, [P, P, u32, u32, u32, P, P, P]),
             "fhd_strip_width": (u32, [u32, u32, u32]),
@@ -149,6 +151,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "fhd_frame_scratch_bytes": (u64, [u32, u32, u32, u32]),
             "fhd_fp64_probe": (i32, [u32, u32, P, ctypes.POINTER(u64), P]),
             "fhd_set_encrypt_route": (i32, [i32]),
+            "fhd_set_keystream_route": (i32, [i32]),
             "encrypt_frames_persistent": (i32, [P, u32, P, P]),
             "decrypt_frames_persistent": (i32, [P, u32, P, P]),
             "cipher_round_trip_persistent": (i32, [P, P, u32, P, P, P]),
@@ -565,6 +568,19 @@ def fhd_set_encrypt_route(route: str = "two_pass"):
     _check(load().fhd_set_encrypt_route(ROUTES[route]))
 
 
+KS_ROUTES = {"pairs": 0, "trajectory": 1}
+
+
+def fhd_set_keystream_route(route: str = "trajectory") -> str:
+    """Keystream route (bit-identical either way): "trajectory" (the default; one LHCS_m trajectory per frame,
+    each worker's window of it copied into D and B) or "pairs" (the n worker pairs as 2n chains).  Returns the
+    previous route."""
+    old = load().fhd_set_keystream_route(KS_ROUTES[route])
+    if old < 0:
+        _check(old)
+    return {v: k for k, v in KS_ROUTES.items()}[old]
+
+
 def fhd_fp64_probe(warps_per_subpartition: int, iters: int, sink: torch.Tensor, stream=None) -> int:
     """Launch the binary64 pipe probe; returns the binary64 lane-operations it executes."""
     if not sink.is_cuda or sink.dtype != torch.float64:
@@ -603,15 +619,22 @@ def fhd_master(state5: torch.Tensor, H: torch.Tensor, n_workers=32, rk4_h=0.01, 
 
 
 def fhd_keystream(IR: torch.Tensor, gamma: float, height: int, width: int, channels: int, n_workers=32,
-                  rk4_h=0.01, stream=None):
-    """Worker pairs -> (D int16[C*(h+w)] holding uint16 bits, B uint8[h*w*C])."""
+                  rk4_h=0.01, stream=None, trajectory=False, B_out=None):
+    """Worker pairs -> (D int16[C*(h+w)] holding uint16 bits, B uint8[h*w*C]).  trajectory=True takes the
+    one-trajectory route (fhd_keystream_trajectory: IR must be LHCS_m's iterates, as fhd_master writes them).
+    B_out: a uint8 device buffer of h*w*C bytes to write B into (any alignment)."""
     assert IR.is_cuda and IR.dtype == torch.float64 and IR.is_contiguous()
     D = torch.empty(channels * (height + width), dtype=torch.int16, device=IR.device)
-    B = torch.empty(height * width * channels, dtype=torch.uint8, device=IR.device)
+    if B_out is None:
+        B = torch.empty(height * width * channels, dtype=torch.uint8, device=IR.device)
+    else:
+        assert B_out.is_cuda and B_out.dtype == torch.uint8 and B_out.is_contiguous()
+        assert B_out.numel() == height * width * channels
+        B = B_out
     p = _params(n_workers, rk4_h)
-    _check(load().fhd_keystream(ctypes.c_void_p(IR.data_ptr()), float(gamma), ctypes.byref(p), height, width,
-                                channels, ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(B.data_ptr()),
-                                _stream_ptr(stream)))
+    fn = load().fhd_keystream_trajectory if trajectory else load().fhd_keystream
+    _check(fn(ctypes.c_void_p(IR.data_ptr()), float(gamma), ctypes.byref(p), height, width, channels,
+              ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(B.data_ptr()), _stream_ptr(stream)))
     return D, B
 
 

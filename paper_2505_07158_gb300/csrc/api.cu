@@ -459,10 +459,12 @@ int ensure_scratch(fhd_cipher *c, cudaStream_t s, size_t need, uint8_t **out) {
     return FHD_OK;
 }
 
-// Per-frame scratch: n sub-frame digests, 2n LHCS_m iterates, D, B, and the
-// frame between the two permutation passes.
+// Per-frame scratch: n sub-frame digests, 2n LHCS_m iterates, D, B, the
+// frame between the two permutation passes, and the trajectory records.
 uint64_t frame_scratch(uint32_t n, uint32_t h, uint32_t w, uint32_t C) {
-    return align16(32ull * n) + align16(64ull * n) + align16(2ull * C * (h + w)) + 2 * align16((uint64_t)h * w * C);
+    const uint64_t LD = (uint64_t)C * (h + w), N = (uint64_t)h * w * C;
+    return align16(32ull * n) + align16(64ull * n) + align16(2 * LD) + 2 * align16(N) +
+           align16(fhd::traj_bytes(LD, N, n));
 }
 
 int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *stream, bool encrypt,
@@ -551,6 +553,7 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
             d.D = reinterpret_cast<uint16_t *>(p); p += align16(2ull * d.C * (d.h + d.w));
             d.B = p; p += align16(d.N);
             d.G = p; p += align16(d.N);
+            d.T = p; p += align16(fhd::traj_bytes((uint64_t)d.C * (d.h + d.w), d.N, c->n));
             d.P = fhd::strip_width(d.h, d.w, d.C);
             d.cta0 = ctas;
             ctas += fhd::permute_strips(d.w, d.P);
@@ -611,7 +614,12 @@ int run_frames(fhd_cipher *c, uint32_t count, const fhd_frame *frames, void *str
             for (uint32_t k = 0; k < hk.n_worker_waits; ++k)
                 if (hk.worker_waits[k] && (e = cudaStreamWaitEvent(sb, (cudaEvent_t)hk.worker_waits[k], 0)) != cudaSuccess)
                     return cuda_fail(c, e, "wait worker event");
-        if ((e = timed(c, FHD_K_KEYSTREAM, sb, [&] { return fhd::launch_keystream(b, sb, c->layout == FHD_LAYOUT_THROUGHPUT, c->worker_cta, c->worker_smem); })) != cudaSuccess)
+        if ((e = timed(c, FHD_K_KEYSTREAM, sb, [&] {
+                 return fhd::keystream_route() == FHD_KS_ROUTE_TRAJECTORY
+                            ? fhd::launch_trajectory_keystream(b, sb)
+                            : fhd::launch_keystream(b, sb, c->layout == FHD_LAYOUT_THROUGHPUT, c->worker_cta,
+                                                    c->worker_smem);
+             })) != cudaSuccess)
             return cuda_fail(c, e, "keystream launch");
         if (keystream_done && base + m >= count && (e = cudaEventRecord(keystream_done, sb)) != cudaSuccess)
             return cuda_fail(c, e, "record keystream event");
@@ -683,6 +691,7 @@ int persistent_side(fhd_cipher *c, uint32_t count, const fhd_frame *frames, bool
         d.D = reinterpret_cast<uint16_t *>(p); p += align16(2ull * d.C * (d.h + d.w));
         d.B = p; p += align16(d.N);
         d.G = p; p += align16(d.N);
+        d.T = p; p += align16(fhd::traj_bytes((uint64_t)d.C * (d.h + d.w), d.N, c->n));
         // at most 64 pixels: the persistent column pass (352 threads) covers a strip row (<= 256 bytes) per pass
         uint32_t P = std::min(fhd::strip_width(d.h, d.w, d.C), 64u);
         while (P > 1 && fhd::strip_smem_bytes(d.h, P, d.C) > lim) P /= 2;
@@ -853,6 +862,10 @@ const char *bounds_site_name(unsigned site) {
         case kSiteWorkerIR: return "worker: initial value past the iterates";
         case kSiteWorkerD: return "worker: shift-distance byte past C (h + w) entries";
         case kSiteWorkerB: return "worker: XOR byte past the frame";
+        case kSiteTrajIR: return "trajectory: iterate past 2n x 4";
+        case kSiteTrajRecord: return "trajectory: record past the frame's records";
+        case kSiteEmitLoad: return "emission: record byte past the frame's records";
+        case kSiteEmitStore: return "emission: D or B byte past its buffer";
         case kSiteRowLoad: return "row pass: frame load";
         case kSiteRowShift: return "row pass: row shift load";
         case kSiteRowSmem: return "row pass: shared-memory band or shift table";
@@ -1248,6 +1261,12 @@ int cipher_profile_spans(fhd_cipher *c, void *origin, uint32_t cap, int32_t *kin
 
 uint64_t fhd_launch_count(void) { return g_launches.load(); }
 
+int fhd_set_keystream_route(int route) {
+    const int old = fhd::set_keystream_route(route);
+    if (old < 0) return fail(nullptr, FHD_ERR_INVALID_ARG, "route must be FHD_KS_ROUTE_PAIRS or FHD_KS_ROUTE_TRAJECTORY");
+    return old;
+}
+
 int fhd_set_encrypt_route(int route) {
     if (fhd::set_encrypt_route(route) != 0) return fail(nullptr, FHD_ERR_INVALID_ARG, "route must be FHD_ROUTE_TWO_PASS or FHD_ROUTE_SINGLE_PASS");
     return FHD_OK;
@@ -1521,8 +1540,8 @@ int fhd_master(double *state, const uint8_t *H, const fhd_params *params, double
     return FHD_OK;
 }
 
-int fhd_keystream(const double *IR, double gamma, const fhd_params *params, uint32_t height, uint32_t width,
-                  uint32_t channels, uint16_t *D, uint8_t *B, void *stream) {
+static int keystream_one(const double *IR, double gamma, const fhd_params *params, uint32_t height, uint32_t width,
+                         uint32_t channels, uint16_t *D, uint8_t *B, void *stream, bool trajectory) {
     if (!IR || !D || !B) return fail(nullptr, FHD_ERR_INVALID_ARG, "null argument");
     uint32_t n, u[4];
     double h;
@@ -1545,10 +1564,28 @@ int fhd_keystream(const double *IR, double gamma, const fhd_params *params, uint
     d.w = width;
     d.C = channels;
     d.N = (uint64_t)height * width * channels;
-    cudaError_t e = timed(nullptr, FHD_K_KEYSTREAM, (cudaStream_t)stream,
-                          [&] { return fhd::launch_keystream(b, (cudaStream_t)stream); });
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (trajectory) {
+        e = cudaMallocAsync(&d.T, fhd::traj_bytes((uint64_t)channels * (height + width), d.N, n), s);
+        if (e != cudaSuccess) return fail(nullptr, FHD_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+        e = timed(nullptr, FHD_K_KEYSTREAM, s, [&] { return fhd::launch_trajectory_keystream(b, s); });
+        cudaFreeAsync(d.T, s);
+    } else {
+        e = timed(nullptr, FHD_K_KEYSTREAM, s, [&] { return fhd::launch_keystream(b, s); });
+    }
     if (e != cudaSuccess) return fail(nullptr, FHD_ERR_CUDA, std::string("keystream launch: ") + cudaGetErrorString(e));
     return FHD_OK;
+}
+
+int fhd_keystream(const double *IR, double gamma, const fhd_params *params, uint32_t height, uint32_t width,
+                  uint32_t channels, uint16_t *D, uint8_t *B, void *stream) {
+    return keystream_one(IR, gamma, params, height, width, channels, D, B, stream, false);
+}
+
+int fhd_keystream_trajectory(const double *IR, double gamma, const fhd_params *params, uint32_t height,
+                             uint32_t width, uint32_t channels, uint16_t *D, uint8_t *B, void *stream) {
+    return keystream_one(IR, gamma, params, height, width, channels, D, B, stream, true);
 }
 
 static int permute_one(const uint8_t *src, uint8_t *dst, uint32_t height, uint32_t width, uint32_t channels,

@@ -21,6 +21,7 @@ struct FrameDesc {
     double *IR;        // 2n x 4 iterates of LHCS_m (scratch)
     uint8_t *part;     // n x 32 sub-frame digests (scratch)
     uint8_t *G;        // N bytes: frame between the row and the column pass (scratch)
+    uint8_t *T;        // trajectory records of the one-trajectory keystream route (scratch, traj_bytes)
     uint64_t N;        // h*w*C
     double gamma;      // control parameter of the frame's stream
     uint32_t h, w, C;
@@ -47,6 +48,21 @@ struct Batch {
     uint16_t group_begin[kMaxBatch + 1];
     FrameDesc f[kMaxBatch];
 };
+
+// One-trajectory keystream route (chaos.cu).  Worker pair i starts from the LHCS_m iterates IR[2i] and
+// IR[2i+1] and iterates the same map with the same step (Algorithm 2), so its two systems are the frame's
+// LHCS_m trajectory continued: with s_t the state after t steps from the reconstructed initial condition
+// (IR[t-1] = s_t), step k of pair i yields the stream bytes of s_{2i+1+k} xor those of s_{2i+2+k}.  Record r
+// of the frame is that 24-byte XOR for s_{r+2} and s_{r+3}; worker i's byte stream is the records from byte
+// 48 i on.  traj_records is the number of records the frame's n workers read (a bound: the longest slice
+// plus the offset of the last worker), traj_bytes the scratch they take with the emission's over-read.
+__host__ __device__ inline uint64_t traj_records(uint64_t LD, uint64_t LB, uint32_t n) {
+    const uint64_t need = 2 * ((LD + n - 1) / n) + (LB + n - 1) / n;
+    return (48ull * (n - 1) + need + 23) / 24;
+}
+__host__ __device__ inline uint64_t traj_bytes(uint64_t LD, uint64_t LB, uint32_t n) {
+    return 24 * traj_records(LD, LB, n) + 64;
+}
 
 // ---- Persistent batch launch (persist.cu): one kernel pulls the digest, chaining, worker and permutation
 // tasks of a batch -- of one direction, or of an encryption and the decryption of its ciphertext -- from
@@ -139,6 +155,10 @@ enum : unsigned {
     kSiteWorkerIR = 12,      // a worker chain's initial value past the frame's iterates
     kSiteWorkerD = 13,       // a shift-distance byte past C (h + w) entries
     kSiteWorkerB = 14,       // an XOR byte past the frame
+    kSiteTrajIR = 15,        // trajectory: an LHCS_m iterate past the frame's 2n x 4
+    kSiteTrajRecord = 16,    // trajectory: a record past the frame's traj_records
+    kSiteEmitLoad = 17,      // emission: a record byte past the frame's traj_bytes
+    kSiteEmitStore = 18,     // emission: a D byte past 2 C (h + w) or a B byte past the frame
     kSiteRowLoad = 20,       // row pass: frame (F or G) load
     kSiteRowShift = 21,      // row pass: row shift distance (D) load
     kSiteRowSmem = 22,       // row pass: shared-memory band or shift table
@@ -197,6 +217,11 @@ cudaError_t launch_master_raw(double *state5, const uint8_t *H, uint32_t n, doub
 cudaError_t launch_keystream(const Batch &b, cudaStream_t s, bool dense = false, uint32_t warps_per_cta = 1,
                              uint32_t smem = 0);
 cudaError_t launch_permute(const Batch &b, bool encrypt, cudaStream_t s);
+// The one-trajectory route: every frame's records (one chain per frame, six frames per warp), then D and B
+// from them.  Each frame needs f.T (traj_bytes).
+cudaError_t launch_trajectory_keystream(const Batch &b, cudaStream_t s);
+int set_keystream_route(int route);   // FHD_KS_ROUTE_TRAJECTORY or FHD_KS_ROUTE_PAIRS; -1 on a bad value
+int keystream_route();
 
 // Geometry of the permutation passes: strip width (column pass) and rows per
 // CTA (row pass), and their dynamic shared memory.

@@ -186,6 +186,11 @@ def test_host_side_checks_of_the_persistent_and_tuning_calls(lib):
     assert lib.cipher_persistent_trace(None, 1, None) == fhd.FHD_ERR_INVALID_ARG
     assert lib.cipher_set_worker_cta(None, 4) == fhd.FHD_ERR_INVALID_ARG
     assert lib.fhd_set_encrypt_route(7) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.fhd_set_keystream_route(7) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.fhd_set_keystream_route(-1) == fhd.FHD_ERR_INVALID_ARG
+    assert lib.fhd_set_keystream_route(0) == 1       # the default is the trajectory route
+    assert fhd.fhd_set_keystream_route("trajectory") == "pairs"
+    assert fhd.fhd_set_keystream_route("trajectory") == "trajectory"
     assert lib.fhd_set_row_band(0, 16, 3, 2) == fhd.FHD_ERR_INVALID_ARG
     assert lib.fhd_set_row_band(16, 16, 3, 65) == fhd.FHD_ERR_INVALID_ARG
     assert lib.fhd_row_band(0, 16, 3) == 0

@@ -108,3 +108,37 @@ def test_workers_fed_from_one_master_trajectory_are_shifted_copies():
 
     assert sixth_chi2(0.001) > 1000.0                        # uniform bytes would give ~255
     assert sixth_chi2(oracle.DEFAULT_H) < 330.0
+
+
+def _records(IR0, gamma, R, h):
+    """Records r = 0..R-1 of one trajectory from s_1 = IR0: the 24 stream bytes of s_{r+2} xor s_{r+3}
+    (x, y, z, w in turn, six low mantissa bytes each, least significant first)."""
+    S = oracle.rk4_trajectory(IR0, gamma, R + 1, h)          # s_2 .. s_{R+2}
+    x = (S.view(np.uint64)[:-1] ^ S.view(np.uint64)[1:]) & np.uint64(0xFFFFFFFFFFFF)
+    return np.stack([(x >> np.uint64(8 * k)) & np.uint64(255) for k in range(6)], axis=-1).astype(np.uint8).reshape(-1)
+
+
+@pytest.mark.parametrize("h,w,C,n", [(16, 16, 3, 32), (1, 16, 3, 32), (7, 5, 1, 4), (9, 33, 3, 1), (2, 2, 1, 64),
+                                     (32, 48, 3, 32), (3, 8, 3, 7)])
+def test_keystream_is_windows_of_one_trajectory(h, w, C, n):
+    """The identity the one-trajectory keystream route computes, checked against the oracle's Algorithm 2:
+    with R = ceil((48 (n - 1) + 2 ceil(L_D / n) + ceil(N / n)) / 24) records of the frame's LHCS_m trajectory
+    continued from IR[0], worker i's slice of D (16-bit little-endian pairs) and then its slice of B are the
+    record bytes from 48 i on.  Shapes with one worker, slices shorter than 16 bytes and n > the number of
+    rows are included."""
+    key = si.key(30 + n)
+    ic = oracle.key_to_ic(key)
+    H = oracle.sha256(bytes(si.rng(n).integers(0, 256, 64, dtype=np.uint8)))
+    IR, _ = oracle.master(np.array(ic[:4]), H, ic[4], n=n)
+    D0, B0 = oracle.keystream(IR, ic[4], h, w, C, n=n)
+    LD, LB = C * (h + w), h * w * C
+    R = -(-(48 * (n - 1) + 2 * -(-LD // n) + -(-LB // n)) // 24)
+    G = _records(np.asarray(IR).reshape(-1, 4)[0], ic[4], R, oracle.DEFAULT_H)
+    D1, B1 = np.zeros(LD, np.uint16), np.zeros(LB, np.uint8)
+    for i, ((d0, d1), (b0, b1)) in enumerate(zip(_slices(LD, n), _slices(LB, n))):
+        src = G[48 * i:48 * i + 2 * (d1 - d0) + (b1 - b0)]
+        assert src.size == 2 * (d1 - d0) + (b1 - b0)       # R records cover every worker's window
+        D1[d0:d1] = src[0:2 * (d1 - d0):2].astype(np.uint16) | (src[1:2 * (d1 - d0):2].astype(np.uint16) << 8)
+        B1[b0:b1] = src[2 * (d1 - d0):]
+    assert np.array_equal(D0, D1)
+    assert np.array_equal(B0, B1)
