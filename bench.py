@@ -108,6 +108,11 @@ def parse():
                     help="time the tile shapes of every workload's frame sizes and the clip pipeline's work split "
                          "(layout, clips in flight, worker window) and write the table to OUT.json "
                          "(the library's tuned.json format); prints it and exits")
+    ap.add_argument("--copy-streams", type=int, default=2, choices=[1, 2, 4],
+                    help="end-to-end run: CUDA streams per copy direction, clips taking them in turn")
+    ap.add_argument("--e2e-out-buffers", type=int, default=2,
+                    help="end-to-end run: pinned host buffers the decrypted clips are copied into, in turn "
+                         "(0: one per clip in flight)")
     ap.add_argument("--spans", default=None,
                     help="write the timed region's launch timeline (sender and receiver, ms from its start) as JSON")
     return ap.parse_args()
@@ -434,16 +439,28 @@ def run_ours(args):
             self.h2d_done = torch.cuda.Event()
             self.used = False
             self.e2e_used = False
-            self.host_out = torch.empty_like(host).pin_memory()
+            self.host_out = torch.empty_like(host).pin_memory() if args.e2e_out_buffers <= 0 else None
             self.host_dig = torch.empty((FRAMES, 32), dtype=torch.uint8).pin_memory()
+            self.index = len(slots)
 
-    slots = [Slot() for _ in range(max(1, args.inflight))]
+    slots = []
+    for _ in range(max(1, args.inflight)):
+        slots.append(Slot())
+    # Decrypted clips go to a ring of pinned host buffers (a consumer reads each before its turn comes round
+    # again), or to one buffer per clip in flight.
+    n_out = max(0, args.e2e_out_buffers)
+    host_outs = [torch.empty_like(host).pin_memory() for _ in range(n_out)]
+    e2e_out_used = set()
     # The end-to-end copies run on two streams of their own, one per direction, so that a copy waiting for
     # its slot to come free never sits in a compute stream.  A clip's host-to-device copy waits only for the
     # slot's previous encryption to have read its frames, so it runs a round trip ahead; the sender waits
     # for that copy and for the slot's previous receiver and copy-out (the ciphertext, digest and output
     # buffers are reused); the copy-out waits for the receiver.
-    h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
+    # With several copy streams per direction, the clips take them in turn; a clip's copy-out stream is the
+    # one of its host buffer (clips that share a buffer share its stream, so their copies stay in order).
+    h2ds = [torch.cuda.Stream() for _ in range(args.copy_streams)]
+    d2hs = [torch.cuda.Stream() for _ in range(args.copy_streams)]
+    clip_no = [0]
     WW = args.worker_window if 0 < args.worker_window < len(slots) else 0
     KEEP = max(2, WW)
     last = [None] * KEEP     # slots of the previous clips, oldest first: the chaining state advances clip after clip
@@ -451,6 +468,15 @@ def run_ours(args):
     def round_trip(sl, e2e=False):
         prev, prev2 = last[-1], last[-2]
         if e2e:
+            k_clip = clip_no[0]
+            clip_no[0] += 1
+            if n_out:
+                ob = k_clip % n_out
+                out_buf, d2h = host_outs[ob], d2hs[ob % len(d2hs)]
+                e2e_out_used.add(ob)
+            else:
+                out_buf, d2h = sl.host_out, d2hs[sl.index % len(d2hs)]
+            h2d = h2ds[k_clip % len(h2ds)]
             if sl.used:
                 h2d.wait_event(sl.cipher_ready)
             with torch.cuda.stream(h2d):
@@ -499,7 +525,7 @@ def run_ours(args):
         if e2e:
             d2h.wait_event(sl.dec_done)
             with torch.cuda.stream(d2h):
-                sl.host_out.copy_(sl.dec_all, non_blocking=True)
+                out_buf.copy_(sl.dec_all, non_blocking=True)
                 sl.host_dig.copy_(sl.digs, non_blocking=True)
             sl.e2e_used = True
             sl.rx_done.record(d2h)
@@ -611,7 +637,8 @@ def run_ours(args):
                  "repeats": {"n": len(e2e_reps), "value": "median",
                              "min": world * FRAMES / (e2e_reps[-1][0] / 1000.0),
                              "max": world * FRAMES / (e2e_reps[0][0] / 1000.0), "values": e2e_values}}
-    e2e_ok = all(torch.equal(sl.host_out, host) for sl in slots if sl.e2e_used)
+    e2e_ok = (all(torch.equal(host_outs[b], host) for b in e2e_out_used) if n_out else
+              all(torch.equal(sl.host_out, host) for sl in slots if sl.e2e_used))
 
     # ---- plain path: one call per frame (the paper's per-frame loop), one CUDA stream
     sl0 = slots[0]
@@ -790,6 +817,8 @@ def run_ours(args):
                        "int_mix_per8": args.int_mix, "worker_smem_bytes": args.worker_smem,
                        "worker_layout": args.layout, "worker_warps_per_cta": args.worker_cta,
                        "encrypt_route": args.encrypt_route, "keystream_route": args.keystream_route,
+                       "e2e_copy_streams_per_direction": args.copy_streams,
+                       "e2e_host_out_buffers": n_out or "one per clip in flight",
                        "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS"),
                        "sm_partition": {"lhcs_m_sms": enc.partition()[0], "other_sms": enc.partition()[1],
                                         "digest_stage_own_sms": bool(args.digest_partition and not args.no_partition)},

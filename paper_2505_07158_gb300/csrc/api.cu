@@ -692,6 +692,8 @@ int persistent_side(fhd_cipher *c, uint32_t count, const fhd_frame *frames, bool
         d.B = p; p += align16(d.N);
         d.G = p; p += align16(d.N);
         d.T = p; p += align16(fhd::traj_bytes((uint64_t)d.C * (d.h + d.w), d.N, c->n));
+        S.emits[k] = fhd::keystream_route() == FHD_KS_ROUTE_TRAJECTORY
+                         ? (uint32_t)((d.N + fhd::kEmitTaskBytes - 1) / fhd::kEmitTaskBytes) : 0u;
         // at most 64 pixels: the persistent column pass (352 threads) covers a strip row (<= 256 bytes) per pass
         uint32_t P = std::min(fhd::strip_width(d.h, d.w, d.C), 64u);
         while (P > 1 && fhd::strip_smem_bytes(d.h, P, d.C) > lim) P /= 2;
@@ -767,7 +769,8 @@ int run_persistent(fhd_cipher *c0, fhd_cipher *c1, uint32_t count, const fhd_fra
     if (rc == FHD_OK && c1) rc = persistent_side(c1, count, f1, false, s, L.s[1], mem_smem);
     if (rc != FHD_OK) return rc;
     L.sides = c1 ? 2 : 1;
-    L.wpf = (c0->n + 2) / 3;
+    L.traj = fhd::keystream_route() == FHD_KS_ROUTE_TRAJECTORY;
+    L.wpf = L.traj ? 1u : (c0->n + 2) / 3;
     L.sha_units = encrypt0 ? (uint32_t)(((uint64_t)count * c0->n + 31) / 32) : 0;
 
     std::vector<uint32_t> idx(count);
@@ -798,8 +801,8 @@ int run_persistent(fhd_cipher *c0, fhd_cipher *c1, uint32_t count, const fhd_fra
     L.memb_begin[0] = 0;
     for (uint32_t r = 0; r < count; ++r) {
         const uint32_t f = L.mprio[r];
-        uint32_t blk = L.s[0].strips[f] + L.s[0].bands[f];
-        if (c1) blk += L.s[1].strips[f] + L.s[1].bands[f];
+        uint32_t blk = L.s[0].emits[f] + L.s[0].strips[f] + L.s[0].bands[f];
+        if (c1) blk += L.s[1].emits[f] + L.s[1].strips[f] + L.s[1].bands[f];
         L.memb_begin[r + 1] = L.memb_begin[r] + blk;
     }
     L.mem_tasks = L.memb_begin[count];

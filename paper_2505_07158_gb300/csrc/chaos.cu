@@ -88,138 +88,38 @@ __global__ void __launch_bounds__(256) keystream_kernel(const __grid_constant__ 
     keystream_warp<kPairs>(b.f[f], b.n, c, pg, threadIdx.x & 31);
 }
 
-// ---- One-trajectory route (see traj_records in common.cuh).
-//
-// K2t: the records of six frames per warp, one chain per frame, in the six-chain layout of LHCS_m (lane
-// 4c + v holds variable v of frame 6 blockIdx.x + c; lanes 24..31 hold the constants).  Steps k = 1, 2, ...
-// take the state from s_k to s_{k+1}: while k < 2n it is LHCS_m's iterate IR[k], read back, and from k = 2n
-// on one RK4 step.  After step k >= 2 the warp writes record k - 2 = (s_k, s_{k+1}): the 48-bit XOR of each
-// variable's two bit patterns (its six low mantissa bytes) is packed with the next variable's by one
-// shuffle, and lanes v = 0, 1, 2 store the record's three 64-bit words.  A chain is strictly sequential, so
-// its time is the number of steps times the step's latency (27 binary64 instructions back to back, plus the
-// hand-offs); the warp runs to its longest frame.
-__device__ __forceinline__ unsigned long long low48(double x) {
-    return (unsigned long long)__double_as_longlong(x) & 0xffffffffffffull;
-}
+// ---- One-trajectory route (see traj_records in common.cuh; the warp and chunk bodies are in chaos_dev.cuh).
 
+// K2t: the records of six frames per warp, one chain per frame (lane 4c + v: variable v of frame
+// 6 blockIdx.x + c).
 __global__ void __launch_bounds__(32) trajectory_kernel(const __grid_constant__ Batch b) {
-    const int lane = threadIdx.x, v = lane & 3, ch = lane >> 2;
-    const uint32_t f = blockIdx.x * kChainsPerWarp + ch;
-    const bool active = ch < kChainsPerWarp && f < b.count;
-    const uint32_t n = b.n;
-    uint64_t R = 0;
-    double gamma = 0.0;
-    const double *IR = nullptr;
-    uint64_t *rec = nullptr;
-    if (active) {
-        const FrameDesc &fd = b.f[f];
-        R = traj_records((uint64_t)fd.C * (fd.h + fd.w), fd.N, n);
-        gamma = fd.gamma;
-        IR = fd.IR;
-        rec = reinterpret_cast<uint64_t *>(fd.T);
-    }
-    unsigned long long Rmax = R;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        const unsigned long long t = __shfl_xor_sync(0xffffffffu, Rmax, o);
-        Rmax = t > Rmax ? t : Rmax;
-    }
-    const Rk4 c{b.hstep, b.hhalf, b.hsixth};
-    const LaneRole role = lane_role(lane, gamma);
-    double s = lane_init(lane, active && FHD_IN(v, 8ull * n, kSiteTrajIR) ? __ldcg(IR + v) : 0.0);   // s_1
-    unsigned long long prev = low48(s);
-    for (uint64_t k = 1; k <= Rmax + 1; ++k) {
-        if (k < 2ull * n) {   // s_{k+1} = IR[k] (uniform over the warp)
-            if (active && FHD_IN(4 * k + v, 8ull * n, kSiteTrajIR)) s = __ldcg(IR + 4 * k + v);
-        } else {
-            rk4_step_lanes(s, role, c);
-        }
-        const unsigned long long cur = low48(s);
-        const unsigned long long x = prev ^ cur;
-        const unsigned long long nx = __shfl_down_sync(0xffffffffu, x, 1);
-        const uint64_t r = k - 2;
-        if (k >= 2 && active && v < 3 && r < R && FHD_IN(3 * r + v, 3 * R, kSiteTrajRecord))
-            rec[3 * r + v] = (x >> (16 * v)) | (nx << (48 - 16 * v));
-        prev = cur;
-    }
+    const int lane = threadIdx.x;
+    const uint32_t f = blockIdx.x * kChainsPerWarp + (lane >> 2);
+    const bool active = (lane >> 2) < kChainsPerWarp && f < b.count;
+    trajectory_warp(active ? &b.f[f] : nullptr, b.n, Rk4{b.hstep, b.hhalf, b.hsixth}, lane);
 }
 
-// K2e: D and B of every frame from its records.  CTA (x, f) takes worker slice i = x / cps of frame f, and
-// part j = x % cps of it: part 0 also writes the slice's D bytes (byte q of the slice's D bytes is record
-// byte 48 i + q), and the parts split the slice's B bytes (B[b0 + m] is record byte 48 i + 2 nd + m) in
-// 16-byte chunks of B, kEmitChunks per thread.  A chunk inside the slice is one 16-byte store of bytes
-// o .. o + 15 of two aligned 16-byte record loads (o = the source offset mod 16, the same for the whole
-// slice); the chunks at the slice's ends, and every chunk of an unaligned B, go byte by byte.
+// K2e: D and B of every frame from its records.  CTA (x, f) takes worker slice i = x / cps of frame f and
+// part j = x % cps of it: part 0 also writes the slice's D bytes, and the parts split the slice's B bytes
+// in runs of kEmitChunks x kEmitThreads 16-byte chunks of B.
 constexpr int kEmitThreads = 256;
 constexpr int kEmitChunks = 4;
-
-__device__ __forceinline__ uint32_t word8(const uint4 &a, const uint4 &b, int i) {
-    switch (i) {
-        case 0: return a.x;
-        case 1: return a.y;
-        case 2: return a.z;
-        case 3: return a.w;
-        case 4: return b.x;
-        case 5: return b.y;
-        case 6: return b.z;
-        default: return b.w;
-    }
-}
 
 __global__ void __launch_bounds__(kEmitThreads) emit_kernel(const __grid_constant__ Batch b, uint32_t cps) {
     const uint32_t f = blockIdx.y, i = blockIdx.x / cps, j = blockIdx.x % cps;
     if (f >= b.count || i >= b.n) return;
     const FrameDesc &fd = b.f[f];
-    const uint64_t LD = (uint64_t)fd.C * (fd.h + fd.w), LB = fd.N;
     __shared__ WorkerSlice ws_s;
-    if (threadIdx.x == 0) ws_s = worker_slice(LD, LB, b.n, i);
+    if (threadIdx.x == 0) ws_s = worker_slice((uint64_t)fd.C * (fd.h + fd.w), fd.N, b.n, i);
     __syncthreads();
     const WorkerSlice ws = ws_s;
-    const uint8_t *T = fd.T;
-    const uint64_t tlim = traj_bytes(LD, LB, b.n);
-    const uint64_t s0 = 48ull * i;   // worker i's stream in the records
-    if (j == 0) {
-        uint8_t *Db = reinterpret_cast<uint8_t *>(fd.D);
-        for (uint64_t q = threadIdx.x; q < 2 * ws.nd; q += kEmitThreads) {
-            const uint8_t byte = FHD_IN(s0 + q, tlim, kSiteEmitLoad) ? T[s0 + q] : 0;
-            if (FHD_IN(2 * ws.d0 + q, 2 * LD, kSiteEmitStore)) Db[2 * ws.d0 + q] = byte;
-        }
-    }
+    if (j == 0) emit_d_slice(fd, b.n, i, ws, threadIdx.x, kEmitThreads);
     if (!ws.nb) return;
-    uint8_t *B = fd.B;
-    const uint64_t sb = s0 + 2 * ws.nd;   // record byte of B[b0]
-    const uint64_t lo = ws.b0, hi = ws.b0 + ws.nb;
-    const bool aligned = (reinterpret_cast<uintptr_t>(B) & 15) == 0;
-    const uint64_t c_lo = lo >> 4, c_hi = (hi + 15) >> 4;   // chunks [16 c, 16 c + 16) meeting the slice
-    const uint32_t o = (uint32_t)((sb - lo) & 15), q = o >> 2, r = 8 * (o & 3);
-#pragma unroll
-    for (int u = 0; u < kEmitChunks; ++u) {
-        const uint64_t cidx = c_lo + ((uint64_t)j * kEmitChunks + u) * kEmitThreads + threadIdx.x;
-        if (cidx >= c_hi) break;
-        const uint64_t p0 = 16 * cidx;
-        if (aligned && p0 >= lo && p0 + 16 <= hi) {
-            const uint64_t sp = sb + (p0 - lo);   // sp mod 16 = o
-            const uint64_t a = sp & ~15ull;
-            uint4 w0 = make_uint4(0, 0, 0, 0), w1 = w0;
-            if (FHD_IN(a + 31, tlim, kSiteEmitLoad)) {
-                w0 = __ldcg(reinterpret_cast<const uint4 *>(T + a));
-                w1 = __ldcg(reinterpret_cast<const uint4 *>(T + a) + 1);
-            }
-            uint4 out;
-            out.x = __funnelshift_r(word8(w0, w1, q), word8(w0, w1, q + 1), r);
-            out.y = __funnelshift_r(word8(w0, w1, q + 1), word8(w0, w1, q + 2), r);
-            out.z = __funnelshift_r(word8(w0, w1, q + 2), word8(w0, w1, q + 3), r);
-            out.w = __funnelshift_r(word8(w0, w1, q + 3), word8(w0, w1, q + 4), r);
-            if (FHD_IN(p0 + 15, LB, kSiteEmitStore)) *reinterpret_cast<uint4 *>(B + p0) = out;
-        } else {
-            const uint64_t e = p0 + 16 < hi ? p0 + 16 : hi;
-            for (uint64_t p = p0 > lo ? p0 : lo; p < e; ++p) {
-                const uint64_t sp = sb + (p - lo);
-                const uint8_t byte = FHD_IN(sp, tlim, kSiteEmitLoad) ? T[sp] : 0;
-                if (FHD_IN(p, LB, kSiteEmitStore)) B[p] = byte;
-            }
-        }
-    }
+    const uint64_t per = 16ull * kEmitThreads * kEmitChunks;
+    const uint64_t base = (ws.b0 >> 4) << 4;   // the slice's first chunk
+    const uint64_t lo = base + j * per, hi = lo + per;
+    const uint64_t a = lo > ws.b0 ? lo : ws.b0, e = hi < ws.b0 + ws.nb ? hi : ws.b0 + ws.nb;
+    if (a < e) emit_b_part(fd, b.n, i, ws, a, e, threadIdx.x, kEmitThreads);
 }
 
 int g_ks_route = FHD_KS_ROUTE_TRAJECTORY;

@@ -338,6 +338,126 @@ __device__ void keystream_warp(const FrameDesc &fd, uint32_t n, const Rk4 &c, ui
     }
 }
 
+// ---- One-trajectory keystream route (traj_records in common.cuh).
+
+__device__ __forceinline__ unsigned long long low48(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0xffffffffffffull;
+}
+
+// The records of one frame per chain of the warp, in the six-chain layout of LHCS_m (lane 4c + v holds
+// variable v of chain c; lanes 24..31 hold the constants).  fd: this lane's frame (the four lanes of a chain
+// share it), nullptr where the chain has none.  Steps k = 1, 2, ... take the state from s_k to s_{k+1}:
+// while k < 2n it is LHCS_m's iterate IR[k], read back, and from k = 2n on one RK4 step.  After step k >= 2
+// the warp writes record k - 2 = (s_k, s_{k+1}): the 48-bit XOR of each variable's two bit patterns (its six
+// low mantissa bytes) is packed with the next variable's by one shuffle, and lanes v = 0, 1, 2 store the
+// record's three 64-bit words.  A chain is strictly sequential, so its time is the number of steps times the
+// step's latency (27 binary64 instructions back to back, plus the hand-offs); the warp runs to its longest
+// frame.  All 32 lanes call it together.
+__device__ void trajectory_warp(const FrameDesc *fd, uint32_t n, const Rk4 &c, int lane) {
+    const int v = lane & 3;
+    const bool active = fd != nullptr && lane < 4 * kChainsPerWarp;
+    uint64_t R = 0;
+    double gamma = 0.0;
+    const double *IR = nullptr;
+    uint64_t *rec = nullptr;
+    if (active) {
+        R = traj_records((uint64_t)fd->C * (fd->h + fd->w), fd->N, n);
+        gamma = fd->gamma;
+        IR = fd->IR;
+        rec = reinterpret_cast<uint64_t *>(fd->T);
+    }
+    unsigned long long Rmax = R;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, Rmax, o);
+        Rmax = t > Rmax ? t : Rmax;
+    }
+    const LaneRole role = lane_role(lane, gamma);
+    double s = lane_init(lane, active && FHD_IN(v, 8ull * n, kSiteTrajIR) ? __ldcg(IR + v) : 0.0);   // s_1
+    unsigned long long prev = low48(s);
+    for (uint64_t k = 1; k <= Rmax + 1; ++k) {
+        if (k < 2ull * n) {   // s_{k+1} = IR[k] (uniform over the warp)
+            if (active && FHD_IN(4 * k + v, 8ull * n, kSiteTrajIR)) s = __ldcg(IR + 4 * k + v);
+        } else {
+            rk4_step_lanes(s, role, c);
+        }
+        const unsigned long long cur = low48(s);
+        const unsigned long long x = prev ^ cur;
+        const unsigned long long nx = __shfl_down_sync(0xffffffffu, x, 1);
+        const uint64_t r = k - 2;
+        if (k >= 2 && active && v < 3 && r < R && FHD_IN(3 * r + v, 3 * R, kSiteTrajRecord))
+            rec[3 * r + v] = (x >> (16 * v)) | (nx << (48 - 16 * v));
+        prev = cur;
+    }
+}
+
+__device__ __forceinline__ uint32_t word8(const uint4 &a, const uint4 &b, uint32_t i) {
+    switch (i) {
+        case 0: return a.x;
+        case 1: return a.y;
+        case 2: return a.z;
+        case 3: return a.w;
+        case 4: return b.x;
+        case 5: return b.y;
+        case 6: return b.z;
+        default: return b.w;
+    }
+}
+
+// Worker slice i's D bytes from the records (byte q of them is record byte 48 i + q), by threads tid of
+// nthreads.
+__device__ void emit_d_slice(const FrameDesc &fd, uint32_t n, uint32_t i, const WorkerSlice &ws, uint32_t tid,
+                             uint32_t nthreads) {
+    const uint64_t LD = (uint64_t)fd.C * (fd.h + fd.w);
+    const uint64_t tlim = traj_bytes(LD, fd.N, n), s0 = 48ull * i;
+    uint8_t *Db = reinterpret_cast<uint8_t *>(fd.D);
+    for (uint64_t q = tid; q < 2 * ws.nd; q += nthreads) {
+        const uint8_t byte = FHD_IN(s0 + q, tlim, kSiteEmitLoad) ? fd.T[s0 + q] : 0;
+        if (FHD_IN(2 * ws.d0 + q, 2 * LD, kSiteEmitStore)) Db[2 * ws.d0 + q] = byte;
+    }
+}
+
+// B[lo, hi) inside worker slice i (B[b0 + m] is record byte 48 i + 2 nd + m), by threads tid of nthreads in
+// 16-byte chunks of B: a chunk inside [lo, hi) is one 16-byte store of bytes o .. o + 15 of two aligned
+// 16-byte record loads (o = the source offset mod 16, the same for the whole slice); the chunks at the ends
+// of [lo, hi), and every chunk of a B that is not 16-byte aligned, go byte by byte.
+__device__ void emit_b_part(const FrameDesc &fd, uint32_t n, uint32_t i, const WorkerSlice &ws, uint64_t lo,
+                            uint64_t hi, uint32_t tid, uint32_t nthreads) {
+    const uint64_t LD = (uint64_t)fd.C * (fd.h + fd.w), LB = fd.N;
+    const uint64_t tlim = traj_bytes(LD, LB, n);
+    const uint8_t *T = fd.T;
+    uint8_t *B = fd.B;
+    const uint64_t sb = 48ull * i + 2 * ws.nd;   // record byte of B[b0]
+    const bool aligned = (reinterpret_cast<uintptr_t>(B) & 15) == 0;
+    const uint32_t o = (uint32_t)((sb - ws.b0) & 15), q = o >> 2, r = 8 * (o & 3);
+    const uint64_t c_hi = (hi + 15) >> 4;
+    for (uint64_t cidx = (lo >> 4) + tid; cidx < c_hi; cidx += nthreads) {
+        const uint64_t p0 = 16 * cidx;
+        if (aligned && p0 >= lo && p0 + 16 <= hi) {
+            const uint64_t sp = sb + (p0 - ws.b0);   // sp mod 16 = o
+            const uint64_t a = sp & ~15ull;
+            uint4 w0 = make_uint4(0, 0, 0, 0), w1 = w0;
+            if (FHD_IN(a + 31, tlim, kSiteEmitLoad)) {
+                w0 = __ldcg(reinterpret_cast<const uint4 *>(T + a));
+                w1 = __ldcg(reinterpret_cast<const uint4 *>(T + a) + 1);
+            }
+            uint4 out;
+            out.x = __funnelshift_r(word8(w0, w1, q), word8(w0, w1, q + 1), r);
+            out.y = __funnelshift_r(word8(w0, w1, q + 1), word8(w0, w1, q + 2), r);
+            out.z = __funnelshift_r(word8(w0, w1, q + 2), word8(w0, w1, q + 3), r);
+            out.w = __funnelshift_r(word8(w0, w1, q + 3), word8(w0, w1, q + 4), r);
+            if (FHD_IN(p0 + 15, LB, kSiteEmitStore)) *reinterpret_cast<uint4 *>(B + p0) = out;
+        } else {
+            const uint64_t e = p0 + 16 < hi ? p0 + 16 : hi;
+            for (uint64_t p = p0 > lo ? p0 : lo; p < e; ++p) {
+                const uint64_t sp = sb + (p - ws.b0);
+                const uint8_t byte = FHD_IN(sp, tlim, kSiteEmitLoad) ? T[sp] : 0;
+                if (FHD_IN(p, LB, kSiteEmitStore)) B[p] = byte;
+            }
+        }
+    }
+}
+
 // LHCS_m of stream group g of a batch (Algorithm 1), one warp (lane = its lane), the group's frames in call
 // order: reconstruct from the chaining state and the frame's digest, 2n RK4 steps into the frame's IR, and
 // chain on.  before(f) runs on every lane before frame f and may refuse it (false ends the group and keeps

@@ -63,6 +63,8 @@ __host__ __device__ inline uint64_t traj_records(uint64_t LD, uint64_t LB, uint3
 __host__ __device__ inline uint64_t traj_bytes(uint64_t LD, uint64_t LB, uint32_t n) {
     return 24 * traj_records(LD, LB, n) + 64;
 }
+// B bytes per emission task of a persistent launch (a multiple of 16; the frame's task 0 also writes D).
+constexpr uint64_t kEmitTaskBytes = 180224;
 
 // ---- Persistent batch launch (persist.cu): one kernel pulls the digest, chaining, worker and permutation
 // tasks of a batch -- of one direction, or of an encryption and the decryption of its ciphertext -- from
@@ -79,6 +81,7 @@ struct PSide {
     uint16_t group_begin[kPMax + 1];
     uint32_t strips[kPMax];   // column-pass strips of frame k
     uint32_t bands[kPMax];    // row-pass bands of frame k
+    uint32_t emits[kPMax];    // emission tasks of frame k (one-trajectory route; 0 with the worker pairs)
     struct StreamState *states;
     unsigned *status;
     FrameDesc f[kPMax];
@@ -93,16 +96,20 @@ struct PCounters {
     unsigned ks_done[2][kPMax];        // worker warps of the frame done
     unsigned rows_done[2][kPMax];      // row-pass bands of the frame done
     unsigned strips_done[2][kPMax];    // column-pass strips of the frame done
+    unsigned emit_done[2][kPMax];      // emission tasks of the frame done (one-trajectory route)
     // %globaltimer at the launch's start and when each of the counters above reached its target
     // (instrumentation: cipher_persistent_trace)
     unsigned long long t0;
     unsigned long long t_digest[kPMax];
     unsigned long long t_master[2][kPMax], t_ks[2][kPMax], t_rows[2][kPMax], t_strips[2][kPMax];
+    unsigned long long t_emit[2][kPMax];
 };
 
 struct PLaunch {
     uint32_t sides;            // 1: one direction; 2: side 0 encrypts, side 1 decrypts side 0's ciphertexts
-    uint32_t wpf;              // worker warps per frame (three worker pairs each)
+    uint32_t traj;             // 1: the one-trajectory route (a frame's keystream task is its trajectory,
+                               // then emission tasks in the permutation queue); 0: worker pairs
+    uint32_t wpf;              // keystream tasks per frame: worker warps (three worker pairs each), or 1
     uint32_t sha_units;        // digest pipelines of side 0 when it encrypts (32 messages each), else 0
     uint32_t chain_tasks;      // the LHCS_m tasks, then per frame (mprio order) its worker warps
     uint32_t chain_masters_total;

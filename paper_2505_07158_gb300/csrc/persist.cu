@@ -10,16 +10,19 @@
 //   * warps 2, 3 and 5: chain workers, one on each of sub-partitions 1-3, so that a chain has its
 //     sub-partition's binary64 pipe, and its issue port, to itself; per frame, smallest first
 //     (the order in which their digests arrive): the LHCS_m task of every stream whose earliest frame it
-//     is (Algorithm 1), then the frame's worker warps (Algorithm 2, three worker pairs each, the two sides
-//     interleaved);
+//     is (Algorithm 1), then the frame's keystream tasks (Algorithm 2, the two sides interleaved): with the
+//     one-trajectory route one task per frame and side, the frame's trajectory records (traj_records in
+//     common.cuh); with the worker pairs one per three pairs;
 //   * warps 4 and 6-15: a permutation group of 352 threads with the CTA's large shared memory: per frame,
-//     smallest first, the row bands and column strips of the encryption, then the decryption's column
-//     strips and row bands (Sec. II-C, Algos 3-7, and the inverse).
+//     smallest first, the encryption's emission tasks (one-trajectory route: D and B from the records, in
+//     runs of kEmitTaskBytes of B), row bands and column strips, then the decryption's emission tasks,
+//     column strips and row bands (Sec. II-C, Algos 3-7, and the inverse).
 // A task waits for its inputs on per-frame counters: LHCS_m for the frame digest (the decryption's for the
-// encryption's LHCS_m of the same frame, which writes the transmitted digest), a worker warp for its frame's
-// LHCS_m, an encrypting row band for the frame's keystream (the row shifts), an encrypting strip for the
-// frame's row bands, a decrypting strip for its keystream and the ciphertext, a decrypting row band for
-// the frame's strips.  Tasks are dequeued in an order in
+// encryption's LHCS_m of the same frame, which writes the transmitted digest), a keystream task for its
+// frame's LHCS_m, an emission task for its frame's trajectory, an encrypting row band for the frame's
+// keystream (the row shifts: its worker warps, or its emission tasks), an encrypting strip for the frame's
+// row bands, a decrypting strip for its keystream and the ciphertext, a decrypting row band for the
+// frame's strips.  Tasks are dequeued in an order in
 // which every dependency of a task was dequeued before it, by a worker that does not wait on anything
 // later, so the launch completes whatever number of its CTAs is resident.  Every wait is bounded: past the
 // launch's time limit (%globaltimer, and an iteration cap as a second bound) the waiting task sets the
@@ -174,13 +177,39 @@ __device__ __noinline__ void keystream_task(const FrameDesc &fd, uint32_t n, con
     keystream_warp<3>(fd, n, c, pg, lane);
 }
 
-// The same for the permutation group's four task bodies.
-__device__ __noinline__ void mem_task(uint32_t kind, const FrameDesc &fd, uint32_t idx, uint8_t *smem, uint32_t mtid) {
+// One-trajectory route: the frame's trajectory on chain 0 of the warp (lanes 0..3).
+__device__ __noinline__ void trajectory_task(const FrameDesc &fd, uint32_t n, const Rk4 &c, int lane) {
+    trajectory_warp(lane < 4 ? &fd : nullptr, n, c, lane);
+}
+
+// Emission task idx of a frame (one-trajectory route): B bytes [idx kEmitTaskBytes, (idx + 1) kEmitTaskBytes)
+// from the records, slice by slice, and for idx 0 also every slice's D bytes.
+__device__ void emit_task(const FrameDesc &fd, uint32_t n, uint32_t idx, uint32_t mtid) {
+    const uint64_t LD = (uint64_t)fd.C * (fd.h + fd.w), LB = fd.N;
+    if (idx == 0)
+        for (uint32_t i = 0; i < n; ++i) emit_d_slice(fd, n, i, worker_slice(LD, LB, n, i), mtid, kMemThreads);
+    const uint64_t lo = (uint64_t)idx * kEmitTaskBytes;
+    const uint64_t hi = lo + kEmitTaskBytes < LB ? lo + kEmitTaskBytes : LB;
+    if (lo >= hi) return;
+    // the slice holding B[lo]: the largest i with floor(i LB / n) <= lo
+    uint32_t i = (uint32_t)(((lo + 1) * n - 1) / LB);
+    for (; i < n; ++i) {
+        const WorkerSlice ws = worker_slice(LD, LB, n, i);
+        if (ws.b0 >= hi) break;
+        const uint64_t a = lo > ws.b0 ? lo : ws.b0, e = hi < ws.b0 + ws.nb ? hi : ws.b0 + ws.nb;
+        if (a < e) emit_b_part(fd, n, i, ws, a, e, mtid, kMemThreads);
+    }
+}
+
+// The same for the permutation group's task bodies (kind 4: an emission task).
+__device__ __noinline__ void mem_task(uint32_t kind, const FrameDesc &fd, uint32_t n, uint32_t idx, uint8_t *smem,
+                                      uint32_t mtid) {
     auto sync = [] { bar_sync(kBarMem, kMemThreads); };
     if (kind == 0) row_pass<true, true>(fd, idx, smem, mtid, kMemThreads, sync);
     else if (kind == 1) strip_pass<true, true>(fd, idx, smem, mtid, kMemThreads, sync);
     else if (kind == 2) strip_pass<false, true>(fd, idx, smem, mtid, kMemThreads, sync);
-    else row_pass<false, true>(fd, idx, smem, mtid, kMemThreads, sync);
+    else if (kind == 3) row_pass<false, true>(fd, idx, smem, mtid, kMemThreads, sync);
+    else emit_task(fd, n, idx, mtid);
 }
 
 // ---- chain workers (warps 2-5): LHCS_m tasks, then worker warps
@@ -198,7 +227,7 @@ __device__ void chain_worker(const PLaunch &L, uint8_t *H) {
         task = __shfl_sync(0xffffffffu, task, 0);
         if (task >= L.chain_tasks) return;
         // first every LHCS_m task (the groups in the order of their earliest frame, side 0 then side 1),
-        // then per frame (smallest first) its worker warps, the sides interleaved
+        // then per frame (smallest first) its keystream tasks, the sides interleaved
         if (task < L.chain_masters_total) {
             const uint32_t r = segment(L.chain_begin, L.s[0].count, task);
             const uint32_t f = L.mprio[r], side = task - L.chain_begin[r];
@@ -224,8 +253,10 @@ __device__ void chain_worker(const PLaunch &L, uint8_t *H) {
                 !FHD_IN(side, L.sides, kSitePersistTask))
                 continue;
             const PSide &S = L.s[side];
-            if (wait(&L.cnt->master_done[side][f], 1u))
-                keystream_task(S.f[f], S.n, Rk4{S.hstep, S.hhalf, S.hsixth}, pg, lane);
+            if (wait(&L.cnt->master_done[side][f], 1u)) {
+                if (L.traj) trajectory_task(S.f[f], S.n, Rk4{S.hstep, S.hhalf, S.hsixth}, lane);
+                else keystream_task(S.f[f], S.n, Rk4{S.hstep, S.hhalf, S.hsixth}, pg, lane);
+            }
             __threadfence();
             __syncwarp();
             if (lane == 0) publish(&L.cnt->ks_done[side][f], 1u, L.wpf, &L.cnt->t_ks[side][f]);
@@ -238,11 +269,19 @@ __device__ void mem_worker(const PLaunch &L, uint8_t *smem, unsigned *slot) {
     const uint32_t mtid = 32 * mem_index(threadIdx.x >> 5) + (threadIdx.x & 31);
     auto sync = [] { bar_sync(kBarMem, kMemThreads); };
     const PSide &S0 = L.s[0];
+    // The frame's keystream of one side is ready: its worker warps are done (worker pairs), or its emission
+    // tasks (one-trajectory route).
+    auto keystream_ready = [&](uint32_t side, uint32_t f) {
+        return L.traj ? wait_geq(&L.cnt->emit_done[side][f], L.s[side].emits[f], L)
+                      : wait_geq(&L.cnt->ks_done[side][f], L.wpf, L);
+    };
     for (;;) {
         // kind: 0 row pass (encrypting), 1 column pass (encrypting), 2 column pass (decrypting), 3 row pass
-        // (decrypting); side, frame and strip or band index of the task.  A frame's tasks, in queue order:
-        // encrypting: row bands (they read the row shifts of the keystream), column strips (the row-rotated
-        // frame); decrypting: column strips (its keystream, and the ciphertext), row bands (the strips).
+        // (decrypting), 4 emission (one-trajectory route); side, frame and strip, band or emission index of
+        // the task.  A frame's tasks, in queue order: encrypting: emissions (they read the frame's
+        // trajectory), row bands (they read the row shifts of the keystream), column strips (the row-rotated
+        // frame); decrypting: emissions, column strips (its keystream, and the ciphertext), row bands (the
+        // strips).
         if (mtid == 0) {
             const uint32_t t = ld_acquire(&L.cnt->abort) ? L.mem_tasks : atomicAdd(&L.cnt->mem_next, 1u);
             uint32_t kind = 0, side = 0, f = 0, idx = 0, ok = 0;
@@ -250,10 +289,16 @@ __device__ void mem_worker(const PLaunch &L, uint8_t *smem, unsigned *slot) {
                 const uint32_t r = segment(L.memb_begin, S0.count, t);
                 f = L.mprio[r];
                 uint32_t o = t - L.memb_begin[r];
-                if (S0.encrypt) {
+                const bool emit0 = o < S0.emits[f];
+                if (!emit0) o -= S0.emits[f];
+                if (emit0) {
+                    kind = 4;
+                    idx = o;
+                    ok = wait_geq(&L.cnt->ks_done[0][f], L.wpf, L);
+                } else if (S0.encrypt) {
                     if (o < S0.bands[f]) {
                         idx = o;
-                        ok = wait_geq(&L.cnt->ks_done[0][f], L.wpf, L);
+                        ok = keystream_ready(0, f);
                     } else if ((o -= S0.bands[f]) < S0.strips[f]) {
                         kind = 1;
                         idx = o;
@@ -261,11 +306,14 @@ __device__ void mem_worker(const PLaunch &L, uint8_t *smem, unsigned *slot) {
                     } else {
                         o -= S0.strips[f];
                         side = 1;
-                        if (o < L.s[1].strips[f]) {
+                        if (o < L.s[1].emits[f]) {
+                            kind = 4;
+                            idx = o;
+                            ok = wait_geq(&L.cnt->ks_done[1][f], L.wpf, L);
+                        } else if ((o -= L.s[1].emits[f]) < L.s[1].strips[f]) {
                             kind = 2;
                             idx = o;
-                            ok = wait_geq(&L.cnt->ks_done[1][f], L.wpf, L) &&
-                                 wait_geq(&L.cnt->strips_done[0][f], S0.strips[f], L);
+                            ok = keystream_ready(1, f) && wait_geq(&L.cnt->strips_done[0][f], S0.strips[f], L);
                         } else {
                             kind = 3;
                             idx = o - L.s[1].strips[f];
@@ -275,7 +323,7 @@ __device__ void mem_worker(const PLaunch &L, uint8_t *smem, unsigned *slot) {
                 } else if (o < S0.strips[f]) {
                     kind = 2;
                     idx = o;
-                    ok = wait_geq(&L.cnt->ks_done[0][f], L.wpf, L);
+                    ok = keystream_ready(0, f);
                 } else {
                     kind = 3;
                     idx = o - S0.strips[f];
@@ -283,7 +331,7 @@ __device__ void mem_worker(const PLaunch &L, uint8_t *smem, unsigned *slot) {
                 }
             }
             slot[0] = t;
-            slot[1] = kind | (side << 2) | (ok << 3);
+            slot[1] = kind | (side << 3) | (ok << 4);
             slot[2] = f;
             slot[3] = idx;
         }
@@ -291,16 +339,19 @@ __device__ void mem_worker(const PLaunch &L, uint8_t *smem, unsigned *slot) {
         const uint32_t t = slot[0], code = slot[1], f = slot[2], idx = slot[3];
         sync();
         if (t >= L.mem_tasks) return;
-        const uint32_t kind = code & 3, side = (code >> 2) & 1;
+        const uint32_t kind = code & 7, side = (code >> 3) & 1;
         if (!FHD_IN(f, L.s[0].count, kSitePersistTask) || !FHD_IN(side, L.sides, kSitePersistTask) ||
-            !FHD_IN(idx, kind == 0 || kind == 3 ? L.s[side].bands[f] : L.s[side].strips[f], kSitePersistTask))
+            !FHD_IN(idx, kind == 4 ? L.s[side].emits[f] : kind == 0 || kind == 3 ? L.s[side].bands[f] : L.s[side].strips[f],
+                    kSitePersistTask))
             continue;
         const FrameDesc &fd = L.s[side].f[f];
-        if (code & 8) mem_task(kind, fd, idx, smem, mtid);
+        if (code & 16) mem_task(kind, fd, L.s[side].n, idx, smem, mtid);
         __threadfence();
         sync();
-        if (mtid == 0 && (code & 8)) {
-            if (kind == 0 || kind == 3)
+        if (mtid == 0 && (code & 16)) {
+            if (kind == 4)
+                publish(&L.cnt->emit_done[side][f], 1u, L.s[side].emits[f], &L.cnt->t_emit[side][f]);
+            else if (kind == 0 || kind == 3)
                 publish(&L.cnt->rows_done[side][f], 1u, L.s[side].bands[f], &L.cnt->t_rows[side][f]);
             else
                 publish(&L.cnt->strips_done[side][f], 1u, L.s[side].strips[f], &L.cnt->t_strips[side][f]);

@@ -175,3 +175,34 @@ def test_long_streams_and_mixed_sizes_within_a_stream():
         enc.round_trip_persistent(dec, ei + ei[:1], di + di[:1])
     enc.close()
     dec.close()
+
+
+@pytest.fixture
+def ks_route():
+    """Set the process-wide keystream route for one test and restore the default afterwards."""
+    yield fhd.fhd_set_keystream_route
+    fhd.fhd_set_keystream_route("trajectory")
+
+
+@pytest.mark.parametrize("ks", ["pairs", "trajectory"])
+def test_round_trip_under_both_keystream_routes(ks_route, ks):
+    """The persistent round trip with the worker-pair keystream tasks and with the one-trajectory tasks (a
+    trajectory task per frame and side, then emission tasks of 180,224 bytes of B each): frames of one to
+    sixteen emission tasks, one whose size is not a multiple of 16 and one of a single task, all equal to
+    the oracle."""
+    ks_route(ks)
+    shapes = [(480, 640, 3), (16, 16, 3), (720, 1280, 3), (30, 50, 3), (481, 641, 3)]
+    keys = [si.key(1800 + k) for k in range(len(shapes) - 1)]
+    enc, dec, ei, di, frames, owner = _batch(keys, shapes, 32, seed=21)
+    enc.round_trip_persistent(dec, ei, di)
+    torch.cuda.synchronize()
+    enc.sync_status()
+    dec.sync_status()
+    refs = [oracle.Stream.from_key(k, n=32) for k in keys]
+    for k, F in enumerate(frames):
+        E_ref, H_ref = refs[owner[k]].encrypt(F)
+        assert np.array_equal(host(ei[k][2]), E_ref), k
+        assert bytes(host(ei[k][3])) == H_ref, k
+        assert np.array_equal(host(di[k][2]), F), k
+    enc.close()
+    dec.close()
