@@ -242,23 +242,29 @@ def test_worker_gate_on_the_receiver_and_a_null_schedule():
     assert torch.equal(R2, F2)
 
 
-def test_launch_count_per_call():
-    """fhd_launch_count counts every kernel: digest (SHA + fold), LHCS_m, workers, and the two
-    permutation passes on encryption; LHCS_m, workers and the two passes on decryption."""
-    key = si.key(620)
-    F = to_dev(si.uniform_frame(40, 56, 3, seed=621))
-    snd, rcv = fhd.Cipher(key), fhd.Cipher(key)
-    sid, rid = snd.open_stream(), rcv.open_stream()
-    E, R = torch.empty_like(F), torch.empty_like(F)
-    H = torch.empty(32, dtype=torch.uint8, device=dev())
-    l0 = fhd.fhd_launch_count()
-    snd.encrypt_frames([(sid, F, E, H)])
-    l1 = fhd.fhd_launch_count()
-    rcv.decrypt_frames([(rid, E, R, H)])
-    l2 = fhd.fhd_launch_count()
-    torch.cuda.synchronize()
-    assert (l1 - l0, l2 - l1) == (6, 4)
-    assert torch.equal(R, F)
+@pytest.mark.parametrize("ks,counts", [("trajectory", (7, 5)), ("pairs", (6, 4))])
+def test_launch_count_per_call(ks, counts):
+    """fhd_launch_count counts every kernel: digest (SHA + fold), LHCS_m, the keystream (trajectory and
+    emission, or the worker pairs), and the two permutation passes on encryption; LHCS_m, the keystream
+    and the two passes on decryption."""
+    fhd.fhd_set_keystream_route(ks)
+    try:
+        key = si.key(620)
+        F = to_dev(si.uniform_frame(40, 56, 3, seed=621))
+        snd, rcv = fhd.Cipher(key), fhd.Cipher(key)
+        sid, rid = snd.open_stream(), rcv.open_stream()
+        E, R = torch.empty_like(F), torch.empty_like(F)
+        H = torch.empty(32, dtype=torch.uint8, device=dev())
+        l0 = fhd.fhd_launch_count()
+        snd.encrypt_frames([(sid, F, E, H)])
+        l1 = fhd.fhd_launch_count()
+        rcv.decrypt_frames([(rid, E, R, H)])
+        l2 = fhd.fhd_launch_count()
+        torch.cuda.synchronize()
+        assert (l1 - l0, l2 - l1) == counts
+        assert torch.equal(R, F)
+    finally:
+        fhd.fhd_set_keystream_route("trajectory")
 
 
 def test_sm_partition_matches_single_stream():
