@@ -56,6 +56,10 @@ RK4_FP64_OPS = 104      # per chain step: 4 x 13 (Eq. 1) + 3 x 8 (stages) + 4 x 
 TRAFFIC_PER_FRAME = {"keystream": (29952 + 0) / 4,
                      "encrypt": (186890496 + 130175232 + 374881536 + 156594944) / 30,
                      "decrypt": (411278336 + 127123200 + 186961664 + 125687808) / 30, "sha": None, "master": None}
+# The one-trajectory keystream route, per 1080p frame: trajectory_kernel on a 4-frame clip (24,064 bytes read,
+# none written: the records stay in L2) plus emit_kernel on the 30-frame clip (5,954,048 read, 126,382,848
+# written), both from ncu captures.
+TRAFFIC_TRAJ_PER_FRAME = (24064 + 0) / 4 + (5954048 + 126382848) / 30
 
 
 def parse():
@@ -757,7 +761,7 @@ def run_ours(args):
         n_l = kern[k]["launches_per_step"] * args.steps
         gpu_ach = n_l * steps * per_step_frames * RK4_FP64_OPS / (busy_ms(k) / 1000.0) / 1e12
         return {"bound": "alu", "achieved": ach, "peak": sp_peak, "unit": "Gop/s (binary64 lane-ops, one sub-partition)",
-                "frac": ach / sp_peak, "traffic": None,
+                "frac": ach / sp_peak, "traffic": TRAFFIC_TRAJ_PER_FRAME * per_step_frames,
                 "peak_source": fp64_source + f", divided by {sms} SMs x 4 sub-partitions",
                 "per_launch_units": f"{per_step_frames} frames x one trajectory of {steps} RK4 steps "
                                     f"({RK4_FP64_INSTR} binary64 warp instructions each) + the D/B emission",
