@@ -147,8 +147,8 @@ int decrypt_frames_ex(fhd_cipher *c, uint32_t count, const fhd_frame *frames, vo
  * frames[i].digest, before LHCS_m runs (after it with FHD_TRANSPORT_MASKED,
  * whose transmitted digest LHCS_m writes).  A receiver on the same device can
  * wait on it to start its own chaotic stage while the sender's keystream and
- * permutation are still running.  For more than 128 frames it is recorded
- * after the digests of the last group of 128.  `keystream_done` (may be
+ * permutation are still running.  For more than 256 frames it is recorded
+ * after the digests of the last group of 256.  `keystream_done` (may be
  * NULL) is recorded right after the last worker kernel (Sec. II-B), before
  * the permutation: later chaotic work gated on it does not share the FP64
  * pipes with this call's keystream, while the permutation may overlap it. */
@@ -190,7 +190,7 @@ int decrypt_frames_split(fhd_cipher *c, uint32_t count, const fhd_frame *frames,
  *   master_done    recorded right after LHCS_m;
  *   keystream_done recorded right after the last worker kernel, before the
  *                  permutation.
- * All hooks apply to the first group of 128 frames of the call, the output
+ * All hooks apply to the first group of 256 frames of the call, the output
  * events to the last; groups of one call run in order.  A pipeline that keeps
  * many CUDA streams busy (clips in flight, serving lanes, and with the SM
  * partition two internal streams per caller stream) should run with

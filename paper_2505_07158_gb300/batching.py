@@ -39,14 +39,12 @@ class GraphedCall:
         for sid, st in saved.items():
             cipher.import_state(sid, st)
         self.graph = torch.cuda.CUDAGraph()
+        l0 = _lib.fhd_launch_count()
         with torch.cuda.graph(self.graph, stream=self.stream):
             fn(self.items, stream=self.stream)
         torch.cuda.synchronize()
-        self.kernels_per_replay = self._kernels()
-
-    def _kernels(self) -> int:
-        chunks = -(-len(self.items) // 128)
-        return chunks * (4 if self.encrypt else 3)
+        # the library counts the kernels it launches, captured ones included
+        self.kernels_per_replay = _lib.fhd_launch_count() - l0
 
     def replay(self):
         self.graph.replay()

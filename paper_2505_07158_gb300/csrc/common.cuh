@@ -9,7 +9,7 @@ namespace fhd {
 
 // Frames per launch: the per-frame descriptors travel as a kernel parameter
 // (well under the 32 KB parameter limit of sm_70+ with CUDA 12.1+).
-constexpr int kMaxBatch = 128;
+constexpr int kMaxBatch = 256;
 
 // Per-frame launch descriptor.  All pointers are device pointers.
 struct FrameDesc {

@@ -314,11 +314,11 @@ def test_sm_partition_matches_single_stream():
 
 
 def test_more_than_one_descriptor_group():
-    """130 frames of one stream in one call (two groups of at most 128 descriptors): the groups
-    reuse the scratch, so each group's LHCS_m must wait for the previous group's workers; with the
+    """260 frames of one stream in one call (two groups of at most 256 descriptors): the groups
+    reuse the scratch, so each group's LHCS_m must wait for the previous group's keystream; with the
     SM partition they run on different internal streams."""
     key = si.key(640)
-    F = 130
+    F = 260
     frames = torch.stack([to_dev(si.uniform_frame(8, 16, 3, seed=641 + t)) for t in range(F)])
     snd, rcv = fhd.Cipher(key), fhd.Cipher(key)
     sid, rid = snd.open_stream(), rcv.open_stream()
@@ -331,7 +331,7 @@ def test_more_than_one_descriptor_group():
     ref = oracle.Stream.from_key(key)
     for t in range(F):
         E_ref, H_ref = ref.encrypt(host(frames[t]))
-        if t in (0, 127, 128, 129):
+        if t in (0, 255, 256, 259):
             assert np.array_equal(host(E[t]), E_ref), t
             assert bytes(host(H[t])) == H_ref, t
 
