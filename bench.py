@@ -1151,8 +1151,8 @@ def run_stress(rank, fhd, torch, frames=256):
     Hd = torch.empty((frames, 32), dtype=torch.uint8, device=dev)
     # scratch for the batch is sized by a first call on a throwaway stream of the same handles
     tmp_s, tmp_r = enc.open_stream(), dec.open_stream()
-    enc.encrypt_frames([(tmp_s, src[k], E[k], Hd[k]) for k in range(min(frames, 128))])
-    dec.decrypt_frames([(tmp_r, E[k], R[k], Hd[k]) for k in range(min(frames, 128))])
+    enc.encrypt_frames([(tmp_s, src[k], E[k], Hd[k]) for k in range(min(frames, 256))])
+    dec.decrypt_frames([(tmp_r, E[k], R[k], Hd[k]) for k in range(min(frames, 256))])
     torch.cuda.synchronize()
     enc.profile(True)
     dec.profile(True)
