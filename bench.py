@@ -112,8 +112,9 @@ def parse():
                     help="time the tile shapes of every workload's frame sizes and the clip pipeline's work split "
                          "(layout, clips in flight, worker window) and write the table to OUT.json "
                          "(the library's tuned.json format); prints it and exits")
-    ap.add_argument("--copy-streams", type=int, default=2, choices=[1, 2, 4],
-                    help="end-to-end run: CUDA streams per copy direction, clips taking them in turn")
+    ap.add_argument("--copy-streams", type=int, default=None, choices=[1, 2, 4],
+                    help="end-to-end run: CUDA streams per copy direction, clips taking them in turn (default: "
+                         "the tuned table's, else 2)")
     ap.add_argument("--e2e-out-buffers", type=int, default=2,
                     help="end-to-end run: pinned host buffers the decrypted clips are copied into, in turn "
                          "(0: one per clip in flight)")
@@ -387,11 +388,14 @@ def run_ours(args):
     from paper_2505_07158_gb300 import autotune
     tuned = autotune.tune([(HGT, WID, CH)])
     # the clip pipeline's work split: flags, else the tuned table for this GPU, else the built-in defaults
+    # (the worker-pair route has its own record in the table)
     pipe = autotune.pipeline_defaults() or {}
+    if args.keystream_route == "pairs":
+        pipe = pipe.get("pairs_route") or pipe
     split_source = {}
     for name, attr, default in (("layout", "layout", "throughput"), ("inflight", "inflight", 5),
                                 ("worker_window", "worker_window", 3), ("int_mix", "int_mix", 0),
-                                ("worker_smem", "worker_smem", 0)):
+                                ("worker_smem", "worker_smem", 0), ("copy_streams", "copy_streams", 2)):
         if getattr(args, attr) is None:
             setattr(args, attr, pipe.get(name, default))
             split_source[name] = "tuned table" if name in pipe else "built-in default"
@@ -1236,6 +1240,39 @@ def run_dry(args):
     return 0
 
 
+def pick_trajectory_split(results):
+    """The clips-in-flight / copy-streams candidate to keep: the best end-to-end value among those whose
+    device-resident value is within 1 % of the best (the headline's limit is the stream's LHCS_m chain, so
+    the device-resident values of the deeper pipelines tie).  results: {(inflight, copy_streams): (value,
+    e2e)}, None for a failed run."""
+    ok = {k: v for k, v in results.items() if v}
+    top = max(v[0] for v in ok.values())
+    near = [k for k, v in ok.items() if v[0] >= 0.99 * top]
+    return max(near, key=lambda k: (ok[k][1], ok[k][0]))
+
+
+def tune_trajectory_pipeline(inflights=(8, 10, 12, 16), copy_streams=(1, 2)):
+    """The one-trajectory route's work split: the headline at each clips-in-flight / copy-streams candidate,
+    each in its own process (120 steps, median of three timed regions)."""
+    results = {}
+    for inf in inflights:
+        for cs in copy_streams:
+            cmd = [sys.executable, os.path.abspath(__file__), "--no-extras", "--no-cpu-baseline", "--no-probe",
+                   "--repeats", "3", "--keystream-route", "trajectory", "--inflight", str(inf),
+                   "--copy-streams", str(cs)]
+            r = subprocess.run(cmd, capture_output=True, text=True)
+            lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+            d = json.loads(lines[-1]) if r.returncode == 0 and lines else None
+            results[(inf, cs)] = (d["value"], d["e2e"]["value"]) if d else None
+            print(f"pipeline trajectory inflight={inf} copy_streams={cs}: {results[(inf, cs)]}", flush=True)
+    inf, cs = pick_trajectory_split(results)
+    return {"keystream_route": "trajectory", "inflight": inf, "copy_streams": cs, "worker_window": 0,
+            "frames_per_s": results[(inf, cs)][0], "e2e_frames_per_s": results[(inf, cs)][1],
+            "candidates": {f"inflight {a}, copy streams {b}": v for (a, b), v in results.items()},
+            "how": "bench.py headline, 120 steps, median of 3 timed regions per candidate, one process each "
+                   "(frames/s, e2e frames/s); kept: the best e2e within 1 % of the best frames/s"}
+
+
 def run_tune(args):
     """Tile shapes of every workload's frame sizes (timed afresh), then the clip pipeline's work split: the
     headline under each candidate setting, each in its own process (a bench run of 15 steps, median of three
@@ -1248,6 +1285,14 @@ def run_tune(args):
     cache = autotune.load_cache()
     gpu = autotune._gpu_name()
     entries = {k: cache[gpu]["shapes"][k] for k in tuned}
+    if args.keystream_route == "trajectory":
+        pipeline = tune_trajectory_pipeline()
+        pipeline["pairs_route"] = (autotune.pipeline_defaults() or {}).get("pairs_route")
+        table = {gpu: {"shapes": entries, "pipeline": pipeline}}
+        with open(args.tune, "w") as f:
+            json.dump(table, f, indent=1, sort_keys=True)
+        print(json.dumps(table))
+        return 0
     grid = [("throughput", i, w) for i in (3, 4, 5, 6) for w in (2, 3, 4) if w < i] + [("latency", 5, 3)]
     results = {}
     for layout, inflight, window in grid:

@@ -53,3 +53,26 @@ def test_tuned_table_carries_the_pipeline_split():
     assert pipe["layout"] in ("latency", "throughput")
     assert pipe["worker_window"] < pipe["inflight"]
     assert 0 <= pipe["worker_smem"] <= 232448
+
+
+def test_tuned_table_records_both_keystream_routes_and_the_trajectory_pick():
+    """The table's pipeline record is the one-trajectory route's (clips in flight, copy streams), with the
+    worker-pair route's own record beside it; the tuner's pick keeps the best end-to-end value among the
+    candidates within 1 % of the best device-resident value, skipping failed runs."""
+    sys.path.insert(0, ROOT)
+    import bench
+    with open(os.path.join(ROOT, "paper_2505_07158_gb300", "tuned.json")) as f:
+        pipe = json.load(f)["NVIDIA GB300"]["pipeline"]
+    assert pipe["keystream_route"] == "trajectory" and pipe["copy_streams"] in (1, 2, 4)
+    pairs = pipe["pairs_route"]
+    assert pairs["layout"] in ("latency", "throughput") and pairs["worker_window"] < pairs["inflight"]
+    res = {(8, 1): (14000.0, 12000.0), (12, 2): (14460.0, 13400.0), (16, 2): (14470.0, 10000.0),
+           (10, 1): None, (12, 1): (14300.0, 13900.0)}
+    assert bench.pick_trajectory_split(res) == (12, 2)      # (12, 1) is more than 1 % below the best value
+    res[(12, 1)] = (14400.0, 13900.0)
+    assert bench.pick_trajectory_split(res) == (12, 1)
+    sys.argv, old = ["bench.py"], sys.argv
+    try:
+        assert bench.parse().copy_streams is None            # filled in from the table at run time
+    finally:
+        sys.argv = old
