@@ -3,8 +3,9 @@
 
 Workload (one "step"): the 30-frame 1920x1080x3 uint8 clip (smooth 2-D
 gradients + Gaussian noise sigma 8, shifted 2 px per frame) of one video
-stream is encrypted (digest -> LHCS_m -> worker keystream -> fused confusion +
-XOR, Algorithm 1) and then decrypted (inverse), one library call each.  The
+stream is encrypted (digest -> LHCS_m -> keystream, by default from one LHCS_m
+trajectory per frame -> confusion + XOR, Algorithm 1) and then decrypted
+(inverse), one library call each.  The
 metric is round-tripped 1080p frames per second (30 frames per step).
 Inputs are resident in HBM when the timed region starts and are larger than
 L2 (30 x 6.2 MB frames + outputs + keystream ~ 560 MB).
