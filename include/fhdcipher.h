@@ -261,10 +261,14 @@ int cipher_set_persistent_limits(fhd_cipher *c, uint64_t timeout_ns, int hold_fr
  * for the handle's CUDA streams): for frame k < count (call order, at most
  * 64), ms[9k + 0] = when its digest was published, and for side s (0: this
  * handle's direction, 1: the receiver of a round trip) ms[9k + 1 + 4s ..
- * 9k + 4 + 4s] = when its LHCS_m iterates, its last worker warp, its last row
- * band and its last column strip were done, in milliseconds after the
- * launch's start; -1 where that never happened (e.g. no such side). */
+ * 9k + 4 + 4s] = when its LHCS_m iterates, its keystream (its last worker
+ * warp, or its trajectory on the one-trajectory route), its last row band and
+ * its last column strip were done, in milliseconds after the launch's start;
+ * -1 where that never happened (e.g. no such side). */
 int cipher_persistent_trace(fhd_cipher *c, uint32_t count, double *ms);
+/* Device scratch one frame of this shape takes in a call (sub-frame digests,
+ * LHCS_m iterates, D, B, the frame between the permutation passes and the
+ * trajectory records), each part 16-byte aligned. */
 uint64_t fhd_frame_scratch_bytes(uint32_t n_workers, uint32_t height, uint32_t width, uint32_t channels);
 
 /* Receiver-side integrity check (the paper transmits the digests with the
